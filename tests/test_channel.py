@@ -1,0 +1,63 @@
+"""The shared synthetic-channel generator (Section II eqs. 1-3 readings)."""
+import math
+
+import numpy as np
+import torch
+
+from paper_2512_16543_gb300 import channel as ch
+
+
+def test_shapes_dtype_and_reproducibility():
+    sc = ch.scenario_single_small()
+    p1 = ch.draw_trajectories(sc, 3, seed=11)
+    p2 = ch.draw_trajectories(sc, 3, seed=11)
+    H1 = ch.channel_at(p1, 5)
+    H2 = ch.channel_at(p2, 5)
+    assert H1.shape == (3, sc.K, sc.N) and H1.dtype == torch.complex128
+    assert torch.equal(H1, H2)
+    assert not torch.equal(H1, ch.channel_at(ch.draw_trajectories(sc, 3, seed=12), 5))
+    assert ch.channel_at(p1, 5, dtype=torch.complex64).dtype == torch.complex64
+
+
+def test_los_part_is_unit_norm_steering_times_gain():
+    sc = ch.LeoScenario(n_x=4, n_y=4, K=3, k_rician_db=300.0)   # K_R -> infinity: pure LOS
+    p = ch.draw_trajectories(sc, 2, seed=1)
+    H = ch.channel_at(p, 0).numpy()
+    xy = p.user_xy.numpy()
+    dist = np.sqrt(xy[..., 0] ** 2 + xy[..., 1] ** 2 + sc.h_alt ** 2)
+    np.testing.assert_allclose(np.linalg.norm(H, axis=-1), sc.h_alt / dist, rtol=1e-12)
+    # every element has the same modulus (a = N^-1/2 exp(j kappa . r_m))
+    ref = np.broadcast_to((sc.h_alt / dist)[..., None] / math.sqrt(sc.N), H.shape)
+    np.testing.assert_allclose(np.abs(H), ref, rtol=1e-12)
+
+
+def test_steering_phase_matches_geometry():
+    sc = ch.LeoScenario(n_x=2, n_y=1, K=1, k_rician_db=300.0)
+    p = ch.draw_trajectories(sc, 1, seed=2)
+    H = ch.channel_at(p, 3).numpy()[0, 0]
+    x, y = p.user_xy.numpy()[0, 0]
+    xs = sc.v * sc.dt * 3
+    d = np.array([x - xs, y, -sc.h_alt])
+    u = d / np.linalg.norm(d)
+    # elements at x = -lambda/4 and +lambda/4: phase difference kappa_x * lambda / 2 = pi u_x
+    dphi = np.angle(H[1] / H[0])
+    assert abs(dphi - math.pi * u[0]) < 1e-9
+
+
+def test_rician_power_split_and_parameters():
+    sc = ch.scenario_batched_256x32()
+    assert sc.N == 256 and sc.K == 32
+    assert abs(sc.alpha - 32 / 10.0) < 1e-12 and abs(sc.sigma2 - 0.1) < 1e-12
+    p = ch.draw_trajectories(sc, 64, seed=3)
+    g = p.g_nlos.numpy()
+    assert abs(np.mean(np.sum(np.abs(g) ** 2, axis=-1)) - 1.0) < 0.02   # E||g||^2 = 1
+
+
+def test_device_argument_and_subset():
+    sc = ch.scenario_single_small()
+    p = ch.draw_trajectories(sc, 4, seed=4)
+    full = ch.channel_at(p, 2)
+    sub = ch.channel_at(p, 2, index=torch.tensor([1, 3]))
+    assert torch.equal(sub, full[[1, 3]])
+    T = ch.trajectory(p, 3, t0=2)
+    assert torch.equal(T[0], full)
