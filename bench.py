@@ -1,0 +1,407 @@
+"""Benchmark: precoder updates/s of WB-arSVD vs full-inversion RZF on one GB300.
+
+Workload (batched_256x32): 1024 independent LEO trajectories, 16x16 UPA (N = 256) at 20 GHz,
+K = 32 users in a 50 km disc, 600 km altitude, 7.5 km/s, 10 ms between snapshots, Rician
+K_R = 10 dB, SNR 10 dB (alpha = K/SNR), complex64 with FP32 arithmetic, arSVD p = 8,
+k_init = 2, rank capped at 16, direct re-inversion every 20 snapshots.  One launch per
+snapshot covers all 1024 instances.  Inputs are synthetic (seeded) and resident in HBM before
+the timed region; L2 is flushed between timed snapshots (outside the per-snapshot events).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own 1024 trajectories
+(weak scaling, no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "precoder updates/s, WB-arSVD vs full-inverse RZF at fixed rate gap; p99 ms"
+WORKLOAD = ("batched_256x32: 1024 trajectories x (16x16 UPA, N=256, K=32), complex64/FP32, "
+            "p=8, k_init=2, r_max=16, re-inverse every 20 snapshots, 10 ms snapshots")
+BATCH, NX, K_USERS = 1024, 16, 32
+ETA_GRID = (0.65, 0.8, 0.9, 0.95, 0.99)
+RATE_GAP_BOUND = 0.05        # bit/s/Hz, mean |R_WB - R_full|
+
+# DRAM traffic of the step kernel per launch from the committed ncu capture, valid only for
+# the kernel source it was taken on (sha256 of step_kernel.cuh, first 16 hex digits).
+NCU_TRAFFIC = {"source_sha": None, "bytes_per_launch": None}
+
+
+def kernel_source_sha() -> str:
+    p = os.path.join(ROOT, "paper_2512_16543_gb300", "csrc", "step_kernel.cuh")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def algorithmic_bytes_per_update(N: int, K: int, method: str) -> int:
+    """HBM bytes one instance-update must move: read H_t, write W; WB also reads and writes
+    the resident G and X (complex64)."""
+    b = 8 * (K * N + N * K)
+    if method == "wb":
+        b += 8 * 4 * K * K
+    return b
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+def _oracle_worker(args):
+    """Run the FP64 oracle on a few trajectories; returns (updates, seconds)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from oracle import method as om
+    Hs_list, alpha, sigma2, p_t, rule_kw, method, inst0 = args
+    rule = om.RankRule(**rule_kw)
+    t0 = time.perf_counter()
+    n = 0
+    for j, Hs in enumerate(Hs_list):
+        om.run_trajectory([np.asarray(h) for h in Hs], alpha, p_t, sigma2, method=method,
+                          rule=rule, instance=inst0 + j)
+        n += len(Hs)
+    return n, time.perf_counter() - t0
+
+
+def cpu_oracle_baseline(params, sc, rule_kw, n_inst: int, n_steps: int, method: str = "wb",
+                        workers: int | None = None, t0: int = 0):
+    """Time the oracle on n_inst trajectories x n_steps snapshots across a spawn pool."""
+    import multiprocessing as mp
+
+    import numpy as np
+    import torch
+
+    from paper_2512_16543_gb300 import channel
+    idx = torch.arange(n_inst)
+    Hs = np.stack([channel.channel_at(params, t0 + s, index=idx, dtype=torch.complex64)
+                   .numpy().astype(np.complex128) for s in range(n_steps)], axis=1)   # [B,T,K,N]
+    workers = workers or max(1, min(16, os.cpu_count() or 1, n_inst))
+    chunks = [list(range(i, n_inst, workers)) for i in range(workers)]
+    jobs = [([Hs[i] for i in ch], sc.alpha, sc.sigma2, sc.p_t, rule_kw, method, ch[0])
+            for ch in chunks if ch]
+    ctx = mp.get_context("spawn")
+    t_start = time.perf_counter()
+    with ctx.Pool(len(jobs), initializer=os.environ.__setitem__,
+                  initargs=("OPENBLAS_NUM_THREADS", "1")) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t_start
+    n = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return {"updates": n, "wall_s": wall, "busy_s": busy, "cores": len(jobs),
+            "value": n / busy}
+
+
+# ---------------------------------------------------------------------------- main
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--eta", type=float, default=None, help="energy fraction (default: grid)")
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--seed", type=int, default=2512)
+    return ap.parse_args()
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier_max(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step a bounded sample of the workload."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2512_16543_gb300 import channel
+    sc = channel.scenario_batched_256x32()
+    params = channel.draw_trajectories(sc, args.batch, seed=args.seed)
+    rule_kw = dict(eta=args.eta or 0.65, k_init=2, p=8, r_max=16, reinverse_period=20,
+                   seed=77)
+    n_inst = 32
+    res = cpu_oracle_baseline(params, sc, rule_kw, n_inst, args.warmup + args.steps)
+    value = res["value"]
+    sample = (f"{n_inst} of {args.batch} trajectories x {args.warmup + args.steps} snapshots, "
+              f"WB-arSVD eta={rule_kw['eta']}, FP64 numpy oracle, spawn pool")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * args.batch / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "eta": rule_kw["eta"]},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": res["cores"],
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    from paper_2512_16543_gb300 import binding, channel
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sc = channel.scenario_batched_256x32()
+    B = args.batch
+    W_, K_ = args.warmup, args.steps
+    assert W_ >= 3, "at least 3 warm-up steps"
+    params = channel.draw_trajectories(sc, B, seed=args.seed + 7919 * rank)
+    ids = [rank * B + b for b in range(B)]
+    T = 1 + W_ + K_
+    Hs = torch.stack([channel.channel_at(params, t, device=dev, dtype=torch.complex64)
+                      for t in range(T)])                    # [T, B, K, N] resident in HBM
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def make(method, eta):
+        rule = binding.RankRule(eta=eta, k_init=2, p=8, r_max=16, reinverse_period=20,
+                                seed=77)
+        h = binding.WBRZF(B, sc.N, sc.K, sc.alpha, sc.sigma2, p_t=sc.p_t, rule=rule,
+                          method=method, device=dev)
+        h.set_instance_ids(ids)
+        return h
+
+    def timed_run(h, collect_rates=False):
+        Wout = torch.empty(B, sc.N, sc.K, dtype=torch.complex64, device=dev)
+        h.full_inverse(Hs[0], Wout)
+        for t in range(1, 1 + W_):
+            h.update(Hs[t], Wout)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K_)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K_)]
+        rates = []
+        launches0 = h.launches
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for i in range(K_):
+            flush.zero_()                                  # evict L2 outside the events
+            starts[i].record(stream)
+            h.update(Hs[1 + W_ + i], Wout)
+            ends[i].record(stream)
+            if collect_rates:
+                rates.append(h.sum_rate()[1].clone())
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        return ms, h.launches - launches0, rates
+
+    # ---- method gap on the eta grid (rates of both methods on the same snapshots)
+    full = make("full", 0.9)
+    ms_full, _, rates_full = timed_run(full, collect_rates=True)
+    full.close()
+    grid = [args.eta] if args.eta else list(ETA_GRID)
+    chosen, gaps, wb_runs = None, {}, {}
+    clock = ClockSampler(local)
+    for eta in grid:
+        h = make("wb", eta)
+        if chosen is None and eta == grid[0]:
+            clock.start()
+        ms, launches, rates = timed_run(h, collect_rates=True)
+        info = h.step_info()
+        h.close()
+        gap = float(torch.stack([(a - b).abs() for a, b in zip(rates, rates_full)]).mean())
+        gaps[eta] = gap
+        wb_runs[eta] = (ms, launches, info)
+        if chosen is None:
+            clk = clock.stop()
+            if gap <= RATE_GAP_BOUND:
+                chosen = eta
+                break
+    if chosen is None:
+        chosen = grid[-1]
+    ms_wb, launches, info = wb_runs[chosen]
+
+    tot_wb = barrier_max(sum(ms_wb) / 1e3, world)
+    tot_full = barrier_max(sum(ms_full) / 1e3, world)
+    value = world * B * K_ / tot_wb
+    value_full = world * B * K_ / tot_full
+    p50, p99 = float(np.percentile(ms_wb, 50)), float(np.percentile(ms_wb, 99))
+    f50, f99 = float(np.percentile(ms_full, 50)), float(np.percentile(ms_full, 99))
+
+    # ---- roofline of the step kernel (one launch per snapshot)
+    peaks = measured_peaks()
+    abytes = B * algorithmic_bytes_per_update(sc.N, sc.K, "wb")
+    achieved = abytes / (statistics.mean(ms_wb) / 1e3) / 1e9
+    traffic = (NCU_TRAFFIC["bytes_per_launch"]
+               if NCU_TRAFFIC["source_sha"] == kernel_source_sha() else None)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": abytes}
+    abytes_full = B * algorithmic_bytes_per_update(sc.N, sc.K, "full")
+    ach_full = abytes_full / (statistics.mean(ms_full) / 1e3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Hh = Hs[1 + W_:1 + W_ + K_].cpu().pin_memory()
+        Wh = torch.empty(B, sc.N, sc.K, dtype=torch.complex64).pin_memory()
+        Rh = torch.empty(B, dtype=torch.float32).pin_memory()
+        h = make("wb", chosen)
+        Hd = torch.empty_like(Hs[0])
+        Wd = torch.empty(B, sc.N, sc.K, dtype=torch.complex64, device=dev)
+        Rd = torch.empty(B, dtype=torch.float32, device=dev)
+        h.full_inverse(Hs[0], Wd)
+        for t in range(1, 1 + W_):
+            h.update(Hs[t], Wd)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(K_):
+            Hd.copy_(Hh[i], non_blocking=True)
+            h.update(Hd, Wd)
+            binding._check(binding.lib().wbrzf_sum_rate(h._h, None, Rd.data_ptr()), "sum_rate")
+            Wh.copy_(Wd, non_blocking=True)
+            Rh.copy_(Rd, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        h.close()
+        t_e2e = barrier_max(e0.elapsed_time(e1) / 1e3, world)
+        e2e = {"value": world * B * K_ / t_e2e, "unit": "updates/s",
+               "h2d_bytes_per_step": Hh[0].numel() * 8,
+               "d2h_bytes_per_step": Wh.numel() * 8 + Rh.numel() * 4}
+
+    # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N = 1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rule_kw = dict(eta=chosen, k_init=2, p=8, r_max=16, reinverse_period=20, seed=77)
+        n_inst, n_steps = 32, 40
+        res = cpu_oracle_baseline(params, sc, rule_kw, n_inst, n_steps)
+        cpu = {"value": res["value"], "unit": "updates/s", "cores": res["cores"],
+               "kind": "oracle",
+               "sample": f"{n_inst} of {B} trajectories x {n_steps} snapshots (WB-arSVD, "
+                         f"eta={chosen}), FP64 numpy oracle, one process per core"}
+
+    if rank == 0:
+        branches = {}
+        for i in info:
+            branches[binding.BRANCH_NAMES[i["branch"]]] = branches.get(
+                binding.BRANCH_NAMES[i["branch"]], 0) + 1
+        line = {
+            "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+            "steps": K_, "warmup": W_, "ms_per_step": statistics.mean(ms_wb),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": world * B, "eta": chosen,
+                       "eta_grid_gaps_bits": gaps, "rate_gap_bound_bits": RATE_GAP_BOUND,
+                       "l2": "flushed (512 MB write) between timed snapshots",
+                       "parallelism": f"instances sharded over {world} GPU(s)"},
+            "p50_ms": p50, "p99_ms": p99,
+            "full_inverse_rzf": {"value": value_full, "unit": "updates/s", "p50_ms": f50,
+                                 "p99_ms": f99, "hbm_gbs": ach_full},
+            "wb_over_full": value / value_full,
+            "last_step_branches": branches,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * wbrzf.h -- C ABI of the GB300 (sm_103a) WB-arSVD RZF precoder-update library.
+ *
+ * Method (Momani, Delamotte, Knopp, "Efficient Precoding for LEO Satellites: A Low-Complexity
+ * Matrix Inversion Method via Woodbury Matrix Identity and arSVD"):
+ *   For each of `batch` independent instances (one satellite beam / trajectory each) and each
+ *   snapshot t with channel H_t (K users x N antennas):
+ *     G_t  = H_t H_t^H + alpha I_K                         (Gram matrix, Section II eq. 5)
+ *     dG   = G_t - G_{t-1}                                 (Section III eqs. 7-9)
+ *     dG  ~= U_r Sigma_r V_r^H by adaptive randomized SVD  (Section IV, eq. 14, Algorithm 1)
+ *     X    = G_t^{-1} by the Woodbury identity when k_est/K <= switch ratio, else directly
+ *                                                          (Section III eq. 12, Algorithm 2)
+ *     W    = s H_t^H X,  s = sqrt(P_t) / ||H_t^H X||_F     (RZF precoder and power constraint,
+ *                                                           Section II eq. 5)
+ *     SINR_n, R_sum = sum_n log2(1 + SINR_n)               (Section VI eq. 15; user n's gain on
+ *                                                           beam i is (H_t W)_{n i})
+ *   One kernel launch per call processes every instance; all of the steps above run in the
+ *   library's own CUDA kernels.
+ *
+ * Memory and layout conventions (all calls):
+ *   - Complex numbers are interleaved (re, im): complex64 (2 x float) for WBRZF_C64*,
+ *     complex128 (2 x double) for WBRZF_C128.
+ *   - H_t: device pointer, `batch` contiguous row-major K x N matrices (instance b at
+ *     H_t + b*K*N elements).  W_out: device pointer, `batch` contiguous row-major N x K
+ *     matrices.  Both are owned by the caller; the library never keeps them after a call
+ *     returns (it copies what it needs into its workspace).
+ *   - workspace: device memory owned by the caller, at least wbrzf_workspace_bytes() bytes,
+ *     256-byte aligned, valid until wbrzf_destroy().  It holds the resident state (G_{t-1},
+ *     X = G^{-1} per instance), per-instance parameters and per-step outputs.  The library
+ *     allocates no device memory.
+ *   - Every call enqueues its work on the handle's CUDA stream and returns without waiting,
+ *     except the calls documented as synchronising.
+ *   - Errors: every call returns a wbrzf_status; nothing is thrown across the ABI.  A handle
+ *     is not thread-safe; distinct handles are independent.
+ */
+#ifndef WBRZF_H
+#define WBRZF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wbrzf wbrzf;
+
+typedef enum {
+  WBRZF_OK = 0,
+  WBRZF_ERR_INVALID_ARG = 1,     /* a size, pointer, alignment or rule field is out of range */
+  WBRZF_ERR_NOT_INITIALIZED = 2, /* wbrzf_update before the first wbrzf_full_inverse         */
+  WBRZF_ERR_WORKSPACE = 3,       /* workspace smaller than wbrzf_workspace_bytes()           */
+  WBRZF_ERR_NUMERICAL = 4,       /* an instance could not be inverted (see step info)        */
+  WBRZF_ERR_CUDA = 5,            /* a CUDA runtime call failed (see wbrzf_last_cuda_error)   */
+  WBRZF_ERR_UNSUPPORTED = 6      /* shape or precision outside what this build supports      */
+} wbrzf_status;
+
+typedef enum {
+  WBRZF_C128 = 0,     /* complex128 in/out, FP64 arithmetic throughout                       */
+  WBRZF_C64 = 1       /* complex64 in/out, FP32 arithmetic (FP32-faithful Gram and dG)       */
+} wbrzf_precision;
+
+typedef enum {
+  WBRZF_METHOD_WB_ARSVD = 0,      /* Algorithm 2: Woodbury + arSVD, direct inverse on demand */
+  WBRZF_METHOD_FULL_INVERSE = 1   /* conventional RZF: direct inverse at every snapshot      */
+} wbrzf_method;
+
+/* Branch taken by one instance at one snapshot (wbrzf_step_info.branch). */
+enum {
+  WBRZF_BRANCH_KEEP = 0,      /* ||dG||_F <= dg_floor_rel ||G_t||_F: X kept                  */
+  WBRZF_BRANCH_WOODBURY = 1,  /* rank-r Woodbury update (eq. 12)                             */
+  WBRZF_BRANCH_INIT = 2,      /* first snapshot: direct inverse (Algorithm 2, else-branch)   */
+  WBRZF_BRANCH_PERIODIC = 3,  /* periodic direct re-inversion                                */
+  WBRZF_BRANCH_RANK = 4,      /* k_est > r_max or k_est/K > switch_ratio: direct inverse     */
+  WBRZF_BRANCH_FULL = 5,      /* conventional method: direct inverse                         */
+  WBRZF_BRANCH_FALLBACK = 6   /* Woodbury capacitance matrix numerically singular: direct    */
+};
+
+/* Per-instance status bits (wbrzf_step_info.status). */
+enum {
+  WBRZF_STATUS_OK = 0,
+  WBRZF_STATUS_NOT_PD = 1,      /* direct inverse met a non-positive pivot: G_t not HPD      */
+  WBRZF_STATUS_NONFINITE = 2    /* a NaN/Inf reached the precoder or the scale               */
+};
+
+/* Rank rule and method parameters (Algorithm 1 inputs, Algorithm 2 switch). */
+typedef struct {
+  double eta;               /* energy fraction retained, 0 < eta <= 1 (eq. 14)              */
+  int k_init;               /* initial working rank k0 >= 1 (Algorithm 1)                   */
+  int p;                    /* oversampling p >= 0; sketch width d = min(k0 + p, K)          */
+  int i_max;                /* iterations; 0 -> ceil(log2(r_max / k_init)) + 1               */
+  int r_max;                /* largest rank used by a Woodbury update; 0 -> K                */
+  double switch_ratio;      /* Algorithm 2 uses Woodbury when k_est / K <= switch_ratio     */
+  int reinverse_period;     /* direct re-inversion when t % period == 0 (t > 0); 0 = never   */
+  unsigned long long seed;  /* key of the Philox-4x32-10 stream that draws Omega            */
+  double dg_floor_rel;      /* skip the update (keep X) when ||dG||_F <= this * ||G_t||_F    */
+} wbrzf_rank_rule;
+
+/* Per-instance outcome of the last call (wbrzf_step_info_get). */
+typedef struct {
+  int32_t branch;           /* WBRZF_BRANCH_*                                                */
+  int32_t r;                /* k_est of Algorithm 1 (0 when no low-rank step ran)            */
+  int32_t iters;            /* Algorithm 1 iterations used                                   */
+  int32_t d;                /* sketch width of the last iteration                            */
+  float dg_fro2;            /* ||dG||_F^2                                                    */
+  float scale;              /* power-normalisation scale s                                   */
+  float sum_rate;           /* R_sum of eq. 15 [bit/s/Hz]                                    */
+  int32_t status;           /* WBRZF_STATUS_* bits                                           */
+} wbrzf_step_info;
+
+/* Bytes of device workspace a handle with these sizes needs (0 on invalid sizes). */
+size_t wbrzf_workspace_bytes(int batch, int N, int K, wbrzf_precision prec,
+                             const wbrzf_rank_rule* rule);
+
+/*
+ * Create a handle for `batch` instances of size K x N (1 <= K <= 64, N >= 1).
+ *   alpha[batch], sigma2[batch]: host arrays, regulariser alpha >= 0 and noise variance
+ *       sigma_n^2 > 0 per instance (copied; the caller may free them on return).
+ *   p_t: total transmit power P_t > 0 (eq. 5 power constraint).
+ *   rule: Algorithm 1 / 2 parameters (copied); ignored fields for WBRZF_METHOD_FULL_INVERSE.
+ *   workspace / workspace_bytes: see the conventions above; the contents need no
+ *       initialisation.
+ *   cuda_stream: cudaStream_t the handle enqueues on (NULL = legacy default stream).
+ * Synchronises the stream once (parameter upload).  On success *out is the new handle.
+ */
+wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const double* sigma2,
+                          double p_t, const wbrzf_rank_rule* rule, wbrzf_method method,
+                          wbrzf_precision prec, void* workspace, size_t workspace_bytes,
+                          void* cuda_stream, wbrzf** out);
+
+/*
+ * Snapshot t = 0 of every instance (Algorithm 2, else-branch): G_0 = H_0 H_0^H + alpha I,
+ * X = G_0^{-1} directly, W_out = s H_0^H X, SINR and sum-rate.  Resets the snapshot counter
+ * (the Philox step index) to 0; the next wbrzf_update is snapshot t = 1.
+ */
+wbrzf_status wbrzf_full_inverse(wbrzf* h, const void* H_t, void* W_out);
+
+/*
+ * Snapshot t of every instance: the whole per-snapshot path described at the top (WB-arSVD
+ * method), or a direct inverse for WBRZF_METHOD_FULL_INVERSE.  W_out receives the normalised
+ * precoders.  Returns WBRZF_ERR_NOT_INITIALIZED for the WB method before wbrzf_full_inverse.
+ */
+wbrzf_status wbrzf_update(wbrzf* h, const void* H_t, void* W_out);
+
+/*
+ * Copy the last call's per-user SINR (device float[batch*K], may be NULL) and per-instance
+ * sum-rate R_sum (device float[batch], may be NULL) into caller buffers, on the stream.
+ */
+wbrzf_status wbrzf_sum_rate(wbrzf* h, float* sinr_out, float* sum_rate_out);
+
+/* Copy the last call's per-instance outcome for instances [0, count) into host memory.
+ * Synchronises the stream.  Returns WBRZF_ERR_NUMERICAL if any of them has status != 0. */
+wbrzf_status wbrzf_step_info_get(wbrzf* h, wbrzf_step_info* host_out, int count);
+
+/* Copy the resident state (device, batch contiguous K x K row-major, the handle's complex
+ * type): G of the last snapshot and X = its inverse as maintained by the method.  Either
+ * pointer may be NULL.  Asynchronous on the stream. */
+wbrzf_status wbrzf_get_state(wbrzf* h, void* G_out, void* X_out);
+
+/*
+ * Optional trace of the low-rank step for testing: when `trace` is non-NULL (device memory
+ * of at least wbrzf_trace_bytes() bytes, owned by the caller), each later call writes per
+ * instance the squared singular values of B (descending), the factors L = U_r (K x r_max)
+ * and R^H = Sigma_r V_r^H (r_max x K, so dG ~= L R^H), in the handle's real/complex type.
+ * NULL switches tracing off.
+ */
+size_t wbrzf_trace_bytes(const wbrzf* h);
+wbrzf_status wbrzf_set_trace(wbrzf* h, void* trace, size_t bytes);
+
+/* Set the instance identities (host array of `count` <= batch entries, each < 2^28): instance
+ * b draws Algorithm 1's test matrices from Philox counters keyed by ids[b], so its results do
+ * not depend on its position in a batch.  Default: ids[b] = b.  Synchronises the stream. */
+wbrzf_status wbrzf_set_instance_ids(wbrzf* h, const uint32_t* ids, int count);
+
+/* Rebind the handle to another stream (cudaStream_t; NULL = legacy default stream). */
+wbrzf_status wbrzf_set_stream(wbrzf* h, void* cuda_stream);
+
+/* Kernel launches issued by this handle so far. */
+long long wbrzf_launch_count(const wbrzf* h);
+
+/* Release the handle (host memory only; the workspace stays the caller's). NULL is a no-op. */
+void wbrzf_destroy(wbrzf* h);
+
+/* Static description of a status code; the last CUDA error string seen by any handle. */
+const char* wbrzf_status_string(wbrzf_status s);
+const char* wbrzf_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WBRZF_H */

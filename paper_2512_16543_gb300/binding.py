@@ -1,0 +1,277 @@
+"""ctypes binding of libwbrzf.so (the C ABI in include/wbrzf.h).
+
+Argument marshalling only: torch tensors supply device memory and the CUDA stream; every
+step of the precoder update runs in the library's kernels.  There is no fallback path: if
+the shared library is missing or cannot be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libwbrzf.so")
+_lib = None
+
+# enums of wbrzf.h
+C128, C64 = 0, 1
+WB_ARSVD, FULL_INVERSE = 0, 1
+BRANCH_NAMES = {0: "keep", 1: "woodbury", 2: "init", 3: "periodic", 4: "rank", 5: "full",
+                6: "fallback"}
+STATUS = {0: "ok", 1: "invalid argument", 2: "not initialized", 3: "workspace too small",
+          4: "numerical", 5: "cuda error", 6: "unsupported"}
+
+
+class WbrzfError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        super().__init__(f"{where}: {STATUS.get(code, code)}" + (f" ({detail})" if detail else ""))
+        self.code = code
+
+
+class RankRuleC(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("k_init", ctypes.c_int), ("p", ctypes.c_int),
+                ("i_max", ctypes.c_int), ("r_max", ctypes.c_int),
+                ("switch_ratio", ctypes.c_double), ("reinverse_period", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong), ("dg_floor_rel", ctypes.c_double)]
+
+
+class StepInfoC(ctypes.Structure):
+    _fields_ = [("branch", ctypes.c_int32), ("r", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("d", ctypes.c_int32), ("dg_fro2", ctypes.c_float), ("scale", ctypes.c_float),
+                ("sum_rate", ctypes.c_float), ("status", ctypes.c_int32)]
+
+
+@dataclass
+class RankRule:
+    """Algorithm 1 / 2 parameters (mirrors wbrzf_rank_rule)."""
+
+    eta: float = 0.9
+    k_init: int = 2
+    p: int = 1
+    i_max: int = 0
+    r_max: int = 0
+    switch_ratio: float = 0.5
+    reinverse_period: int = 20
+    seed: int = 0
+    dg_floor_rel: float = 0.0
+
+    def to_c(self) -> RankRuleC:
+        return RankRuleC(self.eta, self.k_init, self.p, self.i_max, self.r_max,
+                         self.switch_ratio, self.reinverse_period, self.seed, self.dg_floor_rel)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load libwbrzf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with "
+                           "`python -m paper_2512_16543_gb300.build` (no fallback path exists)")
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, sz, i32, dbl = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_double
+    L.wbrzf_workspace_bytes.restype = sz
+    L.wbrzf_workspace_bytes.argtypes = [i32, i32, i32, i32, ctypes.POINTER(RankRuleC)]
+    L.wbrzf_create.restype = i32
+    L.wbrzf_create.argtypes = [i32, i32, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl), dbl,
+                               ctypes.POINTER(RankRuleC), i32, i32, vp, sz, vp,
+                               ctypes.POINTER(vp)]
+    for name in ("wbrzf_full_inverse", "wbrzf_update"):
+        f = getattr(L, name)
+        f.restype = i32
+        f.argtypes = [vp, vp, vp]
+    L.wbrzf_sum_rate.restype = i32
+    L.wbrzf_sum_rate.argtypes = [vp, vp, vp]
+    L.wbrzf_step_info_get.restype = i32
+    L.wbrzf_step_info_get.argtypes = [vp, ctypes.POINTER(StepInfoC), i32]
+    L.wbrzf_get_state.restype = i32
+    L.wbrzf_get_state.argtypes = [vp, vp, vp]
+    L.wbrzf_trace_bytes.restype = sz
+    L.wbrzf_trace_bytes.argtypes = [vp]
+    L.wbrzf_set_trace.restype = i32
+    L.wbrzf_set_trace.argtypes = [vp, vp, sz]
+    L.wbrzf_set_instance_ids.restype = i32
+    L.wbrzf_set_instance_ids.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), i32]
+    L.wbrzf_set_stream.restype = i32
+    L.wbrzf_set_stream.argtypes = [vp, vp]
+    L.wbrzf_launch_count.restype = ctypes.c_longlong
+    L.wbrzf_launch_count.argtypes = [vp]
+    L.wbrzf_destroy.restype = None
+    L.wbrzf_destroy.argtypes = [vp]
+    L.wbrzf_status_string.restype = ctypes.c_char_p
+    L.wbrzf_status_string.argtypes = [i32]
+    L.wbrzf_last_cuda_error.restype = ctypes.c_char_p
+    L.wbrzf_last_cuda_error.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(code: int, where: str) -> None:
+    if code != 0:
+        detail = lib().wbrzf_last_cuda_error().decode() if code == 5 else ""
+        raise WbrzfError(code, where, detail)
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+class WBRZF:
+    """One handle over `batch` independent K x N instances (see include/wbrzf.h).
+
+    H tensors: complex, shape [batch, K, N] (or [K, N] when batch == 1), contiguous, on the
+    handle's device.  W tensors: shape [batch, N, K].
+    """
+
+    def __init__(self, batch: int, N: int, K: int, alpha, sigma2, *, p_t: float = 1.0,
+                 rule: RankRule | None = None, method: str = "wb", precision: str = "c64",
+                 device="cuda", stream: torch.cuda.Stream | None = None):
+        L = lib()
+        self.batch, self.N, self.K = int(batch), int(N), int(K)
+        self.prec = {"c64": C64, "c128": C128}[precision]
+        self.method = {"wb": WB_ARSVD, "full": FULL_INVERSE}[method]
+        self.dtype = torch.complex64 if self.prec == C64 else torch.complex128
+        self.rdtype = torch.float32 if self.prec == C64 else torch.float64
+        self.device = torch.device(device)
+        self.rule = rule or RankRule()
+        self._rule_c = self.rule.to_c()
+        a = [float(x) for x in (alpha if hasattr(alpha, "__len__") else [alpha] * self.batch)]
+        s = [float(x) for x in (sigma2 if hasattr(sigma2, "__len__") else [sigma2] * self.batch)]
+        if len(a) != self.batch or len(s) != self.batch:
+            raise ValueError("alpha / sigma2 need one entry per instance")
+        nbytes = L.wbrzf_workspace_bytes(self.batch, self.N, self.K, self.prec,
+                                         ctypes.byref(self._rule_c))
+        if nbytes == 0:
+            raise WbrzfError(1, "wbrzf_workspace_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        with torch.cuda.device(self.device):
+            self.stream = stream or torch.cuda.current_stream(self.device)
+        arr = ctypes.c_double * self.batch
+        h = ctypes.c_void_p()
+        _check(L.wbrzf_create(self.batch, self.N, self.K, arr(*a), arr(*s), float(p_t),
+                              ctypes.byref(self._rule_c), self.method, self.prec,
+                              _ptr(self.workspace), nbytes, self.stream.cuda_stream,
+                              ctypes.byref(h)), "wbrzf_create")
+        self._h = h
+        self._trace = None
+
+    # ------------------------------------------------------------------ helpers
+    def _in(self, H: torch.Tensor) -> torch.Tensor:
+        if H.dtype != self.dtype or H.device != self.device or not H.is_contiguous():
+            raise ValueError(f"H must be a contiguous {self.dtype} tensor on {self.device}")
+        if H.numel() != self.batch * self.K * self.N:
+            raise ValueError(f"H has {H.numel()} elements, expected {self.batch}x{self.K}x{self.N}")
+        return H
+
+    def _out(self, W: torch.Tensor | None) -> torch.Tensor:
+        if W is None:
+            return torch.empty(self.batch, self.N, self.K, dtype=self.dtype, device=self.device)
+        if W.dtype != self.dtype or W.device != self.device or not W.is_contiguous() or \
+                W.numel() != self.batch * self.N * self.K:
+            raise ValueError("W_out has the wrong dtype, device, layout or size")
+        return W
+
+    # ------------------------------------------------------------------ API
+    def full_inverse(self, H: torch.Tensor, W: torch.Tensor | None = None) -> torch.Tensor:
+        W = self._out(W)
+        _check(lib().wbrzf_full_inverse(self._h, _ptr(self._in(H)), _ptr(W)), "wbrzf_full_inverse")
+        return W
+
+    def update(self, H: torch.Tensor, W: torch.Tensor | None = None) -> torch.Tensor:
+        W = self._out(W)
+        _check(lib().wbrzf_update(self._h, _ptr(self._in(H)), _ptr(W)), "wbrzf_update")
+        return W
+
+    def sum_rate(self) -> tuple[torch.Tensor, torch.Tensor]:
+        sinr = torch.empty(self.batch, self.K, dtype=torch.float32, device=self.device)
+        rate = torch.empty(self.batch, dtype=torch.float32, device=self.device)
+        _check(lib().wbrzf_sum_rate(self._h, _ptr(sinr), _ptr(rate)), "wbrzf_sum_rate")
+        return sinr, rate
+
+    def step_info(self, raise_on_numerical: bool = False) -> list[dict]:
+        arr = (StepInfoC * self.batch)()
+        code = lib().wbrzf_step_info_get(self._h, arr, self.batch)
+        if code not in (0, 4) or (code == 4 and raise_on_numerical):
+            _check(code, "wbrzf_step_info_get")
+        return [{f: getattr(x, f) for f, _ in StepInfoC._fields_} for x in arr]
+
+    def state(self) -> tuple[torch.Tensor, torch.Tensor]:
+        G = torch.empty(self.batch, self.K, self.K, dtype=self.dtype, device=self.device)
+        X = torch.empty_like(G)
+        _check(lib().wbrzf_get_state(self._h, _ptr(G), _ptr(X)), "wbrzf_get_state")
+        return G, X
+
+    def enable_trace(self, on: bool = True) -> None:
+        if not on:
+            _check(lib().wbrzf_set_trace(self._h, None, 0), "wbrzf_set_trace")
+            self._trace = None
+            return
+        n = lib().wbrzf_trace_bytes(self._h)
+        self._trace = torch.zeros(n, dtype=torch.uint8, device=self.device)
+        _check(lib().wbrzf_set_trace(self._h, _ptr(self._trace), n), "wbrzf_set_trace")
+
+    def trace(self, dmax: int, rcap: int):
+        """Split the trace buffer: (sigma_hat^2 [batch, dmax], L [batch, K, rcap],
+        R^H [batch, rcap, K]) for the last call's Woodbury instances."""
+        if self._trace is None:
+            raise RuntimeError("tracing is off")
+        rb = 4 if self.prec == C64 else 8
+        cb = 2 * rb
+        a16 = lambda x: (x + 15) // 16 * 16
+        rec = a16(dmax * rb) + a16(2 * self.K * rcap * cb)
+        raw = self._trace.view(self.batch, rec)
+        sig = raw[:, :dmax * rb].contiguous().view(self.rdtype)
+        fac = raw[:, a16(dmax * rb):a16(dmax * rb) + 2 * self.K * rcap * cb].contiguous()
+        fac = fac.view(self.dtype).view(self.batch, 2, self.K * rcap)
+        Lm = fac[:, 0].reshape(self.batch, self.K, rcap)
+        Rh = fac[:, 1].reshape(self.batch, rcap, self.K)
+        return sig, Lm, Rh
+
+    def set_instance_ids(self, ids) -> None:
+        ids = [int(x) for x in ids]
+        arr = (ctypes.c_uint32 * len(ids))(*ids)
+        _check(lib().wbrzf_set_instance_ids(self._h, arr, len(ids)), "wbrzf_set_instance_ids")
+
+    def set_stream(self, stream: torch.cuda.Stream) -> None:
+        self.stream = stream
+        _check(lib().wbrzf_set_stream(self._h, stream.cuda_stream), "wbrzf_set_stream")
+
+    @property
+    def launches(self) -> int:
+        return int(lib().wbrzf_launch_count(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().wbrzf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def resolved_sizes(K: int, rule: RankRule) -> tuple[int, int, int, int]:
+    """(r_max, i_max, dmax, rcap) as the library resolves them (for reading traces)."""
+    r_max = rule.r_max if 0 < rule.r_max < K else K
+    if rule.i_max > 0:
+        i_max = rule.i_max
+    else:
+        e, k = 0, rule.k_init
+        while k < r_max:
+            k *= 2
+            e += 1
+        i_max = e + 1
+    k0, dmax = rule.k_init, 1
+    for _ in range(i_max):
+        dmax = max(dmax, min(k0 + rule.p, K))
+        if k0 < K:
+            k0 *= 2
+    return r_max, i_max, dmax, min(r_max, dmax)

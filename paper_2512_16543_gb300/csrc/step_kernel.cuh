@@ -1,0 +1,699 @@
+// Fused per-snapshot kernel of the WB-arSVD RZF precoder update.
+//
+// One CTA of kThreads threads owns one instance for the whole snapshot; every step of the
+// path runs here, in this order:
+//   1. Gram      G_t = H_t H_t^H + alpha I                       (Section II eq. 5)
+//   2. dG        dG = G_t - G_{t-1}, ||dG||_F^2                   (Section III eqs. 7-9)
+//   3. arSVD     Omega (Philox), Y = dG Omega, Q = CholQR2(Y), B = Q^H dG, eigen-
+//                decomposition of B B^H (= U_hat Sigma_hat^2 U_hat^H, i.e. the left factor
+//                and singular values of svd(B)), energy rule, k0 doubling (Algorithm 1, eq. 14)
+//   4. branch    Woodbury vs direct inverse (Algorithm 2)
+//   5. Woodbury  L = Q U_r, R^H = U_r^H B (= Sigma_r V_r^H), T = X L, Z = R^H X,
+//                C = I + Z L, X <- X - T C^{-1} Z                  (Section III eq. 12)
+//      or direct inverse of G_t (in-place Gauss-Jordan exchange steps)
+//   6. scale and SINR: M = (G_t - alpha I) X = H_t H_t^H X, ||W||_F^2 = Re tr(X^H M),
+//                s = sqrt(P_t)/||W||_F, SINR_n from s M            (Section II, Section VI eq. 15)
+//   7. precoder  W = s H_t^H X                                      (Section II eq. 5)
+// H_t is streamed through shared memory twice (Gram, then precoder) in chunks of kChunk
+// antenna columns with cp.async double buffering; the second pass is served mostly by L2.
+#pragma once
+#include <math.h>
+
+#include "step_common.cuh"
+
+namespace wbk {
+
+// ------------------------------------------------------------------ complex helpers
+template <class T> __device__ __forceinline__ cx<T> cmk(T r, T i) { cx<T> z; z.re = r; z.im = i; return z; }
+template <class T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return cmk(a.re + b.re, a.im + b.im); }
+template <class T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return cmk(a.re - b.re, a.im - b.im); }
+template <class T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return cmk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class T> __device__ __forceinline__ cx<T> cconj(cx<T> a) { return cmk(a.re, -a.im); }
+template <class T> __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return cmk(a.re * s, a.im * s); }
+template <class T> __device__ __forceinline__ T cabs2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+// acc += a * b
+template <class T> __device__ __forceinline__ void cfma(cx<T>& acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re); acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im); acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += a * conj(b)
+template <class T> __device__ __forceinline__ void cfma_cj(cx<T>& acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re); acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.im, b.re, acc.im); acc.im = fma(-a.re, b.im, acc.im);
+}
+// acc += conj(a) * b
+template <class T> __device__ __forceinline__ void cfma_jc(cx<T>& acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re); acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im); acc.im = fma(-a.im, b.re, acc.im);
+}
+template <class T> __device__ __forceinline__ cx<T> crecip(cx<T> a) {
+  T n = a.re * a.re + a.im * a.im;
+  return cmk(a.re / n, -a.im / n);
+}
+template <class T> __device__ __forceinline__ bool cfinite(cx<T> a) { return isfinite(a.re) && isfinite(a.im); }
+
+// ------------------------------------------------------------------ Philox-4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11: multipliers 0xD2511F53 / 0xCD9E8D57, Weyl increments
+// 0x9E3779B9 / 0xBB67AE85, 10 rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+// u = ((x >> 9) + 0.5) 2^-23 (exact in binary32 and binary64); omega = sqrt(-ln u_a) e^{j 2 pi u_b}
+__device__ __forceinline__ cx<float> box_muller(uint32_t xa, uint32_t xb, float) {
+  const float ua = (__uint2float_rn(xa >> 9) + 0.5f) * 1.1920928955078125e-7f;
+  const float ub = (__uint2float_rn(xb >> 9) + 0.5f) * 1.1920928955078125e-7f;
+  const float rad = sqrtf(-logf(ua));
+  float sn, cs;
+  sincospif(2.0f * ub, &sn, &cs);
+  return cmk(rad * cs, rad * sn);
+}
+__device__ __forceinline__ cx<double> box_muller(uint32_t xa, uint32_t xb, double) {
+  const double ua = ((double)(xa >> 9) + 0.5) * 1.1920928955078125e-7;
+  const double ub = ((double)(xb >> 9) + 0.5) * 1.1920928955078125e-7;
+  const double rad = sqrt(-log(ua));
+  double sn, cs;
+  sincospi(2.0 * ub, &sn, &cs);
+  return cmk(rad * cs, rad * sn);
+}
+
+// ------------------------------------------------------------------ cp.async
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (BYTES == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// ------------------------------------------------------------------ block reductions
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// Sum over the CTA; every thread gets the result.  red: >= 33 slots.
+template <class T>
+__device__ T block_sum(T v, T* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    T r = (l < kThreads / 32) ? red[l] : T(0);
+    r = warp_sum(r);
+    if (l == 0) red[32] = r;
+  }
+  __syncthreads();
+  const T out = red[32];
+  __syncthreads();
+  return out;
+}
+
+// ------------------------------------------------------------------ H chunk staging
+// Stage columns [n0, n0 + nc) of H (row-major K x N) transposed into buf[n][k] (row stride KP).
+template <class T>
+__device__ __forceinline__ void stage_chunk(const cx<T>* __restrict__ Hb, int K, int N, int n0,
+                                            int nc, cx<T>* buf, int KP) {
+  for (int e = threadIdx.x; e < K * kChunk; e += kThreads) {
+    const int k = e / kChunk, n = e - k * kChunk;
+    if (n < nc) cp_async<sizeof(cx<T>)>(&buf[n * KP + k], &Hb[(size_t)k * N + n0 + n]);
+  }
+  cp_async_commit();
+}
+
+// ------------------------------------------------------------------ small dense products
+// C[m x n] (ldc) (op)= sum_k A(i,k) B(k,j); A(i,k) = AH ? conj(A[k*lda+i]) : A[i*lda+k],
+// B(k,j) = BH ? conj(B[j*ldb+k]) : B[k*ldb+j].  Each thread owns whole outputs.
+enum MMStore { MM_SET = 0, MM_SUB = 1 };
+template <class T, bool AH, bool BH, int STORE>
+__device__ void mm(int m, int n, int kk, const cx<T>* A, int lda, const cx<T>* B, int ldb,
+                   cx<T>* C, int ldc) {
+  for (int idx = threadIdx.x; idx < m * n; idx += kThreads) {
+    const int i = idx / n, j = idx - i * n;
+    cx<T> acc = cmk<T>(0, 0);
+    for (int k = 0; k < kk; ++k) {
+      cx<T> a = AH ? cconj(A[k * lda + i]) : A[i * lda + k];
+      cx<T> b = BH ? cconj(B[j * ldb + k]) : B[k * ldb + j];
+      cfma(acc, a, b);
+    }
+    if (STORE == MM_SET) C[i * ldc + j] = acc;
+    else C[i * ldc + j] = csub(C[i * ldc + j], acc);
+  }
+}
+
+// ------------------------------------------------------------------ the kernel
+template <class T>
+__global__ void __launch_bounds__(kThreads) wbrzf_step_kernel(const StepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int K = a.K, N = a.N, KK = K * K;
+  const Layout Ly = make_layout(K, a.dmax, a.rcap, sizeof(cx<T>), sizeof(T));
+  cx<T>* const smc = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* const G = smc + Ly.oG;
+  cx<T>* const X = smc + Ly.oX;
+  cx<T>* const D = smc + Ly.oD;
+  cx<T>* const Hbuf0 = smc + Ly.oH0;
+  cx<T>* const Hbuf1 = smc + Ly.oH1;
+  cx<T>* const Om = smc + Ly.oOm;   // later L
+  cx<T>* const Q = smc + Ly.oQ;
+  cx<T>* const Gy = smc + Ly.oGy;   // Y^H Y, then B B^H (eigen workspace)
+  cx<T>* const Bm = smc + Ly.oB;
+  cx<T>* const Uh = smc + Ly.oUh;
+  cx<T>* const Rh = smc + Ly.oRh;
+  cx<T>* const Tm = smc + Ly.oT;
+  cx<T>* const CZ = smc + Ly.oCZ;
+  cx<T>* const tmp = smc + Ly.oTmp;
+  const int dmax = a.dmax, rcap = a.rcap, KP = Ly.KP;
+  T* const red = reinterpret_cast<T*>(smem_raw + Ly.oRealBytes);       // 40 slots
+  T* const lam = red + 40;                                              // dmax
+  T* const rc = lam + dmax;                                             // dmax (cos)
+  T* const rs = rc + dmax;                                              // dmax (sin)
+  T* const cn = rs + dmax;                                              // dmax (column norms)
+  int* const ibase = reinterpret_cast<int*>(
+      smem_raw + Ly.oRealBytes + align_up((40 + 4 * (size_t)dmax) * sizeof(T), 16));
+  int* const perm = ibase;
+  int* const pp = perm + dmax;
+  int* const pq = pp + dmax;
+  int* const drop = pq + dmax;
+  int* const misc = drop + dmax;                                        // 16
+  cx<T>* const rph = reinterpret_cast<cx<T>*>(
+      reinterpret_cast<unsigned char*>(ibase) + align_up((4 * (size_t)dmax + 16) * sizeof(int), 16));
+
+  const uint32_t inst_id = a.ids[b];
+  const T alpha = a.alpha[b];
+  const T sigma2 = a.sigma2[b];
+  const cx<T>* __restrict__ Hb = a.H + (size_t)b * K * N;
+  const int nchunks = (N + kChunk - 1) / kChunk;
+  int status = WBRZF_STATUS_OK;
+
+  // ---------------------------------------------------------------- 1. Gram matrix
+  constexpr int QMAX = (kMaxK * kMaxK + kThreads - 1) / kThreads;
+  {
+    cx<T> acc[QMAX];
+    int kq[QMAX], lq[QMAX];
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+      acc[q] = cmk<T>(0, 0);
+      const int idx = tid + q * kThreads;
+      kq[q] = (idx < KK) ? idx / K : -1;
+      lq[q] = (idx < KK) ? idx - (idx / K) * K : 0;
+    }
+    stage_chunk(Hb, K, N, 0, min(kChunk, N), Hbuf0, KP);
+    for (int c = 0; c < nchunks; ++c) {
+      if (c + 1 < nchunks) {
+        const int n1 = (c + 1) * kChunk;
+        stage_chunk(Hb, K, N, n1, min(kChunk, N - n1), (c & 1) ? Hbuf0 : Hbuf1, KP);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const cx<T>* hb = (c & 1) ? Hbuf1 : Hbuf0;
+      const int nc = min(kChunk, N - c * kChunk);
+      for (int n = 0; n < nc; ++n) {
+        const cx<T>* row = hb + n * KP;
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+          if (kq[q] >= 0) cfma_cj(acc[q], row[kq[q]], row[lq[q]]);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+      const int idx = tid + q * kThreads;
+      if (idx < KK) G[idx] = acc[q];
+    }
+    __syncthreads();
+    // exact Hermitian symmetry and the regulariser: upper triangle wins
+    for (int idx = tid; idx < KK; idx += kThreads) {
+      const int k = idx / K, l = idx - k * K;
+      if (k > l) G[idx] = cconj(G[l * K + k]);
+    }
+    __syncthreads();
+    if (tid < K) G[tid * K + tid] = cmk<T>(G[tid * K + tid].re + alpha, T(0));
+    __syncthreads();
+  }
+
+  // ---------------------------------------------------------------- 2. perturbation, state
+  cx<T>* const Gsb = a.Gs + (size_t)b * KK;
+  cx<T>* const Xsb = a.Xs + (size_t)b * KK;
+  int branch;
+  double dg2 = 0.0;
+  if (a.mode == MODE_UPDATE) {
+    T s_dg = 0, s_g = 0;
+    for (int idx = tid; idx < KK; idx += kThreads) {
+      const cx<T> g = G[idx];
+      const cx<T> d = csub(g, Gsb[idx]);
+      D[idx] = d;
+      X[idx] = Xsb[idx];
+      Gsb[idx] = g;
+      s_dg += cabs2(d);
+      s_g += cabs2(g);
+    }
+    const T dgs = block_sum(s_dg, red);
+    const T gs = block_sum(s_g, red);
+    dg2 = (double)dgs;
+    if (a.period > 0 && (a.t % a.period) == 0) branch = WBRZF_BRANCH_PERIODIC;
+    else if (sqrt(dg2) <= a.dg_floor_rel * sqrt((double)gs)) branch = WBRZF_BRANCH_KEEP;
+    else branch = -1;   // decided by the low-rank step
+  } else {
+    if (a.mode == MODE_INIT) {
+      for (int idx = tid; idx < KK; idx += kThreads) Gsb[idx] = G[idx];
+    }
+    branch = (a.mode == MODE_INIT) ? WBRZF_BRANCH_INIT : WBRZF_BRANCH_FULL;
+  }
+
+  // ---------------------------------------------------------------- 3. arSVD (Algorithm 1)
+  int r = 0, iters = 0, d = 0;
+  if (branch == -1) {
+    const double E_target = a.eta * dg2;
+    int k0 = a.k_init;
+    bool met = false;
+    for (int it = 0; it < a.i_max; ++it) {
+      d = min(k0 + a.p, K);
+      // 3a. Omega: entry (i, j) from counter (i, j/2, t, 16 b + it)
+      {
+        const int nq = (d + 1) >> 1;
+        for (int e = tid; e < K * nq; e += kThreads) {
+          const int i = e / nq, q = e - i * nq;
+          const uint4 x = philox4x32_10(
+              make_uint4((uint32_t)i, (uint32_t)q, (uint32_t)a.t, 16u * inst_id + (uint32_t)it),
+              a.seed_lo, a.seed_hi);
+          Om[i * dmax + 2 * q] = box_muller(x.x, x.y, T(0));
+          if (2 * q + 1 < d) Om[i * dmax + 2 * q + 1] = box_muller(x.z, x.w, T(0));
+        }
+      }
+      __syncthreads();
+      // 3b. sketch Y = dG Omega (into Q)
+      mm<T, false, false, MM_SET>(K, d, K, D, K, Om, dmax, Q, dmax);
+      __syncthreads();
+      // 3c. Q = orth(Y): CholQR twice, columns that are numerically dependent are dropped
+      if (tid < d) drop[tid] = 0;
+      __syncthreads();
+      const T tol_rel = (sizeof(T) == 4) ? T(1e-4) : T(1e-12);
+      for (int pass = 0; pass < 2; ++pass) {
+        mm<T, true, false, MM_SET>(d, d, K, Q, dmax, Q, dmax, Gy, dmax);   // Y^H Y
+        __syncthreads();
+        if (tid < d) cn[tid] = Gy[tid * dmax + tid].re;
+        __syncthreads();
+        // right-looking Cholesky Gy = R^H R (R upper, stored in the upper triangle)
+        for (int j = 0; j < d; ++j) {
+          if (tid == 0) {
+            const T piv = Gy[j * dmax + j].re;
+            const bool dj = drop[j] || !(cn[j] > T(0)) || !(piv > tol_rel * cn[j]) || !isfinite(piv);
+            drop[j] = dj ? 1 : 0;
+            rc[0] = dj ? T(0) : sqrt(piv);
+          }
+          __syncthreads();
+          const T rjj = rc[0];
+          for (int c = j + tid; c < d; c += kThreads) {
+            Gy[j * dmax + c] = (rjj > T(0)) ? cscale(Gy[j * dmax + c], T(1) / rjj) : cmk<T>(0, 0);
+          }
+          __syncthreads();
+          const int m = d - j - 1;
+          for (int e = tid; e < m * m; e += kThreads) {
+            const int ai = j + 1 + e / m, ci = j + 1 + e % m;
+            if (ai <= ci) {
+              cx<T> v = Gy[ai * dmax + ci];
+              cfma_jc(v, cscale(Gy[j * dmax + ai], T(-1)), Gy[j * dmax + ci]);
+              Gy[ai * dmax + ci] = v;
+            }
+          }
+          __syncthreads();
+        }
+        // Q <- Q R^{-1} row by row (forward substitution on x R = q)
+        for (int i = tid; i < K; i += kThreads) {
+          cx<T>* qi = Q + i * dmax;
+          for (int c = 0; c < d; ++c) {
+            if (drop[c]) { qi[c] = cmk<T>(0, 0); continue; }
+            cx<T> v = qi[c];
+            for (int a2 = 0; a2 < c; ++a2) {
+              if (!drop[a2]) v = csub(v, cmul(qi[a2], Gy[a2 * dmax + c]));
+            }
+            qi[c] = cscale(v, T(1) / Gy[c * dmax + c].re);
+          }
+        }
+        __syncthreads();
+      }
+      // 3d. projection B = Q^H dG  (d x K)
+      mm<T, true, false, MM_SET>(d, K, K, Q, dmax, D, K, Bm, K);
+      __syncthreads();
+      // 3e. E = B B^H (d x d, Hermitian), eigen-decomposition by parallel cyclic Jacobi
+      mm<T, false, true, MM_SET>(d, d, K, Bm, K, Bm, K, Gy, dmax);
+      for (int e = tid; e < d * d; e += kThreads) {
+        const int i = e / d, j = e - i * d;
+        Uh[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
+      }
+      __syncthreads();
+      {
+        const int dd = d + (d & 1);
+        const int npairs = dd >> 1;
+        const int max_sweeps = (sizeof(T) == 4) ? 12 : 20;
+        const T eps = (sizeof(T) == 4) ? T(1e-13) : T(1e-30);
+        for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+          T off = 0, tot = 0;
+          for (int e = tid; e < d * d; e += kThreads) {
+            const int i = e / d, j = e - i * d;
+            const T v = cabs2(Gy[i * dmax + j]);
+            tot += v;
+            if (i != j) off += v;
+          }
+          off = block_sum(off, red);
+          tot = block_sum(tot, red);
+          if (!(off > eps * tot)) break;
+          for (int rnd = 0; rnd < dd - 1; ++rnd) {
+            if (tid < npairs) {
+              // circle-method pairing: x_i = 1 + ((i + rnd) mod (dd - 1)); pairs (0, x_0), (x_k, x_{dd-1-k})
+              int p0, q0;
+              if (tid == 0) { p0 = 0; q0 = 1 + (rnd % (dd - 1)); }
+              else {
+                p0 = 1 + ((tid + rnd) % (dd - 1));
+                q0 = 1 + ((dd - 1 - tid + rnd) % (dd - 1));
+              }
+              const int p1 = min(p0, q0), q1 = max(p0, q0);
+              bool active = q1 < d;
+              T c = 1, s = 0;
+              cx<T> ph = cmk<T>(1, 0);
+              if (active) {
+                const cx<T> bpq = Gy[p1 * dmax + q1];
+                const T ab = sqrt(cabs2(bpq));
+                if (ab > T(0)) {
+                  ph = cmk(bpq.re / ab, -bpq.im / ab);               // e^{-i phi}
+                  const T th = T(0.5) * atan2(T(2) * ab, Gy[q1 * dmax + q1].re - Gy[p1 * dmax + p1].re);
+                  c = cos(th);
+                  s = sin(th);
+                } else {
+                  active = false;
+                }
+              }
+              pp[tid] = active ? p1 : -1;
+              pq[tid] = q1;
+              rc[tid] = c;
+              rs[tid] = s;
+              rph[tid] = ph;
+            }
+            __syncthreads();
+            // columns: col_p <- c col_p - s ph col_q ; col_q <- s col_p + c ph col_q (E and U_hat)
+            for (int e = tid; e < npairs * d; e += kThreads) {
+              const int k = e / d, i = e - k * d;
+              const int p1 = pp[k];
+              if (p1 < 0) continue;
+              const int q1 = pq[k];
+              const T c = rc[k], s = rs[k];
+              const cx<T> ph = rph[k];
+              const cx<T> ep = Gy[i * dmax + p1], eq = cmul(ph, Gy[i * dmax + q1]);
+              Gy[i * dmax + p1] = csub(cscale(ep, c), cscale(eq, s));
+              Gy[i * dmax + q1] = cadd(cscale(ep, s), cscale(eq, c));
+              const cx<T> up = Uh[i * dmax + p1], uq = cmul(ph, Uh[i * dmax + q1]);
+              Uh[i * dmax + p1] = csub(cscale(up, c), cscale(uq, s));
+              Uh[i * dmax + q1] = cadd(cscale(up, s), cscale(uq, c));
+            }
+            __syncthreads();
+            // rows: row_p <- c row_p - s conj(ph) row_q ; row_q <- s row_p + c conj(ph) row_q
+            for (int e = tid; e < npairs * d; e += kThreads) {
+              const int k = e / d, j = e - k * d;
+              const int p1 = pp[k];
+              if (p1 < 0) continue;
+              const int q1 = pq[k];
+              const T c = rc[k], s = rs[k];
+              const cx<T> phc = cconj(rph[k]);
+              const cx<T> ep = Gy[p1 * dmax + j], eq = cmul(phc, Gy[q1 * dmax + j]);
+              Gy[p1 * dmax + j] = csub(cscale(ep, c), cscale(eq, s));
+              Gy[q1 * dmax + j] = cadd(cscale(ep, s), cscale(eq, c));
+            }
+            __syncthreads();
+          }
+        }
+      }
+      // 3f. sigma_hat^2 (eigenvalues, clamped at 0) sorted descending
+      if (tid < d) lam[tid] = fmax(Gy[tid * dmax + tid].re, T(0));
+      __syncthreads();
+      if (tid < d) {
+        const T v = lam[tid];
+        int rk = 0;
+        for (int i = 0; i < d; ++i) rk += (lam[i] > v || (lam[i] == v && i < tid)) ? 1 : 0;
+        perm[rk] = tid;
+      }
+      __syncthreads();
+      // 3g. energy rule: smallest r with sum_{j <= r} sigma_j^2 >= eta ||dG||_F^2
+      if (tid == 0) {
+        double cum = 0.0;
+        int rf = 0;
+        for (int j = 0; j < d; ++j) {
+          cum += (double)lam[perm[j]];
+          if (cum >= E_target) { rf = j + 1; break; }
+        }
+        misc[0] = rf;
+      }
+      __syncthreads();
+      iters = it + 1;
+      if (misc[0] > 0) { r = misc[0]; met = true; break; }
+      k0 *= 2;
+    }
+    if (!met) r = d;    // fall-through: all d components of the last iteration
+    branch = (r > a.r_max || (double)r / (double)K > a.switch_ratio) ? WBRZF_BRANCH_RANK
+                                                                       : WBRZF_BRANCH_WOODBURY;
+    if (a.trace != nullptr) {
+      T* tr = reinterpret_cast<T*>(a.trace + (size_t)b * a.trace_stride);
+      for (int j = tid; j < dmax; j += kThreads) tr[j] = (j < d) ? lam[perm[j]] : T(0);
+    }
+  }
+
+  // ---------------------------------------------------------------- 5a. Woodbury (eq. 12)
+  if (branch == WBRZF_BRANCH_WOODBURY) {
+    cx<T>* const Lm = Om;   // K x r, ld rcap
+    // L = Q U_r (columns perm[0..r)), R^H = U_r^H B
+    for (int idx = tid; idx < K * r; idx += kThreads) {
+      const int i = idx / r, c = idx - i * r;
+      const int pc = perm[c];
+      cx<T> acc = cmk<T>(0, 0);
+      for (int k = 0; k < d; ++k) cfma(acc, Q[i * dmax + k], Uh[k * dmax + pc]);
+      Lm[i * rcap + c] = acc;
+    }
+    for (int idx = tid; idx < r * K; idx += kThreads) {
+      const int c = idx / K, j = idx - c * K;
+      const int pc = perm[c];
+      cx<T> acc = cmk<T>(0, 0);
+      for (int k = 0; k < d; ++k) cfma_jc(acc, Uh[k * dmax + pc], Bm[k * K + j]);
+      Rh[c * K + j] = acc;
+    }
+    __syncthreads();
+    if (a.trace != nullptr) {
+      cx<T>* trl = reinterpret_cast<cx<T>*>(a.trace + (size_t)b * a.trace_stride +
+                                            align_up((size_t)dmax * sizeof(T), 16));
+      for (int idx = tid; idx < K * rcap; idx += kThreads) {
+        const int i = idx / rcap, c = idx - i * rcap;
+        trl[idx] = (c < r) ? Lm[i * rcap + c] : cmk<T>(0, 0);
+      }
+      for (int idx = tid; idx < rcap * K; idx += kThreads) {
+        const int c = idx / K;
+        trl[K * rcap + idx] = (c < r) ? Rh[idx] : cmk<T>(0, 0);
+      }
+    }
+    // T = X L (K x r), Z = R^H X (r x K) stored at CZ[:, rcap:]
+    const int ldcz = rcap + K;
+    mm<T, false, false, MM_SET>(K, r, K, X, K, Lm, rcap, Tm, rcap);
+    mm<T, false, false, MM_SET>(r, K, K, Rh, K, X, K, CZ + rcap, ldcz);
+    __syncthreads();
+    // C = I + Z L (r x r) at CZ[:, :r]
+    for (int idx = tid; idx < r * r; idx += kThreads) {
+      const int c = idx / r, e = idx - c * r;
+      cx<T> acc = cmk<T>(c == e ? T(1) : T(0), T(0));
+      for (int k = 0; k < K; ++k) cfma(acc, CZ[c * ldcz + rcap + k], Lm[k * rcap + e]);
+      CZ[c * ldcz + e] = acc;
+    }
+    __syncthreads();
+    // Gauss-Jordan with partial pivoting on [C | Z] -> [I | C^{-1} Z]
+    T cmax = 0;
+    for (int idx = tid; idx < r * r; idx += kThreads) {
+      const int c = idx / r, e = idx - c * r;
+      cmax = fmax(cmax, sqrt(cabs2(CZ[c * ldcz + e])));
+    }
+    {
+      // block max via sum of a one-hot trick is awkward; use shared slot with atomic-free pass
+      for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+      if ((tid & 31) == 0) red[tid >> 5] = cmax;
+      __syncthreads();
+      if (tid == 0) {
+        T m = 0;
+        for (int w = 0; w < kThreads / 32; ++w) m = fmax(m, red[w]);
+        red[33] = m;
+        misc[1] = 0;
+      }
+      __syncthreads();
+      cmax = red[33];
+    }
+    const T piv_tol = cmax * ((sizeof(T) == 4) ? T(1e-6) : T(1e-14));
+    for (int c = 0; c < r; ++c) {
+      if (tid == 0) {
+        int pr = c;
+        T best = -1;
+        for (int i = c; i < r; ++i) {
+          const T v = cabs2(CZ[i * ldcz + c]);
+          if (v > best) { best = v; pr = i; }
+        }
+        misc[2] = pr;
+        if (!(sqrt(best) > piv_tol) || !isfinite(best)) misc[1] = 1;
+      }
+      __syncthreads();
+      const int pr = misc[2];
+      if (pr != c) {
+        for (int j = tid; j < ldcz; j += kThreads) {
+          const cx<T> t0 = CZ[c * ldcz + j];
+          CZ[c * ldcz + j] = CZ[pr * ldcz + j];
+          CZ[pr * ldcz + j] = t0;
+        }
+        __syncthreads();
+      }
+      const cx<T> ipiv = crecip(CZ[c * ldcz + c]);
+      if (tid < r) tmp[tid] = CZ[tid * ldcz + c];    // column c before elimination
+      __syncthreads();
+      for (int j = tid; j < ldcz; j += kThreads) CZ[c * ldcz + j] = cmul(CZ[c * ldcz + j], ipiv);
+      __syncthreads();
+      for (int e = tid; e < r * ldcz; e += kThreads) {
+        const int i = e / ldcz, j = e - i * ldcz;
+        if (i != c) {
+          cx<T> v = CZ[e];
+          v = csub(v, cmul(tmp[i], CZ[c * ldcz + j]));
+          CZ[e] = v;
+        }
+      }
+      __syncthreads();
+    }
+    if (misc[1]) {
+      branch = WBRZF_BRANCH_FALLBACK;
+    } else {
+      // X <- X - T (C^{-1} Z)
+      for (int idx = tid; idx < KK; idx += kThreads) {
+        const int i = idx / K, j = idx - i * K;
+        cx<T> acc = cmk<T>(0, 0);
+        for (int c = 0; c < r; ++c) cfma(acc, Tm[i * rcap + c], CZ[c * ldcz + rcap + j]);
+        X[idx] = csub(X[idx], acc);
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---------------------------------------------------------------- 5b. direct inverse
+  if (branch == WBRZF_BRANCH_INIT || branch == WBRZF_BRANCH_PERIODIC ||
+      branch == WBRZF_BRANCH_RANK || branch == WBRZF_BRANCH_FULL ||
+      branch == WBRZF_BRANCH_FALLBACK) {
+    for (int idx = tid; idx < KK; idx += kThreads) X[idx] = G[idx];
+    __syncthreads();
+    // Gauss-Jordan exchange steps; G is Hermitian positive definite, so no pivoting:
+    // a = X_pp; X_pp <- 1/a; X_pj <- -X_pj/a; X_ip <- X_ip/a; X_ij <- X_ij - X_ip X_pj / a
+    bool bad = false;
+    for (int p = 0; p < K; ++p) {
+      if (tid < K) {
+        tmp[tid] = X[tid * K + p];          // column p
+        tmp[K + tid] = X[p * K + tid];      // row p
+      }
+      __syncthreads();
+      const cx<T> ap = tmp[p];
+      if (!(ap.re > T(0)) || !cfinite(ap)) bad = true;
+      const cx<T> ia = crecip(ap);
+      for (int idx = tid; idx < KK; idx += kThreads) {
+        const int i = idx / K, j = idx - i * K;
+        cx<T> v;
+        if (i == p && j == p) v = ia;
+        else if (i == p) v = cscale(cmul(tmp[K + j], ia), T(-1));
+        else if (j == p) v = cmul(tmp[i], ia);
+        else v = csub(X[idx], cmul(tmp[i], cmul(tmp[K + j], ia)));
+        X[idx] = v;
+      }
+      __syncthreads();
+    }
+    if (bad) status |= WBRZF_STATUS_NOT_PD;
+  }
+  if (a.mode != MODE_FULL) {
+    for (int idx = tid; idx < KK; idx += kThreads) Xsb[idx] = X[idx];
+  }
+
+  // ---------------------------------------------------------------- 6. scale and SINR
+  // M = G X - alpha X = H H^H X  (into D)
+  for (int idx = tid; idx < KK; idx += kThreads) {
+    const int i = idx / K, j = idx - i * K;
+    cx<T> acc = cscale(X[idx], -alpha);
+    for (int k = 0; k < K; ++k) cfma(acc, G[i * K + k], X[k * K + j]);
+    D[idx] = acc;
+  }
+  __syncthreads();
+  T part = 0;
+  for (int idx = tid; idx < KK; idx += kThreads) {
+    const cx<T> x = X[idx], m = D[idx];
+    part += x.re * m.re + x.im * m.im;          // Re(conj(x) m)
+  }
+  const T wn2 = block_sum(part, red);
+  const T s = sqrt(a.p_t / wn2);
+  T rate = 0;
+  if (tid < K) {
+    const int n = tid;
+    const T sig = s * s * cabs2(D[n * K + n]);
+    T intf = 0;
+    for (int i = 0; i < K; ++i)
+      if (i != n) intf += cabs2(D[n * K + i]);
+    intf *= s * s;
+    const T sinr = sig / (intf + sigma2);
+    a.sinr[(size_t)b * K + n] = (float)sinr;
+    rate = log2(T(1) + sinr);
+  }
+  const T R = block_sum(rate, red);
+  if (!isfinite(s) || !isfinite(R)) status |= WBRZF_STATUS_NONFINITE;
+  if (tid == 0) {
+    wbrzf_step_info inf;
+    inf.branch = branch;
+    inf.r = r;
+    inf.iters = iters;
+    inf.d = d;
+    inf.dg_fro2 = (float)dg2;
+    inf.scale = (float)s;
+    inf.sum_rate = (float)R;
+    inf.status = status;
+    a.info[b] = inf;
+  }
+
+  // ---------------------------------------------------------------- 7. precoder W = s H^H X
+  {
+    cx<T>* __restrict__ Wb = a.W + (size_t)b * N * K;
+    stage_chunk(Hb, K, N, 0, min(kChunk, N), Hbuf0, KP);
+    for (int c = 0; c < nchunks; ++c) {
+      if (c + 1 < nchunks) {
+        const int n1 = (c + 1) * kChunk;
+        stage_chunk(Hb, K, N, n1, min(kChunk, N - n1), (c & 1) ? Hbuf0 : Hbuf1, KP);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const cx<T>* hb = (c & 1) ? Hbuf1 : Hbuf0;
+      const int n0 = c * kChunk;
+      const int nc = min(kChunk, N - n0);
+      for (int idx = tid; idx < nc * K; idx += kThreads) {
+        const int n = idx / K, j = idx - n * K;
+        cx<T> acc = cmk<T>(0, 0);
+        for (int k = 0; k < K; ++k) cfma_jc(acc, hb[n * KP + k], X[k * K + j]);
+        Wb[(size_t)(n0 + n) * K + j] = cscale(acc, s);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace wbk

@@ -1,0 +1,353 @@
+// Host side of the C ABI declared in include/wbrzf.h: argument checking, workspace layout,
+// launch of the per-snapshot kernel, and the small copy-out calls.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "step_common.cuh"
+
+using namespace wbk;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+wbrzf_status cuda_fail(cudaError_t e) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return WBRZF_ERR_CUDA;
+}
+
+struct WsLayout {
+  size_t oG, oX, oInfo, oSinr, oAlpha, oSigma2, oIds, bytes;
+};
+
+size_t cx_bytes(wbrzf_precision p) { return p == WBRZF_C128 ? 16 : 8; }
+size_t re_bytes(wbrzf_precision p) { return p == WBRZF_C128 ? 8 : 4; }
+
+WsLayout ws_layout(int batch, int K, wbrzf_precision prec) {
+  WsLayout w;
+  const size_t B = (size_t)batch, KK = (size_t)K * K;
+  size_t o = 0;
+  w.oG = o;      o = align_up(o + B * KK * cx_bytes(prec), 256);
+  w.oX = o;      o = align_up(o + B * KK * cx_bytes(prec), 256);
+  w.oInfo = o;   o = align_up(o + B * sizeof(wbrzf_step_info), 256);
+  w.oSinr = o;   o = align_up(o + B * K * sizeof(float), 256);
+  w.oAlpha = o;  o = align_up(o + B * re_bytes(prec), 256);
+  w.oSigma2 = o; o = align_up(o + B * re_bytes(prec), 256);
+  w.oIds = o;    o = align_up(o + B * sizeof(uint32_t), 256);
+  w.bytes = o;
+  return w;
+}
+
+struct Resolved {
+  double eta, switch_ratio, dg_floor_rel;
+  int k_init, p, i_max, r_max, period, dmax, rcap;
+  unsigned long long seed;
+};
+
+bool resolve_rule(const wbrzf_rank_rule* rule, int K, Resolved* out) {
+  wbrzf_rank_rule r;
+  if (rule) {
+    r = *rule;
+  } else {
+    memset(&r, 0, sizeof(r));
+    r.eta = 0.9; r.k_init = 2; r.p = 1; r.switch_ratio = 0.5; r.reinverse_period = 20;
+  }
+  if (!(r.eta > 0.0 && r.eta <= 1.0) || r.k_init < 1 || r.p < 0 || r.i_max < 0 || r.r_max < 0 ||
+      !(r.switch_ratio >= 0.0) || r.reinverse_period < 0 || !(r.dg_floor_rel >= 0.0))
+    return false;
+  Resolved o;
+  o.eta = r.eta;
+  o.switch_ratio = r.switch_ratio;
+  o.dg_floor_rel = r.dg_floor_rel;
+  o.k_init = r.k_init;
+  o.p = r.p;
+  o.r_max = (r.r_max > 0 && r.r_max < K) ? r.r_max : K;
+  if (r.i_max > 0) {
+    o.i_max = r.i_max;
+  } else {      // smallest e with k_init 2^e >= r_max, plus one
+    int e = 0;
+    long long k = r.k_init;
+    while (k < o.r_max) { k *= 2; ++e; }
+    o.i_max = e + 1;
+  }
+  if (o.i_max > 16) return false;      // the Philox counter reserves 4 bits for the iteration
+  o.period = r.reinverse_period;
+  o.seed = r.seed;
+  long long k0 = r.k_init;
+  int dmax = 1;
+  for (int it = 0; it < o.i_max; ++it) {
+    const long long d = k0 + r.p < K ? k0 + r.p : K;
+    if (d > dmax) dmax = (int)d;
+    if (k0 < K) k0 *= 2;
+  }
+  o.dmax = dmax;
+  o.rcap = o.r_max < dmax ? o.r_max : dmax;
+  *out = o;
+  return true;
+}
+
+}  // namespace
+
+struct wbrzf {
+  int batch, N, K;
+  wbrzf_precision prec;
+  wbrzf_method method;
+  Resolved rule;
+  double p_t;
+  cudaStream_t stream;
+  unsigned char* ws;
+  WsLayout wl;
+  int t;                 // next snapshot index
+  bool initialized;
+  size_t smem;
+  unsigned char* trace;
+  size_t trace_stride;
+  long long launches;
+};
+
+namespace {
+
+template <class T>
+StepArgs<T> make_args(const wbrzf* h, const void* H, void* W, int mode, int t) {
+  StepArgs<T> a;
+  a.H = static_cast<const cx<T>*>(H);
+  a.W = static_cast<cx<T>*>(W);
+  a.Gs = reinterpret_cast<cx<T>*>(h->ws + h->wl.oG);
+  a.Xs = reinterpret_cast<cx<T>*>(h->ws + h->wl.oX);
+  a.info = reinterpret_cast<wbrzf_step_info*>(h->ws + h->wl.oInfo);
+  a.sinr = reinterpret_cast<float*>(h->ws + h->wl.oSinr);
+  a.alpha = reinterpret_cast<const T*>(h->ws + h->wl.oAlpha);
+  a.sigma2 = reinterpret_cast<const T*>(h->ws + h->wl.oSigma2);
+  a.ids = reinterpret_cast<const uint32_t*>(h->ws + h->wl.oIds);
+  a.trace = h->trace;
+  a.p_t = (T)h->p_t;
+  a.batch = h->batch;
+  a.N = h->N;
+  a.K = h->K;
+  a.mode = mode;
+  a.t = t;
+  a.eta = h->rule.eta;
+  a.k_init = h->rule.k_init;
+  a.p = h->rule.p;
+  a.i_max = h->rule.i_max;
+  a.r_max = h->rule.r_max;
+  a.switch_ratio = h->rule.switch_ratio;
+  a.period = h->rule.period;
+  a.seed_lo = (uint32_t)(h->rule.seed & 0xFFFFFFFFull);
+  a.seed_hi = (uint32_t)(h->rule.seed >> 32);
+  a.dg_floor_rel = h->rule.dg_floor_rel;
+  a.dmax = h->rule.dmax;
+  a.rcap = h->rule.rcap;
+  a.trace_stride = h->trace_stride;
+  return a;
+}
+
+wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
+  if (!h || !H || !W) return WBRZF_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(H) | reinterpret_cast<uintptr_t>(W)) % cx_bytes(h->prec))
+    return WBRZF_ERR_INVALID_ARG;
+  cudaError_t e;
+  if (h->prec == WBRZF_C128) {
+    e = launch_step_f64(make_args<double>(h, H, W, mode, h->t), h->smem, h->stream);
+  } else {
+    e = launch_step_f32(make_args<float>(h, H, W, mode, h->t), h->smem, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  h->launches += 1;
+  h->t += 1;
+  return WBRZF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t wbrzf_workspace_bytes(int batch, int N, int K, wbrzf_precision prec,
+                             const wbrzf_rank_rule* rule) {
+  Resolved r;
+  if (batch < 1 || N < 1 || K < 1 || K > kMaxK) return 0;
+  if (prec != WBRZF_C128 && prec != WBRZF_C64) return 0;
+  if (!resolve_rule(rule, K, &r)) return 0;
+  return ws_layout(batch, K, prec).bytes;
+}
+
+wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const double* sigma2,
+                          double p_t, const wbrzf_rank_rule* rule, wbrzf_method method,
+                          wbrzf_precision prec, void* workspace, size_t workspace_bytes,
+                          void* cuda_stream, wbrzf** out) {
+  if (!out) return WBRZF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (batch < 1 || batch > (1 << 28) || N < 1 || K < 1 || !alpha || !sigma2 || !(p_t > 0.0) ||
+      !workspace)
+    return WBRZF_ERR_INVALID_ARG;
+  if (method != WBRZF_METHOD_WB_ARSVD && method != WBRZF_METHOD_FULL_INVERSE)
+    return WBRZF_ERR_INVALID_ARG;
+  if (prec != WBRZF_C128 && prec != WBRZF_C64) return WBRZF_ERR_INVALID_ARG;
+  if (K > kMaxK) return WBRZF_ERR_UNSUPPORTED;
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return WBRZF_ERR_INVALID_ARG;
+  for (int b = 0; b < batch; ++b) {
+    if (!(alpha[b] >= 0.0) || !(sigma2[b] > 0.0) || !isfinite(alpha[b]) || !isfinite(sigma2[b]))
+      return WBRZF_ERR_INVALID_ARG;
+  }
+  Resolved r;
+  if (!resolve_rule(rule, K, &r)) return WBRZF_ERR_INVALID_ARG;
+  const WsLayout wl = ws_layout(batch, K, prec);
+  if (workspace_bytes < wl.bytes) return WBRZF_ERR_WORKSPACE;
+  const Layout sl = make_layout(K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec));
+  if (sl.bytes > 227 * 1024) return WBRZF_ERR_UNSUPPORTED;
+
+  wbrzf* h = new (std::nothrow) wbrzf;
+  if (!h) return WBRZF_ERR_INVALID_ARG;
+  h->batch = batch;
+  h->N = N;
+  h->K = K;
+  h->prec = prec;
+  h->method = method;
+  h->rule = r;
+  h->p_t = p_t;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->ws = static_cast<unsigned char*>(workspace);
+  h->wl = wl;
+  h->t = 0;
+  h->initialized = false;
+  h->smem = sl.bytes;
+  h->trace = nullptr;
+  h->trace_stride = trace_record_bytes(K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec));
+  h->launches = 0;
+
+  // per-instance parameters in the kernel's real type
+  const size_t rb = re_bytes(prec);
+  unsigned char* host = static_cast<unsigned char*>(
+      malloc(2 * (size_t)batch * rb + (size_t)batch * sizeof(uint32_t)));
+  if (!host) { delete h; return WBRZF_ERR_INVALID_ARG; }
+  uint32_t* ids = reinterpret_cast<uint32_t*>(host + 2 * (size_t)batch * rb);
+  for (int b = 0; b < batch; ++b) ids[b] = (uint32_t)b;
+  for (int b = 0; b < batch; ++b) {
+    if (prec == WBRZF_C128) {
+      reinterpret_cast<double*>(host)[b] = alpha[b];
+      reinterpret_cast<double*>(host)[batch + b] = sigma2[b];
+    } else {
+      reinterpret_cast<float*>(host)[b] = (float)alpha[b];
+      reinterpret_cast<float*>(host)[batch + b] = (float)sigma2[b];
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(h->ws + wl.oAlpha, host, batch * rb, cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws + wl.oSigma2, host + batch * rb, batch * rb,
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws + wl.oIds, ids, batch * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  free(host);
+  if (e != cudaSuccess) { delete h; return cuda_fail(e); }
+  *out = h;
+  return WBRZF_OK;
+}
+
+wbrzf_status wbrzf_full_inverse(wbrzf* h, const void* H_t, void* W_out) {
+  if (!h) return WBRZF_ERR_INVALID_ARG;
+  h->t = 0;
+  const int mode = (h->method == WBRZF_METHOD_FULL_INVERSE) ? MODE_FULL : MODE_INIT;
+  wbrzf_status s = run_step(h, H_t, W_out, mode);
+  if (s == WBRZF_OK) h->initialized = true;
+  return s;
+}
+
+wbrzf_status wbrzf_update(wbrzf* h, const void* H_t, void* W_out) {
+  if (!h) return WBRZF_ERR_INVALID_ARG;
+  if (h->method == WBRZF_METHOD_FULL_INVERSE) return run_step(h, H_t, W_out, MODE_FULL);
+  if (!h->initialized) return WBRZF_ERR_NOT_INITIALIZED;
+  return run_step(h, H_t, W_out, MODE_UPDATE);
+}
+
+wbrzf_status wbrzf_sum_rate(wbrzf* h, float* sinr_out, float* sum_rate_out) {
+  if (!h) return WBRZF_ERR_INVALID_ARG;
+  cudaError_t e = cudaSuccess;
+  if (sinr_out)
+    e = cudaMemcpyAsync(sinr_out, h->ws + h->wl.oSinr, (size_t)h->batch * h->K * sizeof(float),
+                        cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess && sum_rate_out)
+    e = cudaMemcpy2DAsync(sum_rate_out, sizeof(float),
+                          h->ws + h->wl.oInfo + offsetof(wbrzf_step_info, sum_rate),
+                          sizeof(wbrzf_step_info), sizeof(float), h->batch,
+                          cudaMemcpyDeviceToDevice, h->stream);
+  return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
+}
+
+wbrzf_status wbrzf_step_info_get(wbrzf* h, wbrzf_step_info* host_out, int count) {
+  if (!h || !host_out || count < 0 || count > h->batch) return WBRZF_ERR_INVALID_ARG;
+  if (count == 0) return WBRZF_OK;
+  cudaError_t e = cudaMemcpyAsync(host_out, h->ws + h->wl.oInfo,
+                                  (size_t)count * sizeof(wbrzf_step_info), cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  for (int b = 0; b < count; ++b)
+    if (host_out[b].status != WBRZF_STATUS_OK) return WBRZF_ERR_NUMERICAL;
+  return WBRZF_OK;
+}
+
+wbrzf_status wbrzf_get_state(wbrzf* h, void* G_out, void* X_out) {
+  if (!h) return WBRZF_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)h->batch * h->K * h->K * cx_bytes(h->prec);
+  cudaError_t e = cudaSuccess;
+  if (G_out) e = cudaMemcpyAsync(G_out, h->ws + h->wl.oG, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess && X_out)
+    e = cudaMemcpyAsync(X_out, h->ws + h->wl.oX, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
+}
+
+size_t wbrzf_trace_bytes(const wbrzf* h) {
+  return h ? h->trace_stride * (size_t)h->batch : 0;
+}
+
+wbrzf_status wbrzf_set_trace(wbrzf* h, void* trace, size_t bytes) {
+  if (!h) return WBRZF_ERR_INVALID_ARG;
+  if (trace && (bytes < wbrzf_trace_bytes(h) || reinterpret_cast<uintptr_t>(trace) % 16))
+    return WBRZF_ERR_INVALID_ARG;
+  h->trace = static_cast<unsigned char*>(trace);
+  return WBRZF_OK;
+}
+
+wbrzf_status wbrzf_set_instance_ids(wbrzf* h, const uint32_t* ids, int count) {
+  if (!h || !ids || count < 0 || count > h->batch) return WBRZF_ERR_INVALID_ARG;
+  for (int b = 0; b < count; ++b)
+    if (ids[b] >= (1u << 28)) return WBRZF_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(h->ws + h->wl.oIds, ids, (size_t)count * sizeof(uint32_t),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
+}
+
+wbrzf_status wbrzf_set_stream(wbrzf* h, void* cuda_stream) {
+  if (!h) return WBRZF_ERR_INVALID_ARG;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  return WBRZF_OK;
+}
+
+long long wbrzf_launch_count(const wbrzf* h) { return h ? h->launches : 0; }
+
+void wbrzf_destroy(wbrzf* h) { delete h; }
+
+const char* wbrzf_status_string(wbrzf_status s) {
+  switch (s) {
+    case WBRZF_OK: return "ok";
+    case WBRZF_ERR_INVALID_ARG: return "invalid argument";
+    case WBRZF_ERR_NOT_INITIALIZED: return "update before the first full inverse";
+    case WBRZF_ERR_WORKSPACE: return "workspace too small";
+    case WBRZF_ERR_NUMERICAL: return "an instance could not be inverted";
+    case WBRZF_ERR_CUDA: return "CUDA runtime error";
+    case WBRZF_ERR_UNSUPPORTED: return "unsupported shape or precision";
+  }
+  return "unknown status";
+}
+
+const char* wbrzf_last_cuda_error(void) { return g_cuda_err; }
+
+}  // extern "C"
