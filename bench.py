@@ -115,9 +115,13 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- CPU oracle
+def _init_oracle_worker():
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["OMP_NUM_THREADS"] = "1"
+
+
 def _oracle_worker(args):
     """Run the FP64 oracle on a few trajectories; returns (updates, seconds)."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     sys.path.insert(0, ROOT)
     import numpy as np
     from oracle import method as om
@@ -150,8 +154,7 @@ def cpu_oracle_baseline(params, sc, rule_kw, n_inst: int, n_steps: int, method: 
             for ch in chunks if ch]
     ctx = mp.get_context("spawn")
     t_start = time.perf_counter()
-    with ctx.Pool(len(jobs), initializer=os.environ.__setitem__,
-                  initargs=("OPENBLAS_NUM_THREADS", "1")) as pool:
+    with ctx.Pool(len(jobs), initializer=_init_oracle_worker) as pool:
         res = pool.map(_oracle_worker, jobs)
     wall = time.perf_counter() - t_start
     n = sum(r[0] for r in res)

@@ -139,6 +139,8 @@ class WBRZF:
         self.dtype = torch.complex64 if self.prec == C64 else torch.complex128
         self.rdtype = torch.float32 if self.prec == C64 else torch.float64
         self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.rule = rule or RankRule()
         self._rule_c = self.rule.to_c()
         a = [float(x) for x in (alpha if hasattr(alpha, "__len__") else [alpha] * self.batch)]

@@ -282,8 +282,16 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_kernel(const StepArgs<T> 
 
   // ---------------------------------------------------------------- 3. arSVD (Algorithm 1)
   int r = 0, iters = 0, d = 0;
+  int dg_exp = 0;      // dG is scaled by 2^-dg_exp (exact) for the low-rank step
   if (branch == -1) {
-    const double E_target = a.eta * dg2;
+    // Bring dG to unit Frobenius norm by an exact power of two so that the squared
+    // quantities of the sketch, CholQR and Jacobi steps stay far from FP32 underflow
+    // whatever the scale of the channel; every result is rescaled exactly afterwards.
+    frexp(sqrt(dg2), &dg_exp);
+    const T down = (T)ldexp(1.0, -dg_exp);
+    for (int idx = tid; idx < KK; idx += kThreads) D[idx] = cscale(D[idx], down);
+    __syncthreads();
+    const double E_target = a.eta * ldexp(dg2, -2 * dg_exp);
     int k0 = a.k_init;
     bool met = false;
     for (int it = 0; it < a.i_max; ++it) {
@@ -366,7 +374,7 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_kernel(const StepArgs<T> 
         const int dd = d + (d & 1);
         const int npairs = dd >> 1;
         const int max_sweeps = (sizeof(T) == 4) ? 12 : 20;
-        const T eps = (sizeof(T) == 4) ? T(1e-13) : T(1e-30);
+        const T eps = (sizeof(T) == 4) ? T(1e-12) : T(1e-28);
         for (int sweep = 0; sweep < max_sweeps; ++sweep) {
           T off = 0, tot = 0;
           for (int e = tid; e < d * d; e += kThreads) {
@@ -393,7 +401,7 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_kernel(const StepArgs<T> 
               cx<T> ph = cmk<T>(1, 0);
               if (active) {
                 const cx<T> bpq = Gy[p1 * dmax + q1];
-                const T ab = sqrt(cabs2(bpq));
+                const T ab = hypot(bpq.re, bpq.im);     // no squaring: unit-modulus phase
                 if (ab > T(0)) {
                   ph = cmk(bpq.re / ab, -bpq.im / ab);               // e^{-i phi}
                   const T th = T(0.5) * atan2(T(2) * ab, Gy[q1 * dmax + q1].re - Gy[p1 * dmax + p1].re);
@@ -472,7 +480,8 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_kernel(const StepArgs<T> 
                                                                        : WBRZF_BRANCH_WOODBURY;
     if (a.trace != nullptr) {
       T* tr = reinterpret_cast<T*>(a.trace + (size_t)b * a.trace_stride);
-      for (int j = tid; j < dmax; j += kThreads) tr[j] = (j < d) ? lam[perm[j]] : T(0);
+      for (int j = tid; j < dmax; j += kThreads)
+        tr[j] = (j < d) ? (T)ldexp((double)lam[perm[j]], 2 * dg_exp) : T(0);
     }
   }
 
@@ -487,12 +496,13 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_kernel(const StepArgs<T> 
       for (int k = 0; k < d; ++k) cfma(acc, Q[i * dmax + k], Uh[k * dmax + pc]);
       Lm[i * rcap + c] = acc;
     }
+    const T up = (T)ldexp(1.0, dg_exp);      // undo the scaling of dG: dG = L (up R^H)
     for (int idx = tid; idx < r * K; idx += kThreads) {
       const int c = idx / K, j = idx - c * K;
       const int pc = perm[c];
       cx<T> acc = cmk<T>(0, 0);
       for (int k = 0; k < d; ++k) cfma_jc(acc, Uh[k * dmax + pc], Bm[k * K + j]);
-      Rh[c * K + j] = acc;
+      Rh[c * K + j] = cscale(acc, up);
     }
     __syncthreads();
     if (a.trace != nullptr) {
