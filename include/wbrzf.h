@@ -181,6 +181,34 @@ long long wbrzf_launch_count(const wbrzf* h);
 /* Release the handle (host memory only; the workspace stays the caller's). NULL is a no-op. */
 void wbrzf_destroy(wbrzf* h);
 
+/*
+ * Conventional (full-inversion) RZF precoders without any caller-provided device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory at all -- code being recorded into a CUDA graph by stream capture (allocation
+ * is not allowed there), hard real-time loops that forbid allocation after start-up, and
+ * plug-ins whose host framework owns all device memory.
+ *
+ * For each of `batch` instances: G = H H^H + alpha I, X = G^{-1} (direct), W_out = s H^H X
+ * with ||W||_F^2 = p_t, and, when sum_rate_out is not NULL, R_sum of eq. 15 per instance
+ * (device float[batch]); the same kernel as a WBRZF_METHOD_FULL_INVERSE handle, so the same
+ * results.  H_t / W_out: device, layouts as for wbrzf_update; alpha, sigma2 are shared by all
+ * instances.  Work is enqueued on cuda_stream (cudaStream_t, NULL = legacy default stream).
+ *
+ * Scratch: a fixed array of WBRZF_NOALLOC_SCRATCH_BYTES compiled into the library (held by
+ * every GPU that loads it until the process exits).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture begins.  All calls share the array and it keeps the last call's contents; calls
+ * whose work overlaps on the GPU race on it, so serialise them (one stream, or events).
+ * Limits: batch <= WBRZF_NOALLOC_MAX_BATCH and the single-CTA limits of wbrzf_create
+ * (K <= 64; K = 64 only for complex64) -- larger requests return WBRZF_ERR_UNSUPPORTED.
+ * The call itself allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ */
+#define WBRZF_NOALLOC_MAX_BATCH 4096
+#define WBRZF_NOALLOC_SCRATCH_BYTES 1310720
+wbrzf_status wbrzf_rzf_noalloc(int batch, int N, int K, wbrzf_precision prec, const void* H_t,
+                               double alpha, double sigma2, double p_t, void* W_out,
+                               float* sum_rate_out, void* cuda_stream);
+
 /* Static description of a status code; the last CUDA error string seen by any handle. */
 const char* wbrzf_status_string(wbrzf_status s);
 const char* wbrzf_last_cuda_error(void);

@@ -277,3 +277,26 @@ def resolved_sizes(K: int, rule: RankRule) -> tuple[int, int, int, int]:
         if k0 < K:
             k0 *= 2
     return r_max, i_max, dmax, min(r_max, dmax)
+
+
+def rzf_noalloc(H: torch.Tensor, alpha: float, sigma2: float, p_t: float = 1.0,
+                W: torch.Tensor | None = None, sum_rate: torch.Tensor | None = None,
+                stream: torch.cuda.Stream | None = None):
+    """Full-inversion RZF precoders through wbrzf_rzf_noalloc: no workspace is needed, for
+    callers that cannot allocate device memory (see include/wbrzf.h).  H: [batch, K, N]
+    complex64/complex128 on the device; returns (W [batch, N, K], sum-rate [batch])."""
+    L = lib()
+    f = L.wbrzf_rzf_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p] + [ctypes.c_double] * 3 + \
+        [ctypes.c_void_p] * 3
+    B, K, N = H.shape
+    prec = C128 if H.dtype == torch.complex128 else C64
+    if W is None:
+        W = torch.empty(B, N, K, dtype=H.dtype, device=H.device)
+    if sum_rate is None:
+        sum_rate = torch.empty(B, dtype=torch.float32, device=H.device)
+    s = stream or torch.cuda.current_stream(H.device)
+    _check(f(B, N, K, prec, H.data_ptr(), alpha, sigma2, p_t, W.data_ptr(),
+             sum_rate.data_ptr(), s.cuda_stream), "wbrzf_rzf_noalloc")
+    return W, sum_rate
