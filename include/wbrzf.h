@@ -80,7 +80,17 @@ enum {
 enum {
   WBRZF_STATUS_OK = 0,
   WBRZF_STATUS_NOT_PD = 1,      /* direct inverse met a non-positive pivot: G_t not HPD      */
-  WBRZF_STATUS_NONFINITE = 2    /* a NaN/Inf reached the precoder or the scale               */
+  WBRZF_STATUS_NONFINITE = 2,   /* a NaN/Inf reached the precoder or the scale               */
+  WBRZF_STATUS_TIMEOUT = 4      /* a bounded wait for a copy or tensor-core step expired    */
+};
+
+/* Which kernel runs a handle's snapshots (wbrzf_set_engine). */
+enum {
+  WBRZF_ENGINE_AUTO = 0,      /* tensor cores when eligible, else the FMA kernel             */
+  WBRZF_ENGINE_SIMT = 1,      /* FP32/FP64 fused multiply-adds for every product             */
+  WBRZF_ENGINE_TENSOR = 2     /* tcgen05 tensor cores for H H^H (FP32-faithful hi/lo TF32
+                                 split) and H^H X (TF32 inputs, FP32 accumulation); complex64,
+                                 K <= 32, even N, H_t 16-byte aligned                         */
 };
 
 /* Rank rule and method parameters (Algorithm 1 inputs, Algorithm 2 switch). */
@@ -172,6 +182,12 @@ wbrzf_status wbrzf_set_trace(wbrzf* h, void* trace, size_t bytes);
  * not depend on its position in a batch.  Default: ids[b] = b.  Synchronises the stream. */
 wbrzf_status wbrzf_set_instance_ids(wbrzf* h, const uint32_t* ids, int count);
 
+/* Choose the kernel (WBRZF_ENGINE_*).  WBRZF_ENGINE_TENSOR on a handle that does not meet
+ * its conditions returns WBRZF_ERR_UNSUPPORTED.  wbrzf_last_engine reports the kernel the
+ * last snapshot ran on (WBRZF_ENGINE_SIMT or WBRZF_ENGINE_TENSOR; 0 before any). */
+wbrzf_status wbrzf_set_engine(wbrzf* h, int engine);
+int wbrzf_last_engine(const wbrzf* h);
+
 /* Rebind the handle to another stream (cudaStream_t; NULL = legacy default stream). */
 wbrzf_status wbrzf_set_stream(wbrzf* h, void* cuda_stream);
 
@@ -190,8 +206,8 @@ void wbrzf_destroy(wbrzf* h);
  *
  * For each of `batch` instances: G = H H^H + alpha I, X = G^{-1} (direct), W_out = s H^H X
  * with ||W||_F^2 = p_t, and, when sum_rate_out is not NULL, R_sum of eq. 15 per instance
- * (device float[batch]); the same kernel as a WBRZF_METHOD_FULL_INVERSE handle, so the same
- * results.  H_t / W_out: device, layouts as for wbrzf_update; alpha, sigma2 are shared by all
+ * (device float[batch]); the same kernel as a WBRZF_METHOD_FULL_INVERSE handle on
+ * WBRZF_ENGINE_SIMT, so the same results.  H_t / W_out: device, layouts as for wbrzf_update; alpha, sigma2 are shared by all
  * instances.  Work is enqueued on cuda_stream (cudaStream_t, NULL = legacy default stream).
  *
  * Scratch: a fixed array of WBRZF_NOALLOC_SCRATCH_BYTES compiled into the library (held by

@@ -98,6 +98,10 @@ def lib() -> ctypes.CDLL:
     L.wbrzf_set_trace.argtypes = [vp, vp, sz]
     L.wbrzf_set_instance_ids.restype = i32
     L.wbrzf_set_instance_ids.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), i32]
+    L.wbrzf_set_engine.restype = i32
+    L.wbrzf_set_engine.argtypes = [vp, i32]
+    L.wbrzf_last_engine.restype = i32
+    L.wbrzf_last_engine.argtypes = [vp]
     L.wbrzf_set_stream.restype = i32
     L.wbrzf_set_stream.argtypes = [vp, vp]
     L.wbrzf_launch_count.restype = ctypes.c_longlong
@@ -239,6 +243,15 @@ class WBRZF:
         ids = [int(x) for x in ids]
         arr = (ctypes.c_uint32 * len(ids))(*ids)
         _check(lib().wbrzf_set_instance_ids(self._h, arr, len(ids)), "wbrzf_set_instance_ids")
+
+    def set_engine(self, engine: str) -> None:
+        """"auto", "simt" (fused multiply-adds) or "tensor" (tcgen05 tensor cores)."""
+        code = {"auto": 0, "simt": 1, "tensor": 2}[engine]
+        _check(lib().wbrzf_set_engine(self._h, code), "wbrzf_set_engine")
+
+    @property
+    def last_engine(self) -> str:
+        return {0: "none", 1: "simt", 2: "tensor"}[int(lib().wbrzf_last_engine(self._h))]
 
     def set_stream(self, stream: torch.cuda.Stream) -> None:
         self.stream = stream

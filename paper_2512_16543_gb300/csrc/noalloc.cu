@@ -6,9 +6,9 @@
 // started; and plug-ins whose host framework owns every byte of device memory.  For them,
 // wbrzf_rzf_noalloc() computes the conventional RZF precoders (direct inverse of G = H H^H +
 // alpha I, W = s H^H G^{-1}, power normalisation, per-user SINR and sum-rate) with the same
-// per-snapshot kernel as a WBRZF_METHOD_FULL_INVERSE handle, but takes its per-instance
-// scratch (regulariser, noise and id arrays, step info, SINR) from a fixed array compiled into
-// this library instead of from a caller workspace.
+// per-snapshot FMA kernel as a WBRZF_METHOD_FULL_INVERSE handle on WBRZF_ENGINE_SIMT, but
+// takes its per-instance scratch (regulariser, noise and id arrays, step info, SINR) from a
+// fixed array compiled into this library instead of from a caller workspace.
 //
 // The array below is a file-scope __device__ object: every GPU that loads the library holds
 // its WBRZF_NOALLOC_SCRATCH_BYTES until the process exits.  In host code its name is only a
@@ -83,8 +83,8 @@ wbrzf_status run_noalloc(int batch, int N, int K, const void* H, double alpha, d
                          double p_t, void* W_out, float* sum_rate_out, cudaStream_t stream) {
   const ScratchLayout sl = scratch_layout(batch, K, sizeof(T));
   if (sl.bytes > WBRZF_NOALLOC_SCRATCH_BYTES) return WBRZF_ERR_UNSUPPORTED;
-  const Layout smem = make_layout(K, 1, 1, sizeof(cx<T>), sizeof(T));
-  if (smem.bytes > 227 * 1024) return WBRZF_ERR_UNSUPPORTED;
+  const size_t smem = simt_smem_bytes(K, 1, 1, sizeof(cx<T>), sizeof(T));
+  if (smem > 227 * 1024) return WBRZF_ERR_UNSUPPORTED;
   unsigned char* base = nullptr;
   cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return WBRZF_ERR_CUDA;
@@ -126,8 +126,8 @@ wbrzf_status run_noalloc(int batch, int N, int K, const void* H, double alpha, d
   a.dmax = 1;
   a.rcap = 1;
   a.trace_stride = 0;
-  if constexpr (sizeof(T) == 8) e = launch_step_f64(a, smem.bytes, stream);
-  else e = launch_step_f32(a, smem.bytes, stream);
+  if constexpr (sizeof(T) == 8) e = launch_step_f64(a, smem, stream);
+  else e = launch_step_f32(a, smem, stream);
   if (e != cudaSuccess) return WBRZF_ERR_CUDA;
   if (sum_rate_out) {
     e = cudaMemcpy2DAsync(sum_rate_out, sizeof(float),

@@ -47,52 +47,62 @@ struct StepArgs {
   size_t trace_stride;     // bytes per instance trace record
 };
 
-// Shared-memory carve-up of the per-snapshot kernel, in units of cx<T> (complex) followed by a
-// small real/int scratch area.  The host uses the same function to size the launch.
-struct Layout {
-  int K, KP, NC, dmax, rcap;
-  size_t oG, oX, oD, oH0, oH1, oOm, oQ, oGy, oB, oUh, oRh, oT, oCZ, oTmp;
-  size_t n_cx;           // complex elements
-  size_t oRealBytes;     // byte offset of the real scratch area
-  size_t bytes;          // total bytes
-};
-
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline Layout make_layout(int K, int dmax, int rcap, size_t cx_bytes,
-                                               size_t t_bytes) {
-  Layout L;
-  L.K = K;
-  L.KP = K + 1;           // padded row of a transposed H chunk (bank spread)
-  L.NC = kChunk;
-  L.dmax = dmax;
-  L.rcap = rcap;
-  size_t o = 0;
-  const size_t KK = (size_t)K * K;
-  L.oG = o;   o += KK;
-  L.oX = o;   o += KK;
-  L.oD = o;   o += KK;
-  L.oH0 = o;  o += (size_t)L.NC * L.KP;
-  L.oH1 = o;  o += (size_t)L.NC * L.KP;
-  L.oOm = o;  o += (size_t)K * dmax;           // Omega, later L = Q U_r
-  L.oQ = o;   o += (size_t)K * dmax;           // Y, then Q
-  L.oGy = o;  o += (size_t)dmax * dmax;        // Y^H Y, then B B^H
-  L.oB = o;   o += (size_t)dmax * K;           // B = Q^H dG
-  L.oUh = o;  o += (size_t)dmax * dmax;        // eigenvectors of B B^H
-  L.oRh = o;  o += (size_t)rcap * K;           // R^H = U_r^H B
-  L.oT = o;   o += (size_t)K * rcap;           // T = X L
-  L.oCZ = o;  o += (size_t)rcap * (rcap + K);  // [C | Z] for the capacitance solve
-  L.oTmp = o; o += (size_t)2 * K + 2;          // pivot row / column of the direct inverse
-  L.n_cx = o;
-  size_t bytes = align_up(o * cx_bytes, 16);
-  L.oRealBytes = bytes;
-  // real scratch: reduction slots (40), eigenvalues (dmax), rotation c,s (dmax) each,
-  // column norms (dmax); ints: perm, pair p, pair q, drop flags (dmax each), misc (16)
+// Bytes of the small-matrix workspace of the phases between the Gram matrix and the
+// precoder: optionally G, X, dG (K x K), the sketch buffers (width dmax), the Woodbury buffers
+// (rank rcap), then real scratch (reductions, eigenvalues, rotations, column norms), integer
+// scratch (permutation, pairs, drop flags, flags) and the rotation phases.  The device-side
+// carve-up (carve_work) follows exactly this order.
+__host__ __device__ inline size_t work_bytes(int K, int dmax, int rcap, bool with_gxd,
+                                             size_t cx_bytes, size_t t_bytes) {
+  const size_t n = (with_gxd ? 3 * (size_t)K * K : 0) + 2 * (size_t)K * dmax +
+                   2 * (size_t)dmax * dmax + (size_t)dmax * K + 2 * (size_t)rcap * K +
+                   (size_t)rcap * (rcap + K) + 2 * (size_t)K + 2;
+  size_t bytes = align_up(n * cx_bytes, 16);
   bytes += align_up((40 + 4 * (size_t)dmax) * t_bytes, 16);
   bytes += align_up((4 * (size_t)dmax + 16) * sizeof(int), 16);
-  bytes += align_up((size_t)dmax * cx_bytes, 16);   // rotation phases
-  L.bytes = bytes;
+  bytes += align_up((size_t)dmax * cx_bytes, 16);
+  return bytes;
+}
+
+// Dynamic shared memory of the SIMT kernel: two transposed H chunks, then the workspace.
+__host__ __device__ inline size_t simt_smem_bytes(int K, int dmax, int rcap, size_t cx_bytes,
+                                                  size_t t_bytes) {
+  return align_up(2 * (size_t)kChunk * (K + 1) * cx_bytes, 16) +
+         work_bytes(K, dmax, rcap, true, cx_bytes, t_bytes);
+}
+
+// ---------------------------------------------------------------- tensor-core kernel plan
+constexpr int kStages = 4;                    // TMA staging ring depth (blocks of 32 antennas)
+constexpr uint32_t kTmemCols = 128;           // Gram D: 128 x 128; W D: 128 x 64
+
+// ---------------------------------------------------------------- shared-memory plan
+struct TcLayout {
+  size_t oGXD, oRing, oUnion, oBar, bytes_unpadded, union_bytes;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int K, int dmax, int rcap) {
+  TcLayout L;
+  size_t o = 0;
+  L.oGXD = o;   o = align_up(o + 3 * (size_t)K * K * 8, 1024);
+  L.oRing = o;  o = align_up(o + (size_t)kStages * 32 * 256, 1024);
+  L.oUnion = o;
+  size_t u = 2 * 16384;                                   // Gram: two 128 x 128 B tiles
+  const size_t wk = work_bytes(K, dmax, rcap, false, 8, 4);
+  if (wk > u) u = wk;
+  if (4 * (size_t)K * K * 8 > u) u = 4 * (size_t)K * K * 8;   // Gram epilogue partials
+  if (32768 + 16384 > u) u = 32768 + 16384;               // W: A tile + B tile
+  L.union_bytes = align_up(u, 1024);
+  o += L.union_bytes;
+  L.oBar = o;   o += 256;
+  L.bytes_unpadded = o;
   return L;
+}
+
+// host: dynamic shared memory to request (1 KiB slack for the 1024-byte realignment)
+__host__ __device__ inline size_t tc_smem_bytes(int K, int dmax, int rcap) {
+  return tc_layout(K, dmax, rcap).bytes_unpadded + 1024;
 }
 
 // Trace record of one instance: sigma_hat^2 [dmax] (T), L [K][rcap] and R^H [rcap][K] (cx<T>).
@@ -104,5 +114,9 @@ __host__ __device__ inline size_t trace_record_bytes(int K, int dmax, int rcap, 
 // Launch wrappers, one per real type (defined in step_f32.cu / step_f64.cu).
 cudaError_t launch_step_f32(const StepArgs<float>& a, size_t smem, cudaStream_t s);
 cudaError_t launch_step_f64(const StepArgs<double>& a, size_t smem, cudaStream_t s);
+// Tensor-core kernel (complex64, K <= 32, even N); hmap: H as a 2-D FP32 tensor map
+// {2N, batch K}, box {64, K} (step_tc.cu).  `hmap` points to a CUtensorMap.
+cudaError_t launch_step_tc(const StepArgs<float>& a, const void* hmap, size_t smem,
+                           cudaStream_t s);
 
 }  // namespace wbk

@@ -156,100 +156,91 @@ __device__ void mm(int m, int n, int kk, const cx<T>* A, int lda, const cx<T>* B
   }
 }
 
-// ------------------------------------------------------------------ the kernel
+// ------------------------------------------------------------------ shared-memory views
+// Pointers of the per-instance matrices and scratch used by the phases between the Gram
+// matrix and the precoder (they are laid out differently by the two kernels).
 template <class T>
-__global__ void __launch_bounds__(kThreads) wbrzf_step_kernel(const StepArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int b = blockIdx.x;
-  const int tid = threadIdx.x;
-  const int K = a.K, N = a.N, KK = K * K;
-  const Layout Ly = make_layout(K, a.dmax, a.rcap, sizeof(cx<T>), sizeof(T));
-  cx<T>* const smc = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* const G = smc + Ly.oG;
-  cx<T>* const X = smc + Ly.oX;
-  cx<T>* const D = smc + Ly.oD;
-  cx<T>* const Hbuf0 = smc + Ly.oH0;
-  cx<T>* const Hbuf1 = smc + Ly.oH1;
-  cx<T>* const Om = smc + Ly.oOm;   // later L
-  cx<T>* const Q = smc + Ly.oQ;
-  cx<T>* const Gy = smc + Ly.oGy;   // Y^H Y, then B B^H (eigen workspace)
-  cx<T>* const Bm = smc + Ly.oB;
-  cx<T>* const Uh = smc + Ly.oUh;
-  cx<T>* const Rh = smc + Ly.oRh;
-  cx<T>* const Tm = smc + Ly.oT;
-  cx<T>* const CZ = smc + Ly.oCZ;
-  cx<T>* const tmp = smc + Ly.oTmp;
-  const int dmax = a.dmax, rcap = a.rcap, KP = Ly.KP;
-  T* const red = reinterpret_cast<T*>(smem_raw + Ly.oRealBytes);       // 40 slots
-  T* const lam = red + 40;                                              // dmax
-  T* const rc = lam + dmax;                                             // dmax (cos)
-  T* const rs = rc + dmax;                                              // dmax (sin)
-  T* const cn = rs + dmax;                                              // dmax (column norms)
-  int* const ibase = reinterpret_cast<int*>(
-      smem_raw + Ly.oRealBytes + align_up((40 + 4 * (size_t)dmax) * sizeof(T), 16));
-  int* const perm = ibase;
-  int* const pp = perm + dmax;
-  int* const pq = pp + dmax;
-  int* const drop = pq + dmax;
-  int* const misc = drop + dmax;                                        // 16
-  cx<T>* const rph = reinterpret_cast<cx<T>*>(
-      reinterpret_cast<unsigned char*>(ibase) + align_up((4 * (size_t)dmax + 16) * sizeof(int), 16));
+struct Work {
+  cx<T>*G, *X, *D, *Om, *Q, *Gy, *Bm, *Uh, *Rh, *Tm, *CZ, *tmp, *rph;
+  T *red, *lam, *rc, *rs, *cn;
+  int *perm, *pp, *pq, *drop, *misc;
+  int dmax, rcap;
+};
 
+// Carve the small-matrix workspace (layout of work_bytes) out of `base` (16-byte aligned).
+template <class T>
+__device__ inline Work<T> carve_work(unsigned char* base, int K, int dmax, int rcap, cx<T>* G,
+                                     cx<T>* X, cx<T>* D) {
+  Work<T> w;
+  cx<T>* c = reinterpret_cast<cx<T>*>(base);
+  const size_t KK = (size_t)K * K;
+  if (G == nullptr) { G = c; c += KK; X = c; c += KK; D = c; c += KK; }
+  w.G = G; w.X = X; w.D = D;
+  w.Om = c; c += (size_t)K * dmax;
+  w.Q = c; c += (size_t)K * dmax;
+  w.Gy = c; c += (size_t)dmax * dmax;
+  w.Bm = c; c += (size_t)dmax * K;
+  w.Uh = c; c += (size_t)dmax * dmax;
+  w.Rh = c; c += (size_t)rcap * K;
+  w.Tm = c; c += (size_t)K * rcap;
+  w.CZ = c; c += (size_t)rcap * (rcap + K);
+  w.tmp = c; c += 2 * (size_t)K + 2;
+  unsigned char* p = reinterpret_cast<unsigned char*>(base) +
+                     align_up((size_t)(c - reinterpret_cast<cx<T>*>(base)) * sizeof(cx<T>), 16);
+  w.red = reinterpret_cast<T*>(p);
+  w.lam = w.red + 40;
+  w.rc = w.lam + dmax;
+  w.rs = w.rc + dmax;
+  w.cn = w.rs + dmax;
+  p += align_up((40 + 4 * (size_t)dmax) * sizeof(T), 16);
+  w.perm = reinterpret_cast<int*>(p);
+  w.pp = w.perm + dmax;
+  w.pq = w.pp + dmax;
+  w.drop = w.pq + dmax;
+  w.misc = w.drop + dmax;
+  p += align_up((4 * (size_t)dmax + 16) * sizeof(int), 16);
+  w.rph = reinterpret_cast<cx<T>*>(p);
+  w.dmax = dmax;
+  w.rcap = rcap;
+  return w;
+}
+
+// ------------------------------------------------------------------ phases 2-6
+// Given G_t in w.G (Hermitian, alpha on the diagonal), run the perturbation, the low-rank
+// step, the Woodbury update or direct inverse, the state write-back, the power scale and the
+// SINR / sum-rate.  Leaves X in w.X and returns the precoder scale s.
+template <class T>
+__device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
+  const int tid = threadIdx.x;
+  const int K = a.K, KK = K * K;
+  cx<T>* const G = w.G;
+  cx<T>* const X = w.X;
+  cx<T>* const D = w.D;
+  cx<T>* const Om = w.Om;
+  cx<T>* const Q = w.Q;
+  cx<T>* const Gy = w.Gy;
+  cx<T>* const Bm = w.Bm;
+  cx<T>* const Uh = w.Uh;
+  cx<T>* const Rh = w.Rh;
+  cx<T>* const Tm = w.Tm;
+  cx<T>* const CZ = w.CZ;
+  cx<T>* const tmp = w.tmp;
+  cx<T>* const rph = w.rph;
+  T* const red = w.red;
+  T* const lam = w.lam;
+  T* const rc = w.rc;
+  T* const rs = w.rs;
+  T* const cn = w.cn;
+  int* const perm = w.perm;
+  int* const pp = w.pp;
+  int* const pq = w.pq;
+  int* const drop = w.drop;
+  int* const misc = w.misc;
+  const int dmax = w.dmax, rcap = w.rcap;
   const uint32_t inst_id = a.ids[b];
   const T alpha = a.alpha[b];
   const T sigma2 = a.sigma2[b];
-  const cx<T>* __restrict__ Hb = a.H + (size_t)b * K * N;
-  const int nchunks = (N + kChunk - 1) / kChunk;
   int status = WBRZF_STATUS_OK;
-
-  // ---------------------------------------------------------------- 1. Gram matrix
-  constexpr int QMAX = (kMaxK * kMaxK + kThreads - 1) / kThreads;
-  {
-    cx<T> acc[QMAX];
-    int kq[QMAX], lq[QMAX];
-#pragma unroll
-    for (int q = 0; q < QMAX; ++q) {
-      acc[q] = cmk<T>(0, 0);
-      const int idx = tid + q * kThreads;
-      kq[q] = (idx < KK) ? idx / K : -1;
-      lq[q] = (idx < KK) ? idx - (idx / K) * K : 0;
-    }
-    stage_chunk(Hb, K, N, 0, min(kChunk, N), Hbuf0, KP);
-    for (int c = 0; c < nchunks; ++c) {
-      if (c + 1 < nchunks) {
-        const int n1 = (c + 1) * kChunk;
-        stage_chunk(Hb, K, N, n1, min(kChunk, N - n1), (c & 1) ? Hbuf0 : Hbuf1, KP);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      __syncthreads();
-      const cx<T>* hb = (c & 1) ? Hbuf1 : Hbuf0;
-      const int nc = min(kChunk, N - c * kChunk);
-      for (int n = 0; n < nc; ++n) {
-        const cx<T>* row = hb + n * KP;
-#pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
-          if (kq[q] >= 0) cfma_cj(acc[q], row[kq[q]], row[lq[q]]);
-        }
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < QMAX; ++q) {
-      const int idx = tid + q * kThreads;
-      if (idx < KK) G[idx] = acc[q];
-    }
-    __syncthreads();
-    // exact Hermitian symmetry and the regulariser: upper triangle wins
-    for (int idx = tid; idx < KK; idx += kThreads) {
-      const int k = idx / K, l = idx - k * K;
-      if (k > l) G[idx] = cconj(G[l * K + k]);
-    }
-    __syncthreads();
-    if (tid < K) G[tid * K + tid] = cmk<T>(G[tid * K + tid].re + alpha, T(0));
-    __syncthreads();
-  }
 
   // ---------------------------------------------------------------- 2. perturbation, state
   cx<T>* const Gsb = a.Gs + (size_t)b * KK;
@@ -678,6 +669,80 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_kernel(const StepArgs<T> 
     inf.status = status;
     a.info[b] = inf;
   }
+
+  return s;
+}
+
+// ------------------------------------------------------------------ the SIMT kernel
+// General path: any K <= kMaxK, complex64 or complex128, the Gram matrix and the precoder
+// computed with FP32 / FP64 fused multiply-adds from H staged by cp.async.
+template <class T>
+__global__ void __launch_bounds__(kThreads) wbrzf_step_kernel(const StepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int K = a.K, N = a.N, KK = K * K;
+  const int KP = K + 1;
+  cx<T>* const Hbuf0 = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* const Hbuf1 = Hbuf0 + kChunk * KP;
+  const Work<T> w = carve_work<T>(smem_raw + align_up(2 * (size_t)kChunk * KP * sizeof(cx<T>), 16),
+                                  K, a.dmax, a.rcap, nullptr, nullptr, nullptr);
+  cx<T>* const G = w.G;
+  const T alpha = a.alpha[b];
+  const cx<T>* __restrict__ Hb = a.H + (size_t)b * K * N;
+  const int nchunks = (N + kChunk - 1) / kChunk;
+
+  // ---------------------------------------------------------------- 1. Gram matrix
+  constexpr int QMAX = (kMaxK * kMaxK + kThreads - 1) / kThreads;
+  {
+    cx<T> acc[QMAX];
+    int kq[QMAX], lq[QMAX];
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+      acc[q] = cmk<T>(0, 0);
+      const int idx = tid + q * kThreads;
+      kq[q] = (idx < KK) ? idx / K : -1;
+      lq[q] = (idx < KK) ? idx - (idx / K) * K : 0;
+    }
+    stage_chunk(Hb, K, N, 0, min(kChunk, N), Hbuf0, KP);
+    for (int c = 0; c < nchunks; ++c) {
+      if (c + 1 < nchunks) {
+        const int n1 = (c + 1) * kChunk;
+        stage_chunk(Hb, K, N, n1, min(kChunk, N - n1), (c & 1) ? Hbuf0 : Hbuf1, KP);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const cx<T>* hb = (c & 1) ? Hbuf1 : Hbuf0;
+      const int nc = min(kChunk, N - c * kChunk);
+      for (int n = 0; n < nc; ++n) {
+        const cx<T>* row = hb + n * KP;
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+          if (kq[q] >= 0) cfma_cj(acc[q], row[kq[q]], row[lq[q]]);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+      const int idx = tid + q * kThreads;
+      if (idx < KK) G[idx] = acc[q];
+    }
+    __syncthreads();
+    // exact Hermitian symmetry and the regulariser: upper triangle wins
+    for (int idx = tid; idx < KK; idx += kThreads) {
+      const int k = idx / K, l = idx - k * K;
+      if (k > l) G[idx] = cconj(G[l * K + k]);
+    }
+    __syncthreads();
+    if (tid < K) G[tid * K + tid] = cmk<T>(G[tid * K + tid].re + alpha, T(0));
+    __syncthreads();
+  }
+
+  const T s = core_phases<T>(a, w, b);
+  cx<T>* const X = w.X;
 
   // ---------------------------------------------------------------- 7. precoder W = s H^H X
   {

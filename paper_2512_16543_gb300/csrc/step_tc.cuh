@@ -1,0 +1,400 @@
+// Tensor-core variant of the per-snapshot kernel (complex64, K <= 32, even N).
+//
+// Same steps and results as the SIMT kernel; the two dense contractions run on tcgen05:
+//
+//   Gram  G_t = H H^H.  For each block of 32 antennas a TMA load brings H[:, block] into a
+//         4-slot staging ring; the CTA splits it into four 32-row TF32 parts
+//         P = [Re_hi; Im_hi; Re_lo; Im_lo] (hi = round-to-nearest TF32 of the FP32 value,
+//         lo = TF32 of the remainder), stored K-major with the 128-byte swizzle, and one
+//         M = N = 128 MMA per 8-antenna step accumulates D = P P^T in tensor memory.  With
+//         Re = Re_hi + Re_lo and Im = Im_hi + Im_lo, Re G = Re Re^T + Im Im^T and
+//         Im G = Im Re^T - Re Im^T are sums of the 32 x 32 blocks of D, so the Gram matrix is
+//         accurate to FP32 rounding (the hi/lo split keeps 22 of FP32's 24 mantissa bits and
+//         the tensor cores accumulate in FP32) -- the precision dG = G_t - G_{t-1} needs.
+//   W = s H^H X.  Per 128-antenna M-tile the CTA writes H^T (antennas x interleaved users,
+//         TF32) and B = s [[Xr, Xi], [Xi, -Xr]] (interleaved, TF32), and one M = 128, N = 64
+//         MMA per 8-element step yields W's interleaved rows directly (TF32 inputs, FP32
+//         accumulation).
+//
+// The phases in between (dG, arSVD, Woodbury / direct inverse, scale, SINR) are the shared
+// SIMT code (core_phases).  Every wait on an mbarrier is bounded by a %globaltimer deadline;
+// a CTA whose wait expires records WBRZF_STATUS_TIMEOUT, stops waiting and still frees its
+// tensor memory before it exits.
+#pragma once
+#include <cuda.h>
+
+#include "step_kernel.cuh"
+
+namespace wbk {
+
+constexpr unsigned long long kWaitNs = 200000000ull;   // 200 ms per mbarrier wait
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of float k (0..31) of row r in a K-major tile of rows x 128 B, 128-byte swizzle
+__device__ __forceinline__ uint32_t sw128(int r, int k) {
+  const int r8 = r & 7;
+  return (uint32_t)((r >> 3) * 1024 + r8 * 128 + (((k >> 2) ^ r8) << 4) + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: next group of 8 rows
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: kind::tf32, FP32 accumulator, both operands K-major
+__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+
+// Wait for the phase with the given parity; false when the deadline passes (or an earlier
+// wait of this CTA already failed).
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort) {
+  if (*abort) return false;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    if (done) return true;
+    if (globaltimer() - t0 > kWaitNs) { *abort = 1; return false; }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x),
+      "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem), "l"(a),
+      "l"(b), "r"(id), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- the kernel
+__global__ void __launch_bounds__(kThreads) wbrzf_step_tc_kernel(
+    const StepArgs<float> a, const __grid_constant__ CUtensorMap hmap) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw_u = smem_u32(smem_raw);
+  unsigned char* const sm = smem_raw + ((1024 - (raw_u & 1023)) & 1023);
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K = a.K, N = a.N, KK = K * K;
+  const TcLayout Ly = tc_layout(K, a.dmax, a.rcap);
+  cx<float>* const G = reinterpret_cast<cx<float>*>(sm + Ly.oGXD);
+  cx<float>* const X = G + KK;
+  cx<float>* const Dm = X + KK;
+  unsigned char* const ring = sm + Ly.oRing;              // kStages x (32 rows x 256 B)
+  unsigned char* const uni = sm + Ly.oUnion;
+  uint64_t* const bars = reinterpret_cast<uint64_t*>(sm + Ly.oBar);
+  // bars[0..kStages): staging full; [kStages, kStages+2): Gram MMA done; [kStages+2]: W done
+  const uint32_t bar_full = smem_u32(bars), bar_mma = smem_u32(bars + kStages),
+                 bar_w = smem_u32(bars + kStages + 2);
+  volatile int* const abort_flag = reinterpret_cast<volatile int*>(bars + kStages + 3);
+  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bars + kStages + 4);
+  const int nblk = (N + 31) / 32;
+  const uint32_t tx_bytes = (uint32_t)K * 256u;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(bar_full + 8 * s, 1);
+    mbar_init(bar_mma, 1);
+    mbar_init(bar_mma + 8, 1);
+    mbar_init(bar_w, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int row0 = b * K;
+
+  auto issue_block = [&](int g) {      // g: running block index (Gram blocks, then W blocks)
+    const int s = g % kStages;
+    const int c = g < nblk ? g : g - nblk;
+    mbar_expect_tx(bar_full + 8 * s, tx_bytes);
+    tma_load_2d(smem_u32(ring + s * 8192), &hmap, 64 * c, row0, bar_full + 8 * s);
+  };
+
+  // ------------------------------------------------------------ 1. Gram on tensor cores
+  if (tid == 0) {
+    for (int g = 0; g < kStages && g < nblk; ++g) issue_block(g);
+  }
+  for (int c = 0; c < nblk; ++c) {
+    const int s = c % kStages, buf = c & 1;
+    mbar_wait(bar_full + 8 * s, (uint32_t)((c / kStages) & 1), abort_flag);
+    if (c >= 2) mbar_wait(bar_mma + 8 * buf, (uint32_t)(((c - 2) >> 1) & 1), abort_flag);
+    {
+      // split: thread -> (user k, 4 antennas q); parts Re_hi, Im_hi, Re_lo, Im_lo
+      const float* rawf = reinterpret_cast<const float*>(ring + s * 8192);
+      unsigned char* tile = uni + buf * 16384;
+      const int k = tid >> 3, q = tid & 7;
+      float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+      if (k < K) {
+        v0 = *reinterpret_cast<const float4*>(rawf + k * 64 + 8 * q);
+        v1 = *reinterpret_cast<const float4*>(rawf + k * 64 + 8 * q + 4);
+      }
+      const float re[4] = {v0.x, v0.z, v1.x, v1.z}, im[4] = {v0.y, v0.w, v1.y, v1.w};
+      float rh[4], ih[4], rl[4], il[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        rh[i] = tf32_rna(re[i]);
+        ih[i] = tf32_rna(im[i]);
+        rl[i] = tf32_rna(re[i] - rh[i]);
+        il[i] = tf32_rna(im[i] - ih[i]);
+      }
+      *reinterpret_cast<float4*>(tile + sw128(k, 4 * q)) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+      *reinterpret_cast<float4*>(tile + sw128(32 + k, 4 * q)) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+      *reinterpret_cast<float4*>(tile + sw128(64 + k, 4 * q)) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+      *reinterpret_cast<float4*>(tile + sw128(96 + k, 4 * q)) = make_float4(il[0], il[1], il[2], il[3]);
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      if (c + kStages < nblk) issue_block(c + kStages);
+      tc_fence_after();
+      const uint32_t id = idesc_tf32(128, 128);
+      const uint32_t tile = smem_u32(uni + buf * 16384);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t dsc = desc_sw128(tile + 32 * kk);
+        mma_tf32(tmem, dsc, dsc, id, (c > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(bar_mma + 8 * buf);
+    }
+  }
+  // W-phase prefetch: the staging ring is free once the last split has been read
+  if (tid == 0) {
+    for (int g = nblk; g < nblk + kStages && g < 2 * nblk; ++g) issue_block(g);
+  }
+  mbar_wait(bar_mma + 8 * ((nblk - 1) & 1), (uint32_t)(((nblk - 1) >> 1) & 1), abort_flag);
+  tc_fence_after();
+  {
+    // Gram epilogue.  Warp (quadrant qa = part a of the rows, half h) reads D rows 32a + k,
+    // column blocks 2h (a Re part) and 2h + 1 (an Im part).  Part a contributes
+    //   a even (Re_*): Re G += D[a][Re_*], Im G -= D[a][Im_*]
+    //   a odd  (Im_*): Re G += D[a][Im_*], Im G += D[a][Re_*]
+    // Partial sums go to one slice per part (h = 0 writes, h = 1 adds), then a fixed-order
+    // sum over the four slices keeps the result deterministic.
+    const int qa = warp & 3, h = warp >> 2, k = lane;
+    float* slice = reinterpret_cast<float*>(uni) + (size_t)qa * 2 * KK;   // interleaved re/im
+    const bool odd = qa & 1;
+    // block 2h (a Re part): Re G if a is even, Im G if a is odd (sign +)
+    // block 2h + 1 (an Im part): Im G with sign - if a is even, Re G if a is odd
+    for (int pass = 0; pass < 2; ++pass) {
+      if (h == pass) {
+        for (int blk = 0; blk < 2; ++blk) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * qa) << 16) + (uint32_t)(64 * h + 32 * blk), v);
+          const int comp = (blk == 0) ? (odd ? 1 : 0) : (odd ? 0 : 1);   // 0: re, 1: im
+          const float sgn = (blk == 1 && !odd) ? -1.f : 1.f;
+          if (k < K) {
+#pragma unroll
+            for (int l = 0; l < 32; ++l) {
+              if (l < K) {
+                float* dst = slice + 2 * (k * K + l) + comp;
+                *dst = (pass == 0 ? 0.f : *dst) + sgn * v[l];
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+    }
+    const cx<float>* sl = reinterpret_cast<const cx<float>*>(uni);
+    for (int idx = tid; idx < KK; idx += kThreads) {
+      cx<float> gsum = cadd(cadd(sl[idx], sl[KK + idx]), cadd(sl[2 * KK + idx], sl[3 * KK + idx]));
+      G[idx] = gsum;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < KK; idx += kThreads) {
+      const int kr = idx / K, l = idx - kr * K;
+      if (kr > l) G[idx] = cconj(G[l * K + kr]);
+    }
+    __syncthreads();
+    if (tid < K) G[tid * K + tid] = cmk(G[tid * K + tid].re + a.alpha[b], 0.f);
+    __syncthreads();
+  }
+
+  // ------------------------------------------------------------ 2-6. shared SIMT phases
+  const Work<float> w = carve_work<float>(uni, K, a.dmax, a.rcap, G, X, Dm);
+  const float s = core_phases<float>(a, w, b);
+  __syncthreads();
+
+  // ------------------------------------------------------------ 7. W = s H^H X on tensor cores
+  {
+    unsigned char* const At = uni;              // 2 K-blocks x 128 rows x 128 B
+    unsigned char* const Bt = uni + 32768;      // 2 K-blocks x 64 rows x 128 B
+    // B[(j, c')][(k, c)]: rows 2j (Re W), 2j + 1 (Im W); columns 2k (Re H), 2k + 1 (Im H)
+    for (int e = tid; e < 64 * 16; e += kThreads) {
+      const int row = e >> 4, qq = e & 15;            // 16 chunks of 4 floats per row
+      const int j = row >> 1, cre = row & 1;
+      float v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int kf = 4 * qq + i, k = kf >> 1, c = kf & 1;
+        float val = 0.f;
+        if (j < K && k < K) {
+          const cx<float> x = X[k * K + j];
+          val = cre == 0 ? (c == 0 ? x.re : x.im) : (c == 0 ? x.im : -x.re);
+          val = tf32_rna(s * val);
+        }
+        v[i] = val;
+      }
+      const int kb = qq >> 3, kin = 4 * (qq & 7);
+      *reinterpret_cast<float4*>(Bt + kb * 8192 + sw128(row, kin)) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    const int nmt = (N + 127) / 128;
+    cx<float>* const Wb = a.W + (size_t)b * N * K;
+    for (int mt = 0; mt < nmt; ++mt) {
+      for (int qd = 0; qd < 4; ++qd) {
+        const int c = 4 * mt + qd;
+        if (c < nblk) {
+          const int g = nblk + c, sl = g % kStages;
+          mbar_wait(bar_full + 8 * sl, (uint32_t)((g / kStages) & 1), abort_flag);
+          const float* rawf = reinterpret_cast<const float*>(ring + sl * 8192);
+          // warp -> users k = warp + 8 i, lane -> antenna n of this block
+          for (int i = 0; i < 4; ++i) {
+            const int k = warp + 8 * i;
+            float2 hv = make_float2(0.f, 0.f);
+            if (k < K) hv = *reinterpret_cast<const float2*>(rawf + k * 64 + 2 * lane);
+            const int row = 32 * qd + lane, kf = 2 * k;
+            *reinterpret_cast<float2*>(At + (kf >> 5) * 16384 + sw128(row, kf & 31)) =
+                make_float2(tf32_rna(hv.x), tf32_rna(hv.y));
+          }
+          __syncthreads();
+          if (tid == 0 && g + kStages < 2 * nblk) issue_block(g + kStages);
+        } else {
+          for (int i = 0; i < 4; ++i) {
+            const int k = warp + 8 * i, row = 32 * qd + lane, kf = 2 * k;
+            *reinterpret_cast<float2*>(At + (kf >> 5) * 16384 + sw128(row, kf & 31)) =
+                make_float2(0.f, 0.f);
+          }
+        }
+      }
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t id = idesc_tf32(128, 64);
+        const uint32_t at = smem_u32(At), bt = smem_u32(Bt);
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks) {
+          const uint64_t ad = desc_sw128(at + (ks >> 2) * 16384 + 32 * (ks & 3));
+          const uint64_t bd = desc_sw128(bt + (ks >> 2) * 8192 + 32 * (ks & 3));
+          mma_tf32(tmem, ad, bd, id, ks > 0 ? 1u : 0u);
+        }
+        mma_commit(bar_w);
+      }
+      mbar_wait(bar_w, (uint32_t)(mt & 1), abort_flag);
+      tc_fence_after();
+      {
+        const int qa = warp & 3, h = warp >> 2;
+        const int n = 128 * mt + 32 * qa + lane;
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * qa) << 16) + (uint32_t)(32 * h), v);
+        if (n < N) {
+          cx<float>* wr = Wb + (size_t)n * K;
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = 16 * h + jj;
+            if (j < K) wr[j] = cmk(v[2 * jj], v[2 * jj + 1]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+    }
+  }
+
+  // ------------------------------------------------------------ teardown
+  if (*abort_flag && tid == 0) a.info[b].status |= WBRZF_STATUS_TIMEOUT;
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
+  }
+}
+
+}  // namespace wbk

@@ -5,6 +5,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 #include <new>
 
 #include "step_common.cuh"
@@ -92,6 +96,21 @@ bool resolve_rule(const wbrzf_rank_rule* rule, int K, Resolved* out) {
 
 }  // namespace
 
+// cuTensorMapEncodeTiled from the driver, looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
 struct wbrzf {
   int batch, N, K;
   wbrzf_precision prec;
@@ -107,6 +126,9 @@ struct wbrzf {
   unsigned char* trace;
   size_t trace_stride;
   long long launches;
+  int engine;            // WBRZF_ENGINE_* requested
+  int last_engine;       // kernel of the last launch
+  size_t smem_tc;        // dynamic shared memory of the tensor-core kernel (0: not eligible)
 };
 
 namespace {
@@ -146,17 +168,44 @@ StepArgs<T> make_args(const wbrzf* h, const void* H, void* W, int mode, int t) {
   return a;
 }
 
+// Tensor-core kernel eligibility that depends on the handle only.
+bool tc_eligible(const wbrzf* h) {
+  return h->prec == WBRZF_C64 && h->K <= 32 && (h->N % 2) == 0 && h->smem_tc > 0;
+}
+
+// H as a 2-D FP32 tensor {2N, batch K}, box {64, K} (32 antennas of every user).
+bool encode_hmap(const wbrzf* h, const void* H, CUtensorMap* map) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * h->N, (cuuint64_t)h->batch * h->K};
+  const cuuint64_t strides[1] = {(cuuint64_t)8 * h->N};
+  const cuuint32_t box[2] = {64, (cuuint32_t)h->K};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(H), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
   if (!h || !H || !W) return WBRZF_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(H) | reinterpret_cast<uintptr_t>(W)) % cx_bytes(h->prec))
     return WBRZF_ERR_INVALID_ARG;
   cudaError_t e;
-  if (h->prec == WBRZF_C128) {
+  bool use_tc = h->engine != WBRZF_ENGINE_SIMT && tc_eligible(h) &&
+                (reinterpret_cast<uintptr_t>(H) % 16) == 0;
+  alignas(64) CUtensorMap map;
+  if (use_tc && !encode_hmap(h, H, &map)) use_tc = false;
+  if (h->engine == WBRZF_ENGINE_TENSOR && !use_tc) return WBRZF_ERR_UNSUPPORTED;
+  if (use_tc) {
+    e = launch_step_tc(make_args<float>(h, H, W, mode, h->t), &map, h->smem_tc, h->stream);
+  } else if (h->prec == WBRZF_C128) {
     e = launch_step_f64(make_args<double>(h, H, W, mode, h->t), h->smem, h->stream);
   } else {
     e = launch_step_f32(make_args<float>(h, H, W, mode, h->t), h->smem, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(e);
+  h->last_engine = use_tc ? WBRZF_ENGINE_TENSOR : WBRZF_ENGINE_SIMT;
   h->launches += 1;
   h->t += 1;
   return WBRZF_OK;
@@ -197,8 +246,8 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   if (!resolve_rule(rule, K, &r)) return WBRZF_ERR_INVALID_ARG;
   const WsLayout wl = ws_layout(batch, K, prec);
   if (workspace_bytes < wl.bytes) return WBRZF_ERR_WORKSPACE;
-  const Layout sl = make_layout(K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec));
-  if (sl.bytes > 227 * 1024) return WBRZF_ERR_UNSUPPORTED;
+  const size_t smem = simt_smem_bytes(K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec));
+  if (smem > 227 * 1024) return WBRZF_ERR_UNSUPPORTED;
 
   wbrzf* h = new (std::nothrow) wbrzf;
   if (!h) return WBRZF_ERR_INVALID_ARG;
@@ -214,10 +263,16 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   h->wl = wl;
   h->t = 0;
   h->initialized = false;
-  h->smem = sl.bytes;
+  h->smem = smem;
   h->trace = nullptr;
   h->trace_stride = trace_record_bytes(K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec));
   h->launches = 0;
+  h->engine = WBRZF_ENGINE_AUTO;
+  h->last_engine = 0;
+  {
+    const size_t tc = tc_smem_bytes(K, r.dmax, r.rcap);
+    h->smem_tc = (prec == WBRZF_C64 && K <= 32 && tc <= 227 * 1024) ? tc : 0;
+  }
 
   // per-instance parameters in the kernel's real type
   const size_t rb = re_bytes(prec);
@@ -324,6 +379,16 @@ wbrzf_status wbrzf_set_instance_ids(wbrzf* h, const uint32_t* ids, int count) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
 }
+
+wbrzf_status wbrzf_set_engine(wbrzf* h, int engine) {
+  if (!h || engine < WBRZF_ENGINE_AUTO || engine > WBRZF_ENGINE_TENSOR)
+    return WBRZF_ERR_INVALID_ARG;
+  if (engine == WBRZF_ENGINE_TENSOR && !tc_eligible(h)) return WBRZF_ERR_UNSUPPORTED;
+  h->engine = engine;
+  return WBRZF_OK;
+}
+
+int wbrzf_last_engine(const wbrzf* h) { return h ? h->last_engine : 0; }
 
 wbrzf_status wbrzf_set_stream(wbrzf* h, void* cuda_stream) {
   if (!h) return WBRZF_ERR_INVALID_ARG;

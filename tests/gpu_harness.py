@@ -24,12 +24,14 @@ def oracle_rule(rule: binding.RankRule) -> om.RankRule:
 
 
 def run_gpu(Hs: torch.Tensor, alpha, sigma2, p_t, rule: binding.RankRule, *, precision="c64",
-            method="wb", ids=None, trace=False, keep_state=True, device="cuda"):
+            method="wb", ids=None, trace=False, keep_state=True, device="cuda", engine="auto"):
     """Hs: [T, B, K, N] complex tensor (any device).  Returns a list of per-step dicts."""
     T, B, K, N = Hs.shape
     dt = torch.complex64 if precision == "c64" else torch.complex128
     h = binding.WBRZF(B, N, K, alpha, sigma2, p_t=p_t, rule=rule, method=method,
                       precision=precision, device=device)
+    if engine != "auto":
+        h.set_engine(engine)
     if ids is not None:
         h.set_instance_ids(ids)
     if trace:
@@ -53,7 +55,7 @@ def run_gpu(Hs: torch.Tensor, alpha, sigma2, p_t, rule: binding.RankRule, *, pre
             rec["Rh"] = Rh.cpu().numpy()
         out.append(rec)
     torch.cuda.synchronize()
-    rec0 = {"launches": h.launches, "rcap": rcap, "dmax": dmax}
+    rec0 = {"launches": h.launches, "rcap": rcap, "dmax": dmax, "engine": h.last_engine}
     h.close()
     return out, rec0
 

@@ -3,6 +3,10 @@
 Tolerances (relative Frobenius errors of X = G^-1 and W, absolute sum-rate gaps):
   * complex128 path: FP64 on both sides, every branch and rank identical, X and W within
     1e-10, sum-rate within 1e-9 bit/s/Hz.
+  * complex64, tensor-core engine: the Gram matrix uses the hi/lo TF32 split (FP32-faithful,
+    same X tolerance); the precoder product H^H X takes TF32 inputs (unit roundoff 2^-11 per
+    operand, FP32 accumulation), so W is held to 2e-3 instead of 1e-4.  The SINR and sum-rate
+    come from G and X, not from W, and keep the FP32 tolerance.
   * complex64 path: FP32 arithmetic.  The Gram matrix is accumulated in FP32 (u = 6e-8), so
     dG = G_t - G_{t-1} (about 5e-5 of ||G|| per 10 ms step on these channels) carries a
     relative error of a few 1e-3; through the Woodbury chain and the periodic re-inversion X
@@ -28,10 +32,10 @@ def _traj(sc, B, T, seed, t0=0):
 
 
 def _check(gpu, Hs, sc, rule, prec, *, ids=None, r_tie_tol=1e-3, x_tol=None, w_tol=None,
-           rate_tol=None, alpha=None, sigma2=None, method="wb"):
+           rate_tol=None, alpha=None, sigma2=None, method="wb", engine="simt"):
     T, B = Hs.shape[:2]
     x_tol = x_tol or (1e-10 if prec == "c128" else 1e-4)
-    w_tol = w_tol or (1e-10 if prec == "c128" else 1e-4)
+    w_tol = w_tol or (1e-10 if prec == "c128" else (2e-3 if engine == "tensor" else 1e-4))
     rate_tol = rate_tol or (1e-9 if prec == "c128" else 1e-3)
     alpha = sc.alpha if alpha is None else alpha
     sigma2 = sc.sigma2 if sigma2 is None else sigma2
@@ -101,21 +105,43 @@ def test_lowrank_factors_match_oracle(eta):
     assert nwb > 10
 
 
-def test_batched_shapes_complex64():
-    """16x16 UPA, K = 32, p = 8, r <= 16: FP32 path against the oracle."""
+@pytest.mark.parametrize("engine", ["simt", "tensor"])
+def test_batched_shapes_complex64(engine):
+    """16x16 UPA, K = 32, p = 8, r <= 16: FP32 path against the oracle, on both engines."""
     sc = channel.scenario_batched_256x32()
     Hs = _traj(sc, 3, 30, seed=303)
     rule = binding.RankRule(eta=0.9, k_init=2, p=8, r_max=16, reinverse_period=20, seed=5)
-    gpu, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64")
-    mism = _check(gpu, Hs, sc, rule, "c64")
+    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64", engine=engine)
+    assert meta["engine"] == engine
+    mism = _check(gpu, Hs, sc, rule, "c64", engine=engine)
     assert mism <= 3
 
 
+def test_engines_agree():
+    """The tensor-core and FMA kernels agree on the same snapshots: branches and ranks, X to
+    the FP32 level, W to the TF32 level."""
+    sc = channel.scenario_batched_256x32()
+    Hs = _traj(sc, 4, 25, seed=313)
+    rule = binding.RankRule(eta=0.8, k_init=2, p=8, r_max=16, reinverse_period=20, seed=6)
+    g1, m1 = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, engine="simt")
+    g2, m2 = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, engine="tensor")
+    assert m1["engine"] == "simt" and m2["engine"] == "tensor"
+    same = 0
+    for a, b in zip(g1, g2):
+        for i in range(4):
+            same += a["info"][i]["r"] == b["info"][i]["r"]
+            assert relerr(b["X"][i], a["X"][i]) < 1e-4
+            assert relerr(b["W"][i], a["W"][i]) < 2e-3
+            assert abs(a["rate"][i] - b["rate"][i]) < 1e-3
+    assert same >= 0.95 * 25 * 4
+
+
 @pytest.mark.parametrize("K,N", [(1, 5), (3, 1), (5, 37), (17, 100), (32, 33), (64, 96),
-                                 (8, 1000)])
-@pytest.mark.parametrize("prec", ["c128", "c64"])
-def test_edge_shapes(K, N, prec):
-    """Ragged N (not a multiple of the 32-column staging chunk), K > N, K = 1, K = 64."""
+                                 (8, 1000), (2, 2), (31, 290), (32, 160)])
+@pytest.mark.parametrize("prec,engine", [("c128", "simt"), ("c64", "simt"), ("c64", "tensor")])
+def test_edge_shapes(K, N, prec, engine):
+    """Ragged N (not a multiple of the 32-column staging chunk or of the 128-antenna tile),
+    K > N, K = 1, K = 64; the tensor engine needs K <= 32 and even N and must refuse others."""
     sc = channel.LeoScenario(n_x=N, n_y=1, K=K, disc_radius=50e3)
     Hs = _traj(sc, 2, 6, seed=400 + K + N)
     rule = binding.RankRule(eta=0.9, k_init=2, p=2, r_max=min(K, 16), reinverse_period=4,
@@ -127,8 +153,14 @@ def test_edge_shapes(K, N, prec):
             run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec)
         assert e.value.code == 6
         return
-    gpu, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec)
-    _check(gpu, Hs, sc, rule, prec)
+    if engine == "tensor" and (K > 32 or N % 2):
+        with pytest.raises(binding.WbrzfError) as e:
+            run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec, engine=engine)
+        assert e.value.code == 6
+        return
+    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec, engine=engine)
+    assert meta["engine"] == engine
+    _check(gpu, Hs, sc, rule, prec, engine=engine)
 
 
 def test_keep_branch_on_unchanged_channel():
@@ -161,12 +193,13 @@ def test_full_inversion_method_matches_oracle():
     sc = channel.scenario_batched_256x32()
     Hs = _traj(sc, 2, 4, seed=6)
     rule = binding.RankRule()
-    gpu, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64", method="full",
-                     keep_state=False)
-    for t in range(4):
-        for b in range(2):
-            assert gpu[t]["info"][b]["branch"] == 5
-    _check(gpu, Hs, sc, rule, "c64", method="full")
+    for engine in ("simt", "tensor"):
+        gpu, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64", method="full",
+                         keep_state=False, engine=engine)
+        for t in range(4):
+            for b in range(2):
+                assert gpu[t]["info"][b]["branch"] == 5
+        _check(gpu, Hs, sc, rule, "c64", method="full", engine=engine)
 
 
 def test_rank_switch_forces_direct_inverse():
@@ -180,14 +213,16 @@ def test_rank_switch_forces_direct_inverse():
         assert np.max(np.abs(gpu[t]["X"][0] @ A - np.eye(sc.K))) < 1e-11
 
 
-def test_batch_invariance_with_instance_ids():
+@pytest.mark.parametrize("engine", ["simt", "tensor"])
+def test_batch_invariance_with_instance_ids(engine):
     """An instance gives the same bits alone and inside a batch (same identity)."""
     sc = channel.scenario_batched_256x32()
     Hs = _traj(sc, 5, 6, seed=12).to(torch.complex64)
     rule = binding.RankRule(eta=0.8, k_init=2, p=8, r_max=16, seed=9)
     ids = [40, 41, 42, 43, 44]
-    batch, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, ids=ids)
-    alone, _ = run_gpu(Hs[:, 3:4].contiguous(), sc.alpha, sc.sigma2, sc.p_t, rule, ids=[43])
+    batch, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, ids=ids, engine=engine)
+    alone, _ = run_gpu(Hs[:, 3:4].contiguous(), sc.alpha, sc.sigma2, sc.p_t, rule, ids=[43],
+                       engine=engine)
     for t in range(6):
         np.testing.assert_array_equal(batch[t]["W"][3], alone[t]["W"][0])
         np.testing.assert_array_equal(batch[t]["X"][3], alone[t]["X"][0])
@@ -237,11 +272,12 @@ def test_full_size_batched_sampled_parity():
         rates_s.append(rate[sample].cpu().numpy())
     info = h.step_info()
     assert all(i["status"] == 0 for i in info)
+    assert h.last_engine == "tensor"
     h.close()
     Hs = torch.stack(Hs_s)
     for j, b in enumerate(sample):
         ref = run_oracle(Hs[:, j].numpy().astype(np.complex128), sc.alpha, sc.sigma2, sc.p_t,
                          rule, instance=b)
         for t in range(T):
-            assert relerr(Ws_s[t][j], ref[t].W) < 1e-4
+            assert relerr(Ws_s[t][j], ref[t].W) < 2e-3
             assert abs(rates_s[t][j] - ref[t].sum_rate) < 1e-3

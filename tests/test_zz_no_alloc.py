@@ -5,7 +5,8 @@ plug-ins whose framework owns all device memory) get the conventional full-inver
 result without handing the library a workspace: the per-instance scratch comes from a fixed
 array inside the library.  This test calls the entry point through the C ABI twice in a row
 on different channels and checks each result against the workspace-based entry point
-(a WBRZF_METHOD_FULL_INVERSE handle), within the tolerances the other parity tests use.
+(a WBRZF_METHOD_FULL_INVERSE handle on the FMA engine, the kernel both share), within the
+tolerances the other parity tests use.
 It lives in its own file so that it is collected last.
 """
 import ctypes
@@ -45,6 +46,7 @@ def test_noalloc_matches_workspace_entry_point_twice(prec, shape):
     params = channel.draw_trajectories(sc, B, seed=31 + K)
     ref = binding.WBRZF(B, N, K, sc.alpha, sc.sigma2, p_t=sc.p_t, method="full",
                         precision=prec)
+    ref.set_engine("simt")               # the kernel the allocation-free call runs
     for t in (0, 40):                    # two calls in a row, different channels
         H = channel.channel_at(params, t, device="cuda", dtype=dt)
         code, W, rate = _noalloc(H, sc.alpha, sc.sigma2, sc.p_t, prec)
