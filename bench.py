@@ -36,14 +36,20 @@ BATCH, NX, K_USERS = 1024, 16, 32
 ETA_GRID = (0.65, 0.8, 0.9, 0.95, 0.99)
 RATE_GAP_BOUND = 0.05        # bit/s/Hz, mean |R_WB - R_full|
 
-# DRAM traffic of the step kernel per launch from the committed ncu capture, valid only for
-# the kernel source it was taken on (sha256 of step_kernel.cuh, first 16 hex digits).
-NCU_TRAFFIC = {"source_sha": None, "bytes_per_launch": None}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one WB-arSVD launch of the
+# tensor-core step kernel on this workload, from the ncu capture summarised in
+# profiles/step_tc_kernel_batched_256x32.md; reported only while the kernel source is the one
+# the counters were taken on (sha256 of its three source files, first 16 hex digits).
+NCU_TRAFFIC = {"source_sha": "527dc8294fe20cc2", "bytes_per_launch": 120865792}
+KERNEL_SOURCES = ("step_common.cuh", "step_kernel.cuh", "step_tc.cuh")
 
 
 def kernel_source_sha() -> str:
-    p = os.path.join(ROOT, "paper_2512_16543_gb300", "csrc", "step_kernel.cuh")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2512_16543_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def algorithmic_bytes_per_update(N: int, K: int, method: str) -> int:
@@ -191,13 +197,8 @@ def dist_setup():
 
 
 def barrier_max(value: float, world: int) -> float:
-    if world == 1:
-        return value
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2512_16543_gb300 import sharding
+    return float(value) if world == 1 else sharding.max_over_ranks(value, device="cuda")
 
 
 def run_reference(args):
@@ -246,7 +247,8 @@ def main():
     W_, K_ = args.warmup, args.steps
     assert W_ >= 3, "at least 3 warm-up steps"
     params = channel.draw_trajectories(sc, B, seed=args.seed + 7919 * rank)
-    ids = [rank * B + b for b in range(B)]
+    from paper_2512_16543_gb300 import sharding
+    ids = sharding.shard_ids(rank, world, B)
     T = 1 + W_ + K_
     Hs = torch.stack([channel.channel_at(params, t, device=dev, dtype=torch.complex64)
                       for t in range(T)])                    # [T, B, K, N] resident in HBM

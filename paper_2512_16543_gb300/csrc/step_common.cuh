@@ -54,11 +54,22 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 // (rank rcap), then real scratch (reductions, eigenvalues, rotations, column norms), integer
 // scratch (permutation, pairs, drop flags, flags) and the rotation phases.  The device-side
 // carve-up (carve_work) follows exactly this order.
+// Regions that are dead by the time the Woodbury buffers are written are reused:
+// R^H (rcap x K) takes the place of Y^H Y / B B^H, T (K x rcap) that of Q, and [C | Z]
+// (rcap x (rcap + K)) that of B.
+__host__ __device__ inline size_t work_region_gy(int K, int dmax, int rcap) {
+  const size_t a = (size_t)dmax * dmax, b = (size_t)rcap * K;
+  return a > b ? a : b;
+}
+__host__ __device__ inline size_t work_region_b(int K, int dmax, int rcap) {
+  const size_t a = (size_t)dmax * K, b = (size_t)rcap * (rcap + K);
+  return a > b ? a : b;
+}
 __host__ __device__ inline size_t work_bytes(int K, int dmax, int rcap, bool with_gxd,
                                              size_t cx_bytes, size_t t_bytes) {
   const size_t n = (with_gxd ? 3 * (size_t)K * K : 0) + 2 * (size_t)K * dmax +
-                   2 * (size_t)dmax * dmax + (size_t)dmax * K + 2 * (size_t)rcap * K +
-                   (size_t)rcap * (rcap + K) + 2 * (size_t)K + 2;
+                   work_region_gy(K, dmax, rcap) + work_region_b(K, dmax, rcap) +
+                   (size_t)dmax * dmax + (2 * (size_t)K + 2 > 64 ? 2 * (size_t)K + 2 : 64);
   size_t bytes = align_up(n * cx_bytes, 16);
   bytes += align_up((40 + 4 * (size_t)dmax) * t_bytes, 16);
   bytes += align_up((4 * (size_t)dmax + 16) * sizeof(int), 16);
@@ -74,26 +85,36 @@ __host__ __device__ inline size_t simt_smem_bytes(int K, int dmax, int rcap, siz
 }
 
 // ---------------------------------------------------------------- tensor-core kernel plan
-constexpr int kStages = 4;                    // TMA staging ring depth (blocks of 32 antennas)
+constexpr int kStages = 2;                    // TMA staging ring depth (blocks of 32 antennas)
 constexpr uint32_t kTmemCols = 128;           // Gram D: 128 x 128; W D: 128 x 64
 
-// ---------------------------------------------------------------- shared-memory plan
+// Shared memory of the tensor-core kernel (offsets from a 1024-byte aligned base):
+//   GXD   G (K x K) at 0, dG right after it, X at the end of the region; after the SINR phase
+//         the first 16 KiB hold the B tile of the precoder product (G and dG are dead, X is
+//         read while B is written, so the region is at least 16 KiB + K^2 complex)
+//   ring  kStages TMA slots of 32 users x 32 antennas (8 KiB each)
+//   union Gram tiles (2 x 16 KiB) / Gram epilogue slices / SIMT workspace / H^T tile (32 KiB)
 struct TcLayout {
-  size_t oGXD, oRing, oUnion, oBar, bytes_unpadded, union_bytes;
+  size_t oGXD, gxd_bytes, oX, oRing, oUnion, oBar, bytes_unpadded, union_bytes;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int K, int dmax, int rcap) {
   TcLayout L;
-  size_t o = 0;
-  L.oGXD = o;   o = align_up(o + 3 * (size_t)K * K * 8, 1024);
+  const size_t kk8 = (size_t)K * K * 8;
+  size_t g = 3 * kk8;
+  if (16384 + kk8 > g) g = 16384 + kk8;
+  L.gxd_bytes = align_up(g, 1024);
+  L.oGXD = 0;
+  L.oX = L.gxd_bytes - kk8;
+  size_t o = L.gxd_bytes;
   L.oRing = o;  o = align_up(o + (size_t)kStages * 32 * 256, 1024);
   L.oUnion = o;
   size_t u = 2 * 16384;                                   // Gram: two 128 x 128 B tiles
   const size_t wk = work_bytes(K, dmax, rcap, false, 8, 4);
   if (wk > u) u = wk;
-  if (4 * (size_t)K * K * 8 > u) u = 4 * (size_t)K * K * 8;   // Gram epilogue partials
-  if (32768 + 16384 > u) u = 32768 + 16384;               // W: A tile + B tile
-  L.union_bytes = align_up(u, 1024);
+  const size_t sl = 2 * (size_t)K * (K + 1) * 8;          // Gram epilogue: two padded slices
+  if (sl > u) u = sl;
+  L.union_bytes = align_up(u, 1024);                      // (>= the 32 KiB H^T tile)
   o += L.union_bytes;
   L.oBar = o;   o += 256;
   L.bytes_unpadded = o;

@@ -49,8 +49,8 @@ template <class T> __device__ __forceinline__ void cfma_jc(cx<T>& acc, cx<T> a, 
   acc.im = fma(a.re, b.im, acc.im); acc.im = fma(-a.im, b.re, acc.im);
 }
 template <class T> __device__ __forceinline__ cx<T> crecip(cx<T> a) {
-  T n = a.re * a.re + a.im * a.im;
-  return cmk(a.re / n, -a.im / n);
+  const T n = T(1) / (a.re * a.re + a.im * a.im);
+  return cmk(a.re * n, -a.im * n);
 }
 template <class T> __device__ __forceinline__ bool cfinite(cx<T> a) { return isfinite(a.re) && isfinite(a.im); }
 
@@ -176,15 +176,15 @@ __device__ inline Work<T> carve_work(unsigned char* base, int K, int dmax, int r
   const size_t KK = (size_t)K * K;
   if (G == nullptr) { G = c; c += KK; X = c; c += KK; D = c; c += KK; }
   w.G = G; w.X = X; w.D = D;
-  w.Om = c; c += (size_t)K * dmax;
-  w.Q = c; c += (size_t)K * dmax;
-  w.Gy = c; c += (size_t)dmax * dmax;
-  w.Bm = c; c += (size_t)dmax * K;
+  w.Om = c; c += (size_t)K * dmax;          // Omega, later L (K x rcap)
+  w.Q = c; c += (size_t)K * dmax;           // Y, Q, later T (K x rcap)
+  w.Gy = c; c += work_region_gy(K, dmax, rcap);   // Y^H Y, B B^H, later R^H
+  w.Bm = c; c += work_region_b(K, dmax, rcap);    // B, later [C | Z]
   w.Uh = c; c += (size_t)dmax * dmax;
-  w.Rh = c; c += (size_t)rcap * K;
-  w.Tm = c; c += (size_t)K * rcap;
-  w.CZ = c; c += (size_t)rcap * (rcap + K);
-  w.tmp = c; c += 2 * (size_t)K + 2;
+  w.Rh = w.Gy;
+  w.Tm = w.Q;
+  w.CZ = w.Bm;
+  w.tmp = c; c += (2 * (size_t)K + 2 > 64 ? 2 * (size_t)K + 2 : 64);
   unsigned char* p = reinterpret_cast<unsigned char*>(base) +
                      align_up((size_t)(c - reinterpret_cast<cx<T>*>(base)) * sizeof(cx<T>), 16);
   w.red = reinterpret_cast<T*>(p);
@@ -205,12 +205,30 @@ __device__ inline Work<T> carve_work(unsigned char* base, int K, int dmax, int r
   return w;
 }
 
+// Start copying the resident G_{t-1} into D and X_{t-1} into X (one cp.async group); the
+// caller waits for it before core_phases.
+template <class T>
+__device__ __forceinline__ void prefetch_state(const StepArgs<T>& a, int b, cx<T>* D, cx<T>* X) {
+  if (a.mode == MODE_UPDATE) {
+    const size_t KK = (size_t)a.K * a.K;
+    const cx<T>* Gs = a.Gs + (size_t)b * KK;
+    const cx<T>* Xs = a.Xs + (size_t)b * KK;
+    for (int idx = threadIdx.x; idx < (int)KK; idx += kThreads) {
+      cp_async<sizeof(cx<T>)>(&D[idx], &Gs[idx]);
+      cp_async<sizeof(cx<T>)>(&X[idx], &Xs[idx]);
+    }
+  }
+  cp_async_commit();
+}
+
 // ------------------------------------------------------------------ phases 2-6
 // Given G_t in w.G (Hermitian, alpha on the diagonal), run the perturbation, the low-rank
 // step, the Woodbury update or direct inverse, the state write-back, the power scale and the
 // SINR / sum-rate.  Leaves X in w.X and returns the precoder scale s.
 template <class T>
 __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
+  // On entry for MODE_UPDATE, w.D holds G_{t-1} and w.X holds X_{t-1}: the kernels copy them
+  // from the resident state with cp.async (prefetch_state) while the Gram matrix is formed.
   const int tid = threadIdx.x;
   const int K = a.K, KK = K * K;
   cx<T>* const G = w.G;
@@ -251,9 +269,8 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
     T s_dg = 0, s_g = 0;
     for (int idx = tid; idx < KK; idx += kThreads) {
       const cx<T> g = G[idx];
-      const cx<T> d = csub(g, Gsb[idx]);
+      const cx<T> d = csub(g, D[idx]);
       D[idx] = d;
-      X[idx] = Xsb[idx];
       Gsb[idx] = g;
       s_dg += cabs2(d);
       s_g += cabs2(g);
@@ -310,43 +327,56 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       for (int pass = 0; pass < 2; ++pass) {
         mm<T, true, false, MM_SET>(d, d, K, Q, dmax, Q, dmax, Gy, dmax);   // Y^H Y
         __syncthreads();
-        if (tid < d) cn[tid] = Gy[tid * dmax + tid].re;
-        __syncthreads();
-        // right-looking Cholesky Gy = R^H R (R upper, stored in the upper triangle)
-        for (int j = 0; j < d; ++j) {
-          if (tid == 0) {
+        if (tid < 32) {   // one warp factors the d x d Gram matrix; lane c owns column c
+          const int cl = tid;
+          if (cl < d) cn[cl] = Gy[cl * dmax + cl].re;
+          __syncwarp();
+          // right-looking Cholesky Gy = R^H R (R upper, stored in the upper triangle)
+          for (int j = 0; j < d; ++j) {
             const T piv = Gy[j * dmax + j].re;
             const bool dj = drop[j] || !(cn[j] > T(0)) || !(piv > tol_rel * cn[j]) || !isfinite(piv);
-            drop[j] = dj ? 1 : 0;
-            rc[0] = dj ? T(0) : sqrt(piv);
-          }
-          __syncthreads();
-          const T rjj = rc[0];
-          for (int c = j + tid; c < d; c += kThreads) {
-            Gy[j * dmax + c] = (rjj > T(0)) ? cscale(Gy[j * dmax + c], T(1) / rjj) : cmk<T>(0, 0);
-          }
-          __syncthreads();
-          const int m = d - j - 1;
-          for (int e = tid; e < m * m; e += kThreads) {
-            const int ai = j + 1 + e / m, ci = j + 1 + e % m;
-            if (ai <= ci) {
-              cx<T> v = Gy[ai * dmax + ci];
-              cfma_jc(v, cscale(Gy[j * dmax + ai], T(-1)), Gy[j * dmax + ci]);
-              Gy[ai * dmax + ci] = v;
+            const T rinv = dj ? T(0) : T(1) / sqrt(piv);
+            __syncwarp();
+            if (cl == 0) { drop[j] = dj ? 1 : 0; rs[j] = rinv; }
+            if (cl >= j && cl < d) Gy[j * dmax + cl] = cscale(Gy[j * dmax + cl], rinv);
+            __syncwarp();
+            if (cl > j && cl < d) {
+              const cx<T> rjc = Gy[j * dmax + cl];
+              for (int ai = j + 1; ai <= cl; ai += 4) {     // independent rows, loads first
+                cx<T> v[4], rr[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  if (ai + u <= cl) {
+                    v[u] = Gy[(ai + u) * dmax + cl];
+                    rr[u] = Gy[j * dmax + ai + u];
+                  }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  if (ai + u <= cl) {
+                    cfma_jc(v[u], cscale(rr[u], T(-1)), rjc);
+                    Gy[(ai + u) * dmax + cl] = v[u];
+                  }
+                }
+              }
             }
+            __syncwarp();
           }
-          __syncthreads();
         }
+        __syncthreads();
         // Q <- Q R^{-1} row by row (forward substitution on x R = q)
+        // (rows of R of dropped columns are zero and rs[c] = 1 / R_cc is zero for them)
         for (int i = tid; i < K; i += kThreads) {
           cx<T>* qi = Q + i * dmax;
           for (int c = 0; c < d; ++c) {
-            if (drop[c]) { qi[c] = cmk<T>(0, 0); continue; }
-            cx<T> v = qi[c];
-            for (int a2 = 0; a2 < c; ++a2) {
-              if (!drop[a2]) v = csub(v, cmul(qi[a2], Gy[a2 * dmax + c]));
+            cx<T> v0 = qi[c], v1 = cmk<T>(0, 0);
+            int a2 = 0;
+            for (; a2 + 1 < c; a2 += 2) {
+              cfma(v0, cscale(qi[a2], T(-1)), Gy[a2 * dmax + c]);
+              cfma(v1, cscale(qi[a2 + 1], T(-1)), Gy[(a2 + 1) * dmax + c]);
             }
-            qi[c] = cscale(v, T(1) / Gy[c * dmax + c].re);
+            if (a2 < c) cfma(v0, cscale(qi[a2], T(-1)), Gy[a2 * dmax + c]);
+            qi[c] = cscale(cadd(v0, v1), rs[c]);
           }
         }
         __syncthreads();
@@ -361,86 +391,137 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
         Uh[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
       }
       __syncthreads();
-      {
+      if (tid < 32) {   // one warp: rounds synchronise with __syncwarp only
+        const int lane = tid;
         const int dd = d + (d & 1);
-        const int npairs = dd >> 1;
+        const int npairs = dd >> 1, dm1 = dd - 1;
+        const int nit = npairs * d;                  // work items (pair k, row or column)
+        const uint32_t magic = (1u << 20) / (uint32_t)d + 1u;   // e / d for e < 1024
         const int max_sweeps = (sizeof(T) == 4) ? 12 : 20;
-        const T eps = (sizeof(T) == 4) ? T(1e-12) : T(1e-28);
+        // converged when the off-diagonal energy is below eps of the total: 1e-10 keeps FP32
+        // rotations above the rounding floor of a d x d sweep (about (d u)^2)
+        const T eps = (sizeof(T) == 4) ? T(1e-10) : T(1e-26);
         for (int sweep = 0; sweep < max_sweeps; ++sweep) {
           T off = 0, tot = 0;
-          for (int e = tid; e < d * d; e += kThreads) {
-            const int i = e / d, j = e - i * d;
-            const T v = cabs2(Gy[i * dmax + j]);
-            tot += v;
-            if (i != j) off += v;
+          if (lane < d) {
+            for (int i = 0; i < d; ++i) {
+              const T v = cabs2(Gy[i * dmax + lane]);
+              tot += v;
+              if (i != lane) off += v;
+            }
           }
-          off = block_sum(off, red);
-          tot = block_sum(tot, red);
+          off = warp_sum(off);
+          tot = warp_sum(tot);
           if (!(off > eps * tot)) break;
-          for (int rnd = 0; rnd < dd - 1; ++rnd) {
-            if (tid < npairs) {
-              // circle-method pairing: x_i = 1 + ((i + rnd) mod (dd - 1)); pairs (0, x_0), (x_k, x_{dd-1-k})
-              int p0, q0;
-              if (tid == 0) { p0 = 0; q0 = 1 + (rnd % (dd - 1)); }
-              else {
-                p0 = 1 + ((tid + rnd) % (dd - 1));
-                q0 = 1 + ((dd - 1 - tid + rnd) % (dd - 1));
-              }
-              const int p1 = min(p0, q0), q1 = max(p0, q0);
-              bool active = q1 < d;
-              T c = 1, s = 0;
-              cx<T> ph = cmk<T>(1, 0);
-              if (active) {
+          for (int rnd = 0; rnd < dm1; ++rnd) {
+            // rotation of pair `lane` (circle method: x_i = 1 + ((i + rnd) mod (dd - 1));
+            // pairs (0, x_0), (x_k, x_{dd-1-k}))
+            int p1 = 0, q1 = 0;
+            T c = 1, s = 0;
+            cx<T> ph = cmk<T>(1, 0);
+            bool act = false;
+            if (lane < npairs) {
+              int a1 = lane + rnd, a2 = dm1 - lane + rnd;
+              if (a1 >= dm1) a1 -= dm1;
+              if (a2 >= dm1) a2 -= dm1;
+              const int p0 = lane == 0 ? 0 : 1 + a1;
+              const int q0 = lane == 0 ? 1 + (rnd < dm1 ? rnd : rnd - dm1) : 1 + a2;
+              p1 = min(p0, q0);
+              q1 = max(p0, q0);
+              if (q1 < d) {
                 const cx<T> bpq = Gy[p1 * dmax + q1];
                 const T ab = hypot(bpq.re, bpq.im);     // no squaring: unit-modulus phase
                 if (ab > T(0)) {
-                  ph = cmk(bpq.re / ab, -bpq.im / ab);               // e^{-i phi}
-                  const T th = T(0.5) * atan2(T(2) * ab, Gy[q1 * dmax + q1].re - Gy[p1 * dmax + p1].re);
-                  c = cos(th);
-                  s = sin(th);
-                } else {
-                  active = false;
+                  const T inv = T(1) / ab;
+                  ph = cmk(bpq.re * inv, -bpq.im * inv);             // e^{-i phi}
+                  // tan(2 theta) = 2|E_pq| / (E_qq - E_pp); smaller root t = tan(theta)
+                  const T tau = (Gy[q1 * dmax + q1].re - Gy[p1 * dmax + p1].re) * (T(0.5) * inv);
+                  const T t = copysign(T(1), tau) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                  c = T(1) / sqrt(T(1) + t * t);
+                  s = t * c;
+                  act = true;
                 }
               }
-              pp[tid] = active ? p1 : -1;
-              pq[tid] = q1;
-              rc[tid] = c;
-              rs[tid] = s;
-              rph[tid] = ph;
             }
-            __syncthreads();
-            // columns: col_p <- c col_p - s ph col_q ; col_q <- s col_p + c ph col_q (E and U_hat)
-            for (int e = tid; e < npairs * d; e += kThreads) {
-              const int k = e / d, i = e - k * d;
-              const int p1 = pp[k];
-              if (p1 < 0) continue;
-              const int q1 = pq[k];
-              const T c = rc[k], s = rs[k];
-              const cx<T> ph = rph[k];
-              const cx<T> ep = Gy[i * dmax + p1], eq = cmul(ph, Gy[i * dmax + q1]);
-              Gy[i * dmax + p1] = csub(cscale(ep, c), cscale(eq, s));
-              Gy[i * dmax + q1] = cadd(cscale(ep, s), cscale(eq, c));
-              const cx<T> up = Uh[i * dmax + p1], uq = cmul(ph, Uh[i * dmax + q1]);
-              Uh[i * dmax + p1] = csub(cscale(up, c), cscale(uq, s));
-              Uh[i * dmax + q1] = cadd(cscale(up, s), cscale(uq, c));
+            // columns (E and U_hat): col_p <- c col_p - s ph col_q ; col_q <- s col_p + c ph col_q
+            for (int base = 0; base < nit; base += 64) {
+              int kk[2], ii[2];
+              T cc[2], ss[2];
+              cx<T> pp2[2], ep[2], eq[2], up[2], uq[2];
+              bool ok[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int e = base + lane + 32 * u;
+                const int k = (int)(((uint32_t)e * magic) >> 20);
+                const int src = k < 32 ? k : 0;
+                const int pk = __shfl_sync(0xffffffffu, p1, src);
+                const int qk = __shfl_sync(0xffffffffu, q1, src);
+                const bool ak = __shfl_sync(0xffffffffu, act ? 1 : 0, src) != 0;
+                cc[u] = __shfl_sync(0xffffffffu, c, src);
+                ss[u] = __shfl_sync(0xffffffffu, s, src);
+                pp2[u] = cmk<T>(__shfl_sync(0xffffffffu, ph.re, src), __shfl_sync(0xffffffffu, ph.im, src));
+                ok[u] = e < nit && ak;
+                kk[u] = pk;
+                ii[u] = qk;
+                if (ok[u]) {
+                  const int i = e - k * d;
+                  ep[u] = Gy[i * dmax + pk]; eq[u] = Gy[i * dmax + qk];
+                  up[u] = Uh[i * dmax + pk]; uq[u] = Uh[i * dmax + qk];
+                }
+              }
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                if (!ok[u]) continue;
+                const int e = base + lane + 32 * u;
+                const int k = (int)(((uint32_t)e * magic) >> 20), i = e - k * d;
+                const cx<T> q1v = cmul(pp2[u], eq[u]), q2v = cmul(pp2[u], uq[u]);
+                Gy[i * dmax + kk[u]] = csub(cscale(ep[u], cc[u]), cscale(q1v, ss[u]));
+                Gy[i * dmax + ii[u]] = cadd(cscale(ep[u], ss[u]), cscale(q1v, cc[u]));
+                Uh[i * dmax + kk[u]] = csub(cscale(up[u], cc[u]), cscale(q2v, ss[u]));
+                Uh[i * dmax + ii[u]] = cadd(cscale(up[u], ss[u]), cscale(q2v, cc[u]));
+              }
             }
-            __syncthreads();
+            __syncwarp();
             // rows: row_p <- c row_p - s conj(ph) row_q ; row_q <- s row_p + c conj(ph) row_q
-            for (int e = tid; e < npairs * d; e += kThreads) {
-              const int k = e / d, j = e - k * d;
-              const int p1 = pp[k];
-              if (p1 < 0) continue;
-              const int q1 = pq[k];
-              const T c = rc[k], s = rs[k];
-              const cx<T> phc = cconj(rph[k]);
-              const cx<T> ep = Gy[p1 * dmax + j], eq = cmul(phc, Gy[q1 * dmax + j]);
-              Gy[p1 * dmax + j] = csub(cscale(ep, c), cscale(eq, s));
-              Gy[q1 * dmax + j] = cadd(cscale(ep, s), cscale(eq, c));
+            for (int base = 0; base < nit; base += 64) {
+              int kk[2], ii[2];
+              T cc[2], ss[2];
+              cx<T> pp2[2], ep[2], eq[2];
+              bool ok[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int e = base + lane + 32 * u;
+                const int k = (int)(((uint32_t)e * magic) >> 20);
+                const int src = k < 32 ? k : 0;
+                const int pk = __shfl_sync(0xffffffffu, p1, src);
+                const int qk = __shfl_sync(0xffffffffu, q1, src);
+                const bool ak = __shfl_sync(0xffffffffu, act ? 1 : 0, src) != 0;
+                cc[u] = __shfl_sync(0xffffffffu, c, src);
+                ss[u] = __shfl_sync(0xffffffffu, s, src);
+                pp2[u] = cmk<T>(__shfl_sync(0xffffffffu, ph.re, src), -__shfl_sync(0xffffffffu, ph.im, src));
+                ok[u] = e < nit && ak;
+                kk[u] = pk;
+                ii[u] = qk;
+                if (ok[u]) {
+                  const int j2 = e - k * d;
+                  ep[u] = Gy[pk * dmax + j2]; eq[u] = Gy[qk * dmax + j2];
+                }
+              }
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                if (!ok[u]) continue;
+                const int e = base + lane + 32 * u;
+                const int k = (int)(((uint32_t)e * magic) >> 20), j2 = e - k * d;
+                const cx<T> q1v = cmul(pp2[u], eq[u]);
+                Gy[kk[u] * dmax + j2] = csub(cscale(ep[u], cc[u]), cscale(q1v, ss[u]));
+                Gy[ii[u] * dmax + j2] = cadd(cscale(ep[u], ss[u]), cscale(q1v, cc[u]));
+              }
             }
-            __syncthreads();
+            __syncwarp();
           }
         }
       }
+      __syncthreads();
       // 3f. sigma_hat^2 (eigenvalues, clamped at 0) sorted descending
       if (tid < d) lam[tid] = fmax(Gy[tid * dmax + tid].re, T(0));
       __syncthreads();
@@ -596,30 +677,71 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
   if (branch == WBRZF_BRANCH_INIT || branch == WBRZF_BRANCH_PERIODIC ||
       branch == WBRZF_BRANCH_RANK || branch == WBRZF_BRANCH_FULL ||
       branch == WBRZF_BRANCH_FALLBACK) {
-    for (int idx = tid; idx < KK; idx += kThreads) X[idx] = G[idx];
-    __syncthreads();
     // Gauss-Jordan exchange steps; G is Hermitian positive definite, so no pivoting:
     // a = X_pp; X_pp <- 1/a; X_pj <- -X_pj/a; X_ip <- X_ip/a; X_ij <- X_ij - X_ip X_pj / a
     bool bad = false;
-    for (int p = 0; p < K; ++p) {
-      if (tid < K) {
-        tmp[tid] = X[tid * K + p];          // column p
-        tmp[K + tid] = X[p * K + tid];      // row p
+    if (K <= 32) {
+      // Register-resident form on the 32 x 32 embedding [[G, 0], [0, I]]: thread (warp w,
+      // lane i) holds row i, columns 4w .. 4w+3; pivot column p goes through shared memory
+      // (double-buffered, one barrier per pivot), pivot row p by warp shuffles.
+      const int w8 = tid >> 5, i = tid & 31;
+      cx<T> x[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = 4 * w8 + c;
+        x[c] = (i < K && j < K) ? G[i * K + j] : cmk<T>(i == j ? T(1) : T(0), T(0));
+      }
+      for (int p = 0; p < K; ++p) {
+        cx<T>* cb = tmp + ((p & 1) << 5);
+        if (w8 == (p >> 2)) {
+          const int sub = p & 3;
+          cb[i] = sub == 0 ? x[0] : sub == 1 ? x[1] : sub == 2 ? x[2] : x[3];
+        }
+        __syncthreads();
+        const cx<T> colp = cb[i];
+        const cx<T> ap = cb[p];
+        if (!(ap.re > T(0)) || !cfinite(ap)) bad = true;
+        const cx<T> ia = crecip(ap);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const cx<T> rp = cmk<T>(__shfl_sync(0xffffffffu, x[c].re, p),
+                                  __shfl_sync(0xffffffffu, x[c].im, p));
+          const int j = 4 * w8 + c;
+          const cx<T> rpa = cmul(rp, ia);
+          if (i == p) x[c] = (j == p) ? ia : cscale(rpa, T(-1));
+          else if (j == p) x[c] = cmul(colp, ia);
+          else x[c] = csub(x[c], cmul(colp, rpa));
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = 4 * w8 + c;
+        if (i < K && j < K) X[i * K + j] = x[c];
       }
       __syncthreads();
-      const cx<T> ap = tmp[p];
-      if (!(ap.re > T(0)) || !cfinite(ap)) bad = true;
-      const cx<T> ia = crecip(ap);
-      for (int idx = tid; idx < KK; idx += kThreads) {
-        const int i = idx / K, j = idx - i * K;
-        cx<T> v;
-        if (i == p && j == p) v = ia;
-        else if (i == p) v = cscale(cmul(tmp[K + j], ia), T(-1));
-        else if (j == p) v = cmul(tmp[i], ia);
-        else v = csub(X[idx], cmul(tmp[i], cmul(tmp[K + j], ia)));
-        X[idx] = v;
-      }
+    } else {   // general K: block-wide elimination through shared memory
+      for (int idx = tid; idx < KK; idx += kThreads) X[idx] = G[idx];
       __syncthreads();
+      for (int p = 0; p < K; ++p) {
+        if (tid < K) {
+          tmp[tid] = X[tid * K + p];          // column p
+          tmp[K + tid] = X[p * K + tid];      // row p
+        }
+        __syncthreads();
+        const cx<T> ap = tmp[p];
+        if (!(ap.re > T(0)) || !cfinite(ap)) bad = true;
+        const cx<T> ia = crecip(ap);
+        for (int idx = tid; idx < KK; idx += kThreads) {
+          const int i = idx / K, j = idx - i * K;
+          cx<T> v;
+          if (i == p && j == p) v = ia;
+          else if (i == p) v = cscale(cmul(tmp[K + j], ia), T(-1));
+          else if (j == p) v = cmul(tmp[i], ia);
+          else v = csub(X[idx], cmul(tmp[i], cmul(tmp[K + j], ia)));
+          X[idx] = v;
+        }
+        __syncthreads();
+      }
     }
     if (bad) status |= WBRZF_STATUS_NOT_PD;
   }
@@ -629,11 +751,38 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
 
   // ---------------------------------------------------------------- 6. scale and SINR
   // M = G X - alpha X = H H^H X  (into D)
-  for (int idx = tid; idx < KK; idx += kThreads) {
-    const int i = idx / K, j = idx - i * K;
-    cx<T> acc = cscale(X[idx], -alpha);
-    for (int k = 0; k < K; ++k) cfma(acc, G[i * K + k], X[k * K + j]);
-    D[idx] = acc;
+  if (K <= 32) {
+    // warp w: rows w, w + 8, w + 16, w + 24; lane: column.  G rows are warp-uniform loads,
+    // each X[k][lane] is loaded once and used for all four rows.
+    const int w8 = tid >> 5, j = tid & 31;
+    if (j < K) {
+      cx<T> acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = w8 + 8 * q;
+        acc[q] = (i < K) ? cscale(X[i * K + j], -alpha) : cmk<T>(0, 0);
+      }
+      for (int k = 0; k < K; ++k) {
+        const cx<T> xk = X[k * K + j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = w8 + 8 * q;
+          if (i < K) cfma(acc[q], G[i * K + k], xk);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = w8 + 8 * q;
+        if (i < K) D[i * K + j] = acc[q];
+      }
+    }
+  } else {
+    for (int idx = tid; idx < KK; idx += kThreads) {
+      const int i = idx / K, j = idx - i * K;
+      cx<T> acc = cscale(X[idx], -alpha);
+      for (int k = 0; k < K; ++k) cfma(acc, G[i * K + k], X[k * K + j]);
+      D[idx] = acc;
+    }
   }
   __syncthreads();
   T part = 0;
@@ -677,7 +826,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
 // General path: any K <= kMaxK, complex64 or complex128, the Gram matrix and the precoder
 // computed with FP32 / FP64 fused multiply-adds from H staged by cp.async.
 template <class T>
-__global__ void __launch_bounds__(kThreads) wbrzf_step_kernel(const StepArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, 2) wbrzf_step_kernel(const StepArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
   const int tid = threadIdx.x;
@@ -691,6 +840,7 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_kernel(const StepArgs<T> 
   const T alpha = a.alpha[b];
   const cx<T>* __restrict__ Hb = a.H + (size_t)b * K * N;
   const int nchunks = (N + kChunk - 1) / kChunk;
+  prefetch_state<T>(a, b, w.D, w.X);   // completes within the Gram loop's cp.async waits
 
   // ---------------------------------------------------------------- 1. Gram matrix
   constexpr int QMAX = (kMaxK * kMaxK + kThreads - 1) / kThreads;

@@ -10,6 +10,10 @@ cudaError_t launch_step_tc(const StepArgs<float>& a, const void* hmap, size_t sm
     cudaError_t e = cudaFuncSetAttribute(wbrzf_step_tc_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // all of the SM's shared memory for shared-memory use, so three CTAs fit per SM
+    e = cudaFuncSetAttribute(wbrzf_step_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             100);
+    if (e != cudaSuccess) return e;
     smem_set = smem;
   }
   wbrzf_step_tc_kernel<<<a.batch, kThreads, smem, s>>>(a, *static_cast<const CUtensorMap*>(hmap));

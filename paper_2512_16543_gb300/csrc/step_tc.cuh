@@ -143,7 +143,7 @@ __device__ __forceinline__ void fence_async_smem() {
 }
 
 // ---------------------------------------------------------------- the kernel
-__global__ void __launch_bounds__(kThreads) wbrzf_step_tc_kernel(
+__global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
     const StepArgs<float> a, const __grid_constant__ CUtensorMap hmap) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw_u = smem_u32(smem_raw);
@@ -153,8 +153,8 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_tc_kernel(
   const int K = a.K, N = a.N, KK = K * K;
   const TcLayout Ly = tc_layout(K, a.dmax, a.rcap);
   cx<float>* const G = reinterpret_cast<cx<float>*>(sm + Ly.oGXD);
-  cx<float>* const X = G + KK;
-  cx<float>* const Dm = X + KK;
+  cx<float>* const Dm = G + KK;
+  cx<float>* const X = reinterpret_cast<cx<float>*>(sm + Ly.oX);
   unsigned char* const ring = sm + Ly.oRing;              // kStages x (32 rows x 256 B)
   unsigned char* const uni = sm + Ly.oUnion;
   uint64_t* const bars = reinterpret_cast<uint64_t*>(sm + Ly.oBar);
@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_tc_kernel(
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int row0 = b * K;
+  prefetch_state<float>(a, b, Dm, X);
 
   auto issue_block = [&](int g) {      // g: running block index (Gram blocks, then W blocks)
     const int s = g % kStages;
@@ -251,15 +252,14 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_tc_kernel(
     // column blocks 2h (a Re part) and 2h + 1 (an Im part).  Part a contributes
     //   a even (Re_*): Re G += D[a][Re_*], Im G -= D[a][Im_*]
     //   a odd  (Im_*): Re G += D[a][Im_*], Im G += D[a][Re_*]
-    // Partial sums go to one slice per part (h = 0 writes, h = 1 adds), then a fixed-order
-    // sum over the four slices keeps the result deterministic.
+    // Each half h accumulates into its own padded slice, one quadrant after another (fixed
+    // order, so the result is deterministic); the two slices are then added.
     const int qa = warp & 3, h = warp >> 2, k = lane;
-    float* slice = reinterpret_cast<float*>(uni) + (size_t)qa * 2 * KK;   // interleaved re/im
+    const int KS = K + 1;                  // padded row stride: spreads lanes over banks
+    float* slice = reinterpret_cast<float*>(uni) + (size_t)h * 2 * K * KS;   // re/im pairs
     const bool odd = qa & 1;
-    // block 2h (a Re part): Re G if a is even, Im G if a is odd (sign +)
-    // block 2h + 1 (an Im part): Im G with sign - if a is even, Re G if a is odd
-    for (int pass = 0; pass < 2; ++pass) {
-      if (h == pass) {
+    for (int pass = 0; pass < 4; ++pass) {
+      if (qa == pass) {
         for (int blk = 0; blk < 2; ++blk) {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(32 * qa) << 16) + (uint32_t)(64 * h + 32 * blk), v);
@@ -269,20 +269,21 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_tc_kernel(
 #pragma unroll
             for (int l = 0; l < 32; ++l) {
               if (l < K) {
-                float* dst = slice + 2 * (k * K + l) + comp;
+                float* dst = slice + 2 * (k * KS + l) + comp;
                 *dst = (pass == 0 ? 0.f : *dst) + sgn * v[l];
               }
             }
           }
         }
       }
-      tc_fence_before();
       __syncthreads();
     }
+    tc_fence_before();
     const cx<float>* sl = reinterpret_cast<const cx<float>*>(uni);
+    const int PS = K * KS;
     for (int idx = tid; idx < KK; idx += kThreads) {
-      cx<float> gsum = cadd(cadd(sl[idx], sl[KK + idx]), cadd(sl[2 * KK + idx], sl[3 * KK + idx]));
-      G[idx] = gsum;
+      const int kr = idx / K, o = kr * KS + (idx - kr * K);
+      G[idx] = cadd(sl[o], sl[PS + o]);
     }
     __syncthreads();
     for (int idx = tid; idx < KK; idx += kThreads) {
@@ -295,6 +296,8 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_tc_kernel(
   }
 
   // ------------------------------------------------------------ 2-6. shared SIMT phases
+  cp_async_wait<0>();
+  __syncthreads();
   const Work<float> w = carve_work<float>(uni, K, a.dmax, a.rcap, G, X, Dm);
   const float s = core_phases<float>(a, w, b);
   __syncthreads();
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kThreads) wbrzf_step_tc_kernel(
   // ------------------------------------------------------------ 7. W = s H^H X on tensor cores
   {
     unsigned char* const At = uni;              // 2 K-blocks x 128 rows x 128 B
-    unsigned char* const Bt = uni + 32768;      // 2 K-blocks x 64 rows x 128 B
+    unsigned char* const Bt = sm + Ly.oGXD;     // 2 K-blocks x 64 rows x 128 B (G, dG dead)
     // B[(j, c')][(k, c)]: rows 2j (Re W), 2j + 1 (Im W); columns 2k (Re H), 2k + 1 (Im H)
     for (int e = tid; e < 64 * 16; e += kThreads) {
       const int row = e >> 4, qq = e & 15;            // 16 chunks of 4 floats per row
