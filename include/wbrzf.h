@@ -14,8 +14,9 @@
  *                                                           Section II eq. 5)
  *     SINR_n, R_sum = sum_n log2(1 + SINR_n)               (Section VI eq. 15; user n's gain on
  *                                                           beam i is (H_t W)_{n i})
- *   One kernel launch per call processes every instance; all of the steps above run in the
- *   library's own CUDA kernels.
+ *   Each call processes every instance: one kernel launch on the single-CTA engines (K <= 64),
+ *   a fixed sequence of batched launches on the blocked engine (any K); all of the steps
+ *   above run in the library's own CUDA kernels.
  *
  * Memory and layout conventions (all calls):
  *   - Complex numbers are interleaved (re, im): complex64 (2 x float) for WBRZF_C64*,
@@ -86,11 +87,19 @@ enum {
 
 /* Which kernel runs a handle's snapshots (wbrzf_set_engine). */
 enum {
-  WBRZF_ENGINE_AUTO = 0,      /* tensor cores when eligible, else the FMA kernel             */
-  WBRZF_ENGINE_SIMT = 1,      /* FP32/FP64 fused multiply-adds for every product             */
-  WBRZF_ENGINE_TENSOR = 2     /* tcgen05 tensor cores for H H^H (FP32-faithful hi/lo TF32
+  WBRZF_ENGINE_AUTO = 0,      /* K <= 64: tensor cores when eligible, else the FMA kernel;
+                                 K > 64: the blocked engine                                   */
+  WBRZF_ENGINE_SIMT = 1,      /* one CTA per instance, FP32/FP64 fused multiply-adds for
+                                 every product; K <= 64                                       */
+  WBRZF_ENGINE_TENSOR = 2,    /* tcgen05 tensor cores for H H^H (FP32-faithful hi/lo TF32
                                  split) and H^H X (TF32 inputs, FP32 accumulation); complex64,
                                  K <= 32, even N, H_t 16-byte aligned                         */
+  WBRZF_ENGINE_BLOCKED = 3    /* any K: each step of the path a batched kernel of its own
+                                 (tiled complex GEMMs, per-instance Cholesky / Jacobi /
+                                 capacitance kernels, block Gauss-Jordan inverse on 32 x 32
+                                 pivot blocks); sketch width dmax up to 110 (complex64) / 78
+                                 (complex128), batch <= 65535; needs the larger workspace of
+                                 wbrzf_workspace_bytes_engine(..., WBRZF_ENGINE_BLOCKED)       */
 };
 
 /* Rank rule and method parameters (Algorithm 1 inputs, Algorithm 2 switch). */
@@ -118,12 +127,20 @@ typedef struct {
   int32_t status;           /* WBRZF_STATUS_* bits                                           */
 } wbrzf_step_info;
 
-/* Bytes of device workspace a handle with these sizes needs (0 on invalid sizes). */
+/* Bytes of device workspace a handle with these sizes needs to run on the engine that
+ * WBRZF_ENGINE_AUTO picks (0 on invalid or unsupported sizes). */
 size_t wbrzf_workspace_bytes(int batch, int N, int K, wbrzf_precision prec,
                              const wbrzf_rank_rule* rule);
 
+/* Bytes of device workspace needed to run on `engine` (WBRZF_ENGINE_*); 0 when the sizes are
+ * invalid or the engine cannot run them.  Not part of the paper's method: the blocked engine
+ * needs per-instance scratch in device memory that the single-CTA kernels keep on chip. */
+size_t wbrzf_workspace_bytes_engine(int batch, int N, int K, wbrzf_precision prec,
+                                    const wbrzf_rank_rule* rule, int engine);
+
 /*
- * Create a handle for `batch` instances of size K x N (1 <= K <= 64, N >= 1).
+ * Create a handle for `batch` instances of size K x N (K >= 1, N >= 1; K > 64 runs on the
+ * blocked engine and needs its sketch width within that engine's limit).
  *   alpha[batch], sigma2[batch]: host arrays, regulariser alpha >= 0 and noise variance
  *       sigma_n^2 > 0 per instance (copied; the caller may free them on return).
  *   p_t: total transmit power P_t > 0 (eq. 5 power constraint).
@@ -164,7 +181,8 @@ wbrzf_status wbrzf_step_info_get(wbrzf* h, wbrzf_step_info* host_out, int count)
 
 /* Copy the resident state (device, batch contiguous K x K row-major, the handle's complex
  * type): G of the last snapshot and X = its inverse as maintained by the method.  Either
- * pointer may be NULL.  Asynchronous on the stream. */
+ * pointer may be NULL.  Asynchronous on the stream.  A WBRZF_METHOD_FULL_INVERSE handle keeps
+ * no state between snapshots: there the contents depend on the engine. */
 wbrzf_status wbrzf_get_state(wbrzf* h, void* G_out, void* X_out);
 
 /*
@@ -182,16 +200,19 @@ wbrzf_status wbrzf_set_trace(wbrzf* h, void* trace, size_t bytes);
  * not depend on its position in a batch.  Default: ids[b] = b.  Synchronises the stream. */
 wbrzf_status wbrzf_set_instance_ids(wbrzf* h, const uint32_t* ids, int count);
 
-/* Choose the kernel (WBRZF_ENGINE_*).  WBRZF_ENGINE_TENSOR on a handle that does not meet
- * its conditions returns WBRZF_ERR_UNSUPPORTED.  wbrzf_last_engine reports the kernel the
- * last snapshot ran on (WBRZF_ENGINE_SIMT or WBRZF_ENGINE_TENSOR; 0 before any). */
+/* Choose the kernel (WBRZF_ENGINE_*).  An engine whose conditions the handle does not meet
+ * returns WBRZF_ERR_UNSUPPORTED; WBRZF_ENGINE_BLOCKED on a handle created with less workspace
+ * than wbrzf_workspace_bytes_engine(..., WBRZF_ENGINE_BLOCKED) returns WBRZF_ERR_WORKSPACE.
+ * The resident state carries over between engines.  wbrzf_last_engine reports the engine
+ * the last snapshot ran on (WBRZF_ENGINE_SIMT, _TENSOR or _BLOCKED; 0 before any). */
 wbrzf_status wbrzf_set_engine(wbrzf* h, int engine);
 int wbrzf_last_engine(const wbrzf* h);
 
 /* Rebind the handle to another stream (cudaStream_t; NULL = legacy default stream). */
 wbrzf_status wbrzf_set_stream(wbrzf* h, void* cuda_stream);
 
-/* Kernel launches issued by this handle so far. */
+/* Kernel launches issued by this handle so far (one per snapshot on the single-CTA engines,
+ * one per step of the path on the blocked engine). */
 long long wbrzf_launch_count(const wbrzf* h);
 
 /* Release the handle (host memory only; the workspace stays the caller's). NULL is a no-op. */

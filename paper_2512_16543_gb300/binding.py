@@ -18,6 +18,7 @@ _lib = None
 # enums of wbrzf.h
 C128, C64 = 0, 1
 WB_ARSVD, FULL_INVERSE = 0, 1
+ENGINES = {"auto": 0, "simt": 1, "tensor": 2, "blocked": 3}
 BRANCH_NAMES = {0: "keep", 1: "woodbury", 2: "init", 3: "periodic", 4: "rank", 5: "full",
                 6: "fallback"}
 STATUS = {0: "ok", 1: "invalid argument", 2: "not initialized", 3: "workspace too small",
@@ -78,6 +79,9 @@ def lib() -> ctypes.CDLL:
     vp, sz, i32, dbl = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_double
     L.wbrzf_workspace_bytes.restype = sz
     L.wbrzf_workspace_bytes.argtypes = [i32, i32, i32, i32, ctypes.POINTER(RankRuleC)]
+    L.wbrzf_workspace_bytes_engine.restype = sz
+    L.wbrzf_workspace_bytes_engine.argtypes = [i32, i32, i32, i32, ctypes.POINTER(RankRuleC),
+                                               i32]
     L.wbrzf_create.restype = i32
     L.wbrzf_create.argtypes = [i32, i32, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl), dbl,
                                ctypes.POINTER(RankRuleC), i32, i32, vp, sz, vp,
@@ -135,7 +139,10 @@ class WBRZF:
 
     def __init__(self, batch: int, N: int, K: int, alpha, sigma2, *, p_t: float = 1.0,
                  rule: RankRule | None = None, method: str = "wb", precision: str = "c64",
-                 device="cuda", stream: torch.cuda.Stream | None = None):
+                 device="cuda", stream: torch.cuda.Stream | None = None,
+                 workspace_for: str = "auto"):
+        """workspace_for: the engine whose workspace is allocated ("blocked" sizes it for the
+        blocked engine, so that set_engine("blocked") can be used on any K)."""
         L = lib()
         self.batch, self.N, self.K = int(batch), int(N), int(K)
         self.prec = {"c64": C64, "c128": C128}[precision]
@@ -151,10 +158,11 @@ class WBRZF:
         s = [float(x) for x in (sigma2 if hasattr(sigma2, "__len__") else [sigma2] * self.batch)]
         if len(a) != self.batch or len(s) != self.batch:
             raise ValueError("alpha / sigma2 need one entry per instance")
-        nbytes = L.wbrzf_workspace_bytes(self.batch, self.N, self.K, self.prec,
-                                         ctypes.byref(self._rule_c))
+        nbytes = L.wbrzf_workspace_bytes_engine(self.batch, self.N, self.K, self.prec,
+                                                ctypes.byref(self._rule_c),
+                                                ENGINES[workspace_for])
         if nbytes == 0:
-            raise WbrzfError(1, "wbrzf_workspace_bytes")
+            raise WbrzfError(6, "wbrzf_workspace_bytes_engine")
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         with torch.cuda.device(self.device):
             self.stream = stream or torch.cuda.current_stream(self.device)
@@ -245,13 +253,15 @@ class WBRZF:
         _check(lib().wbrzf_set_instance_ids(self._h, arr, len(ids)), "wbrzf_set_instance_ids")
 
     def set_engine(self, engine: str) -> None:
-        """"auto", "simt" (fused multiply-adds) or "tensor" (tcgen05 tensor cores)."""
-        code = {"auto": 0, "simt": 1, "tensor": 2}[engine]
-        _check(lib().wbrzf_set_engine(self._h, code), "wbrzf_set_engine")
+        """"auto", "simt" (fused multiply-adds, one CTA per instance), "tensor" (tcgen05
+        tensor cores) or "blocked" (one batched kernel per step, any K)."""
+        _check(lib().wbrzf_set_engine(self._h, ENGINES[engine]), "wbrzf_set_engine")
 
     @property
     def last_engine(self) -> str:
-        return {0: "none", 1: "simt", 2: "tensor"}[int(lib().wbrzf_last_engine(self._h))]
+        names = {v: k for k, v in ENGINES.items()}
+        names[0] = "none"
+        return names[int(lib().wbrzf_last_engine(self._h))]
 
     def set_stream(self, stream: torch.cuda.Stream) -> None:
         self.stream = stream

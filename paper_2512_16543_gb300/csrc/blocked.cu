@@ -1,0 +1,816 @@
+// Blocked engine: the per-snapshot path for any K as a fixed sequence of batched kernels.
+//
+// Used for K above the single-CTA limit (the large array: K = 512, N = 4096) and on request
+// for smaller K.  Each step of the path is its own kernel over all instances:
+//   Gram / dG     batched complex GEMM H H^H (FP32/FP64 FMA), then a per-instance kernel that
+//                 adds alpha I, symmetrises, forms dG = G_t - G_{t-1}, its norm and the scaled
+//                 copy used by the low-rank step (Section II eq. 5, Section III eqs. 7-9)
+//   Algorithm 1   per iteration: Omega (Philox), Y = dG Omega, CholQR2 (Gram GEMM, per-instance
+//                 Cholesky with column drop, row-parallel triangular solve), B = Q^H dG,
+//                 E = B B^H, per-instance Jacobi eigendecomposition, energy rule (eq. 14)
+//   Algorithm 2   per-instance branch; Woodbury (eq. 12) as GEMMs around an r x r pivoted
+//                 capacitance inverse; or a direct inverse by block Gauss-Jordan exchange steps
+//                 on 32 x 32 pivot blocks (G is Hermitian positive definite: no pivoting)
+//   precoder      M = (G - alpha I) X, scale s = sqrt(P_t)/||H^H X||_F, SINR and sum-rate, then
+//                 W = s H^H X (Section II eq. 5, Section VI eq. 15)
+// Data-dependent control never returns to the host: every kernel reads per-instance control
+// words (low-rank step still iterating, branch) and instances that are not selected return at
+// once, so one snapshot is always the same launch sequence.
+#include "step_kernel.cuh"
+
+namespace wbk {
+namespace {
+
+enum Ctl { C_ACTIVE = 0, C_BRANCH = 1, C_R = 2, C_D = 3, C_ITERS = 4, C_K0 = 5, C_STATUS = 6, C_EXP = 7 };
+constexpr int kDirectMask = (1 << WBRZF_BRANCH_INIT) | (1 << WBRZF_BRANCH_PERIODIC) |
+                            (1 << WBRZF_BRANCH_RANK) | (1 << WBRZF_BRANCH_FULL) |
+                            (1 << WBRZF_BRANCH_FALLBACK);
+
+constexpr int kPending = 15;   // branch code while the low-rank step has not decided
+
+template <class T>
+struct Bufs {
+  cx<T>*D, *Om, *Q, *Gy, *Bm, *E, *Uh, *Ur, *Lm, *Tm, *Rh, *Z, *Cm, *CZ, *PC, *PR, *PU, *PV, *Pb;
+  T *lam, *rinv, *ws, *nu;
+  double *et, *nrm;
+  int *ctl, *perm, *drop;
+  BlockedLayout L;
+  int dmax, rcap;
+};
+
+template <class T>
+Bufs<T> make_bufs(unsigned char* base, int batch, int K, int dmax, int rcap) {
+  Bufs<T> b;
+  b.L = blocked_layout(batch, K, dmax, rcap, sizeof(cx<T>), sizeof(T));
+  auto C = [&](size_t o) { return reinterpret_cast<cx<T>*>(base + o); };
+  b.D = C(b.L.oD); b.Om = C(b.L.oOm); b.Q = C(b.L.oQ); b.Gy = C(b.L.oGy); b.Bm = C(b.L.oBm);
+  b.E = C(b.L.oE); b.Uh = C(b.L.oUh); b.Ur = C(b.L.oUr); b.Lm = C(b.L.oL); b.Tm = C(b.L.oT);
+  b.Rh = C(b.L.oRh); b.Z = C(b.L.oZ); b.Cm = C(b.L.oCm); b.CZ = C(b.L.oCZ);
+  b.PC = C(b.L.oPC); b.PR = C(b.L.oPR); b.PU = C(b.L.oPU); b.PV = C(b.L.oPV); b.Pb = C(b.L.oPb);
+  b.lam = reinterpret_cast<T*>(base + b.L.oLam);
+  b.rinv = reinterpret_cast<T*>(base + b.L.oRinv);
+  b.ws = reinterpret_cast<T*>(base + b.L.oWs);
+  b.nu = reinterpret_cast<T*>(base + b.L.oNu);
+  b.et = reinterpret_cast<double*>(base + b.L.oEt);
+  b.nrm = reinterpret_cast<double*>(base + b.L.oNrm);
+  b.ctl = reinterpret_cast<int*>(base + b.L.oCtl);
+  b.perm = reinterpret_cast<int*>(base + b.L.oPerm);
+  b.drop = reinterpret_cast<int*>(base + b.L.oDrop);
+  b.dmax = dmax;
+  b.rcap = rcap;
+  return b;
+}
+
+// gate: run instance b iff ctl[b][idx] is one of the values in `mask` (bit set)
+__device__ __forceinline__ bool gate_ok(const int* ctl, int b, int idx, int mask) {
+  return ctl == nullptr || ((mask >> ctl[8 * b + idx]) & 1);
+}
+
+// ---------------------------------------------------------------- batched complex GEMM
+// C_b = alpha * s_b * op(A_b) op(B_b) + beta C_b; op = N or H (conjugate transpose);
+// 64 x 64 tile per CTA, 256 threads with 4 x 4 outputs each, K chunks of 16 through shared
+// memory.  A_b = A + b sA; op(A) is m x k (A stored m x k, or k x m when opA = H).
+template <class T>
+struct GemmArgs {
+  int m, n, k;
+  const cx<T>* A; int lda; size_t sA; int opA;
+  const cx<T>* B; int ldb; size_t sB; int opB;
+  cx<T>* C; int ldc; size_t sC;
+  T alpha; const T* scale;   // alpha * scale[b] (scale may be null)
+  T beta;
+  const int* ctl; int gidx; int gmask;
+  const T* dshift;           // op(A) - dshift[b] I (may be null; square A only)
+};
+
+template <class T>
+__global__ void __launch_bounds__(256) cgemm_kernel(const GemmArgs<T> g) {
+  const int b = blockIdx.z;
+  if (!gate_ok(g.ctl, b, g.gidx, g.gmask)) return;
+  __shared__ cx<T> As[16][64 + 1];
+  __shared__ cx<T> Bs[16][64 + 1];
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const cx<T>* A = g.A + (size_t)b * g.sA;
+  const cx<T>* B = g.B + (size_t)b * g.sB;
+  cx<T> acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = cmk<T>(0, 0);
+  for (int k0 = 0; k0 < g.k; k0 += 16) {
+    for (int e = tid; e < 16 * 64; e += 256) {
+      int r, kk;
+      if (g.opA == 0) { r = e >> 4; kk = e & 15; } else { kk = e >> 6; r = e & 63; }
+      const int gi = m0 + r, gk = k0 + kk;
+      cx<T> v = cmk<T>(0, 0);
+      if (gi < g.m && gk < g.k) {
+        v = (g.opA == 0) ? A[(size_t)gi * g.lda + gk] : cconj(A[(size_t)gk * g.lda + gi]);
+        if (g.dshift != nullptr && gi == gk) v.re -= g.dshift[b];
+      }
+      As[kk][r] = v;
+    }
+    for (int e = tid; e < 16 * 64; e += 256) {
+      int c, kk;
+      if (g.opB == 0) { kk = e >> 6; c = e & 63; } else { c = e >> 4; kk = e & 15; }
+      const int gj = n0 + c, gk = k0 + kk;
+      cx<T> v = cmk<T>(0, 0);
+      if (gj < g.n && gk < g.k)
+        v = (g.opB == 0) ? B[(size_t)gk * g.ldb + gj] : cconj(B[(size_t)gj * g.ldb + gk]);
+      Bs[kk][c] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 16; ++kk) {
+      cx<T> av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma(acc[i][j], av[i], bv[j]);
+    }
+    __syncthreads();
+  }
+  const T al = g.scale ? g.alpha * g.scale[b] : g.alpha;
+  cx<T>* C = g.C + (size_t)b * g.sC;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = m0 + ty + 16 * i;
+    if (gi >= g.m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = n0 + tx + 16 * j;
+      if (gj >= g.n) continue;
+      cx<T> v = cscale(acc[i][j], al);
+      if (g.beta != T(0)) v = cadd(v, cscale(C[(size_t)gi * g.ldc + gj], g.beta));
+      C[(size_t)gi * g.ldc + gj] = v;
+    }
+  }
+}
+
+template <class T>
+cudaError_t gemm(cudaStream_t s, int batch, int m, int n, int k, const cx<T>* A, int lda,
+                 size_t sA, int opA, const cx<T>* B, int ldb, size_t sB, int opB, cx<T>* C,
+                 int ldc, size_t sC, T alpha, const T* scale, T beta, const int* ctl, int gidx,
+                 int gmask, const T* dshift = nullptr) {
+  if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+  GemmArgs<T> g{m, n, k, A, lda, sA, opA, B, ldb, sB, opB, C, ldc, sC, alpha, scale, beta,
+                ctl, gidx, gmask, dshift};
+  dim3 grid((n + 63) / 64, (m + 63) / 64, batch);
+  cgemm_kernel<T><<<grid, 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------- per-instance kernels
+// Gram epilogue: D holds H H^H on entry.  G_t = that + alpha I, exactly Hermitian (upper
+// triangle wins), into the resident Gs; in update mode D becomes dG = G_t - G_{t-1}, scaled by
+// an exact power of two to unit Frobenius norm when the low-rank step will run.
+template <class T>
+__global__ void __launch_bounds__(256) finish_gram_kernel(const StepArgs<T> a, const Bufs<T> w) {
+  __shared__ T red[40];
+  const int b = blockIdx.x, tid = threadIdx.x, K = a.K, KK = K * K;
+  cx<T>* D = w.D + (size_t)b * w.L.sD;
+  cx<T>* Gs = a.Gs + (size_t)b * KK;
+  int* ctl = w.ctl + 8 * b;
+  const T alpha = a.alpha[b];
+  const bool upd = a.mode == MODE_UPDATE;
+  T s_dg = 0, s_g = 0;
+  for (int idx = tid; idx < KK; idx += 256) {
+    const int k = idx / K, l = idx - k * K;
+    if (k > l) continue;
+    cx<T> g = D[idx];
+    if (k == l) g = cmk(g.re + alpha, T(0));
+    if (upd) {
+      const cx<T> d = csub(g, Gs[idx]);
+      D[idx] = d;
+      s_dg += cabs2(d);
+      s_g += cabs2(g);
+      if (k != l) {
+        const cx<T> dl = csub(cconj(g), Gs[l * K + k]);
+        D[l * K + k] = dl;
+        s_dg += cabs2(dl);
+        s_g += cabs2(g);
+      }
+    }
+    Gs[idx] = g;
+    if (k != l) Gs[l * K + k] = cconj(g);
+  }
+  const double dg2 = (double)block_sum(s_dg, red);
+  const double g2 = (double)block_sum(s_g, red);
+  int branch, active = 0, e = 0;
+  if (a.mode == MODE_INIT) branch = WBRZF_BRANCH_INIT;
+  else if (a.mode == MODE_FULL) branch = WBRZF_BRANCH_FULL;
+  else if (a.period > 0 && (a.t % a.period) == 0) branch = WBRZF_BRANCH_PERIODIC;
+  else if (sqrt(dg2) <= a.dg_floor_rel * sqrt(g2)) branch = WBRZF_BRANCH_KEEP;
+  else { branch = kPending; active = 1; frexp(sqrt(dg2), &e); }
+  if (active) {
+    const T down = (T)ldexp(1.0, -e);
+    for (int idx = tid; idx < KK; idx += 256) D[idx] = cscale(D[idx], down);
+  }
+  if (tid == 0) {
+    ctl[C_ACTIVE] = active;
+    ctl[C_BRANCH] = branch;
+    ctl[C_R] = 0;
+    ctl[C_D] = 0;
+    ctl[C_ITERS] = 0;
+    ctl[C_K0] = a.k_init;
+    ctl[C_STATUS] = 0;
+    ctl[C_EXP] = e;
+    w.et[b] = a.eta * ldexp(dg2, -2 * e);
+    w.nrm[2 * b] = dg2;
+    w.nrm[2 * b + 1] = g2;
+    w.nu[b] = (T)ldexp(1.0, e);
+  }
+}
+
+// Omega (K x d, zero-padded to dmax columns) of iteration `it`: entry (i, j) from Philox
+// counter (i, j/2, t, 16 id + it).
+template <class T>
+__global__ void omega_kernel(const StepArgs<T> a, const Bufs<T> w, int it, int d) {
+  const int b = blockIdx.y;
+  if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
+  const int dmax = w.dmax, nq = (dmax + 1) >> 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.K * nq) return;
+  const int i = e / nq, q = e - i * nq;
+  cx<T>* Om = w.Om + (size_t)b * w.L.sOm + (size_t)i * dmax;
+  if (2 * q >= d) {
+    Om[2 * q] = cmk<T>(0, 0);
+    if (2 * q + 1 < dmax) Om[2 * q + 1] = cmk<T>(0, 0);
+    return;
+  }
+  const uint4 x = philox4x32_10(
+      make_uint4((uint32_t)i, (uint32_t)q, (uint32_t)a.t, 16u * a.ids[b] + (uint32_t)it),
+      a.seed_lo, a.seed_hi);
+  Om[2 * q] = box_muller(x.x, x.y, T(0));
+  if (2 * q + 1 < dmax) Om[2 * q + 1] = (2 * q + 1 < d) ? box_muller(x.z, x.w, T(0)) : cmk<T>(0, 0);
+}
+
+// Cholesky Gy = R^H R (d x d, ld dmax) with column drop; R and 1/R_cc (0 for dropped) out.
+template <class T>
+__global__ void __launch_bounds__(256) cholesky_kernel(const Bufs<T> w, int d, int pass) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int b = blockIdx.x, tid = threadIdx.x, dmax = w.dmax;
+  if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
+  cx<T>* A = reinterpret_cast<cx<T>*>(sm);
+  T* cn = reinterpret_cast<T*>(A + (size_t)dmax * dmax);
+  T* rv = cn + dmax;
+  int* drop = reinterpret_cast<int*>(rv + dmax);
+  cx<T>* Gy = w.Gy + (size_t)b * w.L.sGy;
+  int* gdrop = w.drop + (size_t)b * dmax;
+  const T tol_rel = (sizeof(T) == 4) ? T(1e-4) : T(1e-12);
+  for (int e = tid; e < d * d; e += 256) {
+    const int i = e / d, j = e - i * d;
+    A[i * dmax + j] = Gy[i * dmax + j];
+  }
+  for (int c = tid; c < d; c += 256) drop[c] = pass == 0 ? 0 : gdrop[c];
+  __syncthreads();
+  for (int c = tid; c < d; c += 256) cn[c] = A[c * dmax + c].re;
+  __syncthreads();
+  for (int j = 0; j < d; ++j) {
+    if (tid == 0) {
+      const T piv = A[j * dmax + j].re;
+      const bool dj = drop[j] || !(cn[j] > T(0)) || !(piv > tol_rel * cn[j]) || !isfinite(piv);
+      drop[j] = dj ? 1 : 0;
+      rv[j] = dj ? T(0) : T(1) / sqrt(piv);
+    }
+    __syncthreads();
+    const T rinv = rv[j];
+    for (int c = j + tid; c < d; c += 256) A[j * dmax + c] = cscale(A[j * dmax + c], rinv);
+    __syncthreads();
+    const int m = d - j - 1;
+    for (int e = tid; e < m * m; e += 256) {
+      const int ai = j + 1 + e / m, ci = j + 1 + e % m;
+      if (ai <= ci) {
+        cx<T> v = A[ai * dmax + ci];
+        cfma_jc(v, cscale(A[j * dmax + ai], T(-1)), A[j * dmax + ci]);
+        A[ai * dmax + ci] = v;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < d * d; e += 256) {
+    const int i = e / d, j = e - i * d;
+    Gy[i * dmax + j] = (j >= i) ? A[i * dmax + j] : cmk<T>(0, 0);
+  }
+  for (int c = tid; c < d; c += 256) {
+    w.rinv[(size_t)b * dmax + c] = rv[c];
+    gdrop[c] = drop[c];
+  }
+}
+
+// Q <- Q R^{-1}, one thread per row of Q (K x dmax, columns >= d untouched: zero)
+template <class T>
+__global__ void fwdsubst_kernel(const StepArgs<T> a, const Bufs<T> w, int d) {
+  const int b = blockIdx.y;
+  if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.K) return;
+  const int dmax = w.dmax;
+  cx<T>* q = w.Q + (size_t)b * w.L.sOm + (size_t)i * dmax;
+  const cx<T>* R = w.Gy + (size_t)b * w.L.sGy;
+  const T* rv = w.rinv + (size_t)b * dmax;
+  for (int c = 0; c < d; ++c) {
+    cx<T> v = q[c];
+    for (int a2 = 0; a2 < c; ++a2) cfma(v, cscale(q[a2], T(-1)), R[a2 * dmax + c]);
+    q[c] = cscale(v, rv[c]);
+  }
+}
+
+// Cyclic Jacobi eigendecomposition of E (d x d Hermitian, ld dmax): eigenvalues to lam,
+// eigenvectors (columns) to Uh.  Round-robin pairs, one CTA per instance.
+template <class T>
+__global__ void __launch_bounds__(256) jacobi_kernel(const Bufs<T> w, int d) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int b = blockIdx.x, tid = threadIdx.x, dmax = w.dmax;
+  if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
+  cx<T>* E = reinterpret_cast<cx<T>*>(sm);
+  cx<T>* U = E + (size_t)dmax * dmax;
+  cx<T>* ph = U + (size_t)dmax * dmax;
+  T* rc = reinterpret_cast<T*>(ph + dmax);
+  T* rs = rc + dmax;
+  T* red = rs + dmax;
+  int* pp = reinterpret_cast<int*>(red + 40);
+  int* pq = pp + dmax;
+  const cx<T>* Eg = w.E + (size_t)b * w.L.sGy;
+  for (int e = tid; e < d * d; e += 256) {
+    const int i = e / d, j = e - i * d;
+    E[i * dmax + j] = Eg[i * dmax + j];
+    U[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
+  }
+  __syncthreads();
+  const int dd = d + (d & 1), npairs = dd >> 1, dm1 = dd - 1;
+  const T eps = (sizeof(T) == 4) ? T(1e-10) : T(1e-26);
+  for (int sweep = 0; sweep < ((sizeof(T) == 4) ? 12 : 20); ++sweep) {
+    T off = 0, tot = 0;
+    for (int e = tid; e < d * d; e += 256) {
+      const int i = e / d, j = e - i * d;
+      const T v = cabs2(E[i * dmax + j]);
+      tot += v;
+      if (i != j) off += v;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (!(off > eps * tot)) break;
+    for (int rnd = 0; rnd < dm1; ++rnd) {
+      for (int k = tid; k < npairs; k += 256) {
+        int p0, q0;
+        if (k == 0) { p0 = 0; q0 = 1 + rnd; }
+        else {
+          int a1 = k + rnd, a2 = dm1 - k + rnd;
+          if (a1 >= dm1) a1 -= dm1;
+          if (a2 >= dm1) a2 -= dm1;
+          p0 = 1 + a1;
+          q0 = 1 + a2;
+        }
+        const int p1 = min(p0, q0), q1 = max(p0, q0);
+        bool act = false;
+        T c = 1, s = 0;
+        cx<T> f = cmk<T>(1, 0);
+        if (q1 < d) {
+          const cx<T> bpq = E[p1 * dmax + q1];
+          const T ab = hypot(bpq.re, bpq.im);
+          if (ab > T(0)) {
+            const T inv = T(1) / ab;
+            f = cmk(bpq.re * inv, -bpq.im * inv);
+            const T tau = (E[q1 * dmax + q1].re - E[p1 * dmax + p1].re) * (T(0.5) * inv);
+            const T t = copysign(T(1), tau) / (fabs(tau) + sqrt(T(1) + tau * tau));
+            c = T(1) / sqrt(T(1) + t * t);
+            s = t * c;
+            act = true;
+          }
+        }
+        pp[k] = act ? p1 : -1;
+        pq[k] = q1;
+        rc[k] = c;
+        rs[k] = s;
+        ph[k] = f;
+      }
+      __syncthreads();
+      for (int e = tid; e < npairs * d; e += 256) {
+        const int k = e / d, i = e - k * d;
+        const int p1 = pp[k];
+        if (p1 < 0) continue;
+        const int q1 = pq[k];
+        const T c = rc[k], s = rs[k];
+        const cx<T> ep = E[i * dmax + p1], eq = cmul(ph[k], E[i * dmax + q1]);
+        E[i * dmax + p1] = csub(cscale(ep, c), cscale(eq, s));
+        E[i * dmax + q1] = cadd(cscale(ep, s), cscale(eq, c));
+        const cx<T> up = U[i * dmax + p1], uq = cmul(ph[k], U[i * dmax + q1]);
+        U[i * dmax + p1] = csub(cscale(up, c), cscale(uq, s));
+        U[i * dmax + q1] = cadd(cscale(up, s), cscale(uq, c));
+      }
+      __syncthreads();
+      for (int e = tid; e < npairs * d; e += 256) {
+        const int k = e / d, j = e - k * d;
+        const int p1 = pp[k];
+        if (p1 < 0) continue;
+        const int q1 = pq[k];
+        const T c = rc[k], s = rs[k];
+        const cx<T> ep = E[p1 * dmax + j], eq = cmul(cconj(ph[k]), E[q1 * dmax + j]);
+        E[p1 * dmax + j] = csub(cscale(ep, c), cscale(eq, s));
+        E[q1 * dmax + j] = cadd(cscale(ep, s), cscale(eq, c));
+      }
+      __syncthreads();
+    }
+  }
+  cx<T>* Ug = w.Uh + (size_t)b * w.L.sGy;
+  for (int e = tid; e < d * d; e += 256) {
+    const int i = e / d, j = e - i * d;
+    Ug[i * dmax + j] = U[i * dmax + j];
+  }
+  for (int j = tid; j < d; j += 256) w.lam[(size_t)b * dmax + j] = fmax(E[j * dmax + j].re, T(0));
+}
+
+// Energy rule (eq. 14) and Algorithm 1's loop control; on exit the branch of Algorithm 2 and,
+// for a Woodbury step, U_r = U_hat(:, leading r) zero-padded to dmax x rcap.
+template <class T>
+__global__ void __launch_bounds__(256) rank_kernel(const StepArgs<T> a, const Bufs<T> w, int it,
+                                                   int d, int last) {
+  __shared__ int perm[512];
+  __shared__ int rsh;
+  const int b = blockIdx.x, tid = threadIdx.x, dmax = w.dmax, rcap = w.rcap;
+  if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
+  const T* lam = w.lam + (size_t)b * dmax;
+  for (int j = tid; j < d; j += 256) {
+    const T v = lam[j];
+    int rk = 0;
+    for (int i = 0; i < d; ++i) rk += (lam[i] > v || (lam[i] == v && i < j)) ? 1 : 0;
+    perm[rk] = j;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double cum = 0.0;
+    int rf = 0;
+    for (int j = 0; j < d; ++j) {
+      cum += (double)lam[perm[j]];
+      if (cum >= w.et[b]) { rf = j + 1; break; }
+    }
+    int* ctl = w.ctl + 8 * b;
+    if (rf > 0 || last) {
+      const int r = rf > 0 ? rf : d;
+      ctl[C_R] = r;
+      ctl[C_D] = d;
+      ctl[C_ITERS] = it + 1;
+      ctl[C_ACTIVE] = 0;
+      const bool wb = !(r > a.r_max || (double)r / (double)a.K > a.switch_ratio);
+      ctl[C_BRANCH] = wb ? WBRZF_BRANCH_WOODBURY : WBRZF_BRANCH_RANK;
+      rsh = wb ? r : -1;
+    } else {
+      ctl[C_K0] *= 2;
+      rsh = -1;
+    }
+    for (int j = 0; j < d; ++j) w.perm[(size_t)b * dmax + j] = perm[j];
+    if (a.trace != nullptr && (rf > 0 || last)) {
+      T* tr = reinterpret_cast<T*>(a.trace + (size_t)b * a.trace_stride);
+      const int e2 = 2 * ctl[C_EXP];
+      for (int j = 0; j < dmax; ++j) tr[j] = (j < d) ? (T)ldexp((double)lam[perm[j]], e2) : T(0);
+    }
+  }
+  __syncthreads();
+  const int r = rsh;
+  if (r < 0) return;
+  const cx<T>* Uh = w.Uh + (size_t)b * w.L.sGy;
+  cx<T>* Ur = w.Ur + (size_t)b * w.L.sUr;
+  for (int e = tid; e < dmax * rcap; e += 256) {
+    const int i = e / rcap, c = e - i * rcap;
+    Ur[e] = (i < d && c < r) ? Uh[i * dmax + perm[c]] : cmk<T>(0, 0);
+  }
+}
+
+// Capacitance matrix: Cm <- (I + Cm)^{-1} on the leading r x r block (r = the instance's rank;
+// the rest of the rcap x rcap buffer becomes zero, as T and Z vanish there) by Gauss-Jordan
+// with partial pivoting; a numerically singular pivot sends the instance to the direct
+// inverse (fallback branch).
+template <class T>
+__global__ void __launch_bounds__(256) capinv_kernel(const Bufs<T> w) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int b = blockIdx.x, tid = threadIdx.x, rcap = w.rcap;
+  if (!gate_ok(w.ctl, b, C_BRANCH, 1 << WBRZF_BRANCH_WOODBURY)) return;
+  const int n = w.ctl[8 * b + C_R], ld = 2 * n;
+  cx<T>* A = reinterpret_cast<cx<T>*>(sm);
+  cx<T>* col = A + (size_t)rcap * 2 * rcap;
+  T* red = reinterpret_cast<T*>(col + rcap);
+  __shared__ int piv_row, singular;
+  cx<T>* Cm = w.Cm + (size_t)b * w.L.sCm;
+  T cmax = 0;
+  for (int e = tid; e < n * ld; e += 256) {
+    const int i = e / ld, j = e - i * ld;
+    cx<T> v;
+    if (j < n) {
+      v = cadd(Cm[i * rcap + j], cmk<T>(i == j ? T(1) : T(0), T(0)));
+      cmax = fmax(cmax, sqrt(cabs2(v)));
+    } else {
+      v = cmk<T>((j - n) == i ? T(1) : T(0), T(0));
+    }
+    A[e] = v;
+  }
+  for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+  if ((tid & 31) == 0) red[tid >> 5] = cmax;
+  if (tid == 0) singular = 0;
+  __syncthreads();
+  cmax = 0;
+  for (int q = 0; q < 8; ++q) cmax = fmax(cmax, red[q]);
+  const T tol = cmax * ((sizeof(T) == 4) ? T(1e-6) : T(1e-14));
+  for (int c = 0; c < n; ++c) {
+    if (tid == 0) {
+      int pr = c;
+      T best = -1;
+      for (int i = c; i < n; ++i) {
+        const T v = cabs2(A[i * ld + c]);
+        if (v > best) { best = v; pr = i; }
+      }
+      piv_row = pr;
+      if (!(sqrt(best) > tol) || !isfinite(best)) singular = 1;
+    }
+    __syncthreads();
+    const int pr = piv_row;
+    if (pr != c) {
+      for (int j = tid; j < ld; j += 256) {
+        const cx<T> t0 = A[c * ld + j];
+        A[c * ld + j] = A[pr * ld + j];
+        A[pr * ld + j] = t0;
+      }
+      __syncthreads();
+    }
+    const cx<T> ip = crecip(A[c * ld + c]);
+    for (int i = tid; i < n; i += 256) col[i] = A[i * ld + c];
+    __syncthreads();
+    for (int j = tid; j < ld; j += 256) A[c * ld + j] = cmul(A[c * ld + j], ip);
+    __syncthreads();
+    for (int e = tid; e < n * ld; e += 256) {
+      const int i = e / ld, j = e - i * ld;
+      if (i != c) A[e] = csub(A[e], cmul(col[i], A[c * ld + j]));
+    }
+    __syncthreads();
+  }
+  if (singular) {
+    if (tid == 0) w.ctl[8 * b + C_BRANCH] = WBRZF_BRANCH_FALLBACK;
+    return;
+  }
+  for (int e = tid; e < rcap * rcap; e += 256) {
+    const int i = e / rcap, j = e - i * rcap;
+    Cm[e] = (i < n && j < n) ? A[i * ld + n + j] : cmk<T>(0, 0);
+  }
+}
+
+// Trace of a Woodbury step: L (K x rcap) and R^H (rcap x K), zero beyond the rank
+template <class T>
+__global__ void trace_lr_kernel(const StepArgs<T> a, const Bufs<T> w) {
+  const int b = blockIdx.y;
+  if (!gate_ok(w.ctl, b, C_BRANCH, 1 << WBRZF_BRANCH_WOODBURY)) return;
+  const size_t n = (size_t)a.K * w.rcap;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  cx<T>* trl = reinterpret_cast<cx<T>*>(a.trace + (size_t)b * a.trace_stride +
+                                        align_up((size_t)w.dmax * sizeof(T), 16));
+  trl[e] = w.Lm[(size_t)b * w.L.sL + e];
+  trl[n + e] = w.Rh[(size_t)b * w.L.sRh + e];
+}
+
+template <class T>
+__global__ void copy_gx_kernel(const StepArgs<T> a, const Bufs<T> w) {
+  const int b = blockIdx.y;
+  if (!gate_ok(w.ctl, b, C_BRANCH, kDirectMask)) return;
+  const size_t KK = (size_t)a.K * a.K;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < KK) a.Xs[(size_t)b * KK + idx] = a.Gs[(size_t)b * KK + idx];
+}
+
+// Pivot block P = [32p, 32p + bs): PC = X[:, P], PR = X[P, :], Pb = X[P, P]
+template <class T>
+__global__ void panel_kernel(const StepArgs<T> a, const Bufs<T> w, int p, int bs) {
+  const int b = blockIdx.y;
+  if (!gate_ok(w.ctl, b, C_BRANCH, kDirectMask)) return;
+  const int K = a.K, e = blockIdx.x * blockDim.x + threadIdx.x;
+  const cx<T>* X = a.Xs + (size_t)b * K * K;
+  if (e < K * 32) {
+    const int i = e >> 5, c = e & 31;
+    w.PC[(size_t)b * w.L.sPC + e] = (c < bs) ? X[(size_t)i * K + 32 * p + c] : cmk<T>(0, 0);
+    w.PR[(size_t)b * w.L.sPR + (size_t)c * K + i] = (c < bs) ? X[(size_t)(32 * p + c) * K + i] : cmk<T>(0, 0);
+    if (i < 32)
+      w.Pb[(size_t)b * w.L.sPb + (size_t)i * 32 + c] =
+          (i < bs && c < bs) ? X[(size_t)(32 * p + i) * K + 32 * p + c] : cmk<T>(0, 0);
+  }
+}
+
+// Pb <- Pb^{-1} (bs x bs Hermitian positive definite) by Gauss-Jordan exchange steps
+template <class T>
+__global__ void __launch_bounds__(256) blockinv_kernel(const Bufs<T> w, int bs) {
+  __shared__ cx<T> A[32][33];
+  __shared__ cx<T> colp[32], rowp[32];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  if (!gate_ok(w.ctl, b, C_BRANCH, kDirectMask)) return;
+  cx<T>* P = w.Pb + (size_t)b * w.L.sPb;
+  for (int e = tid; e < 32 * 32; e += 256) A[e >> 5][e & 31] = P[e];
+  __syncthreads();
+  bool bad = false;
+  for (int p = 0; p < bs; ++p) {
+    if (tid < bs) { colp[tid] = A[tid][p]; rowp[tid] = A[p][tid]; }
+    __syncthreads();
+    const cx<T> ap = colp[p];
+    if (!(ap.re > T(0)) || !cfinite(ap)) bad = true;
+    const cx<T> ia = crecip(ap);
+    for (int e = tid; e < bs * bs; e += 256) {
+      const int i = e / bs, j = e - i * bs;
+      cx<T> v;
+      if (i == p && j == p) v = ia;
+      else if (i == p) v = cscale(cmul(rowp[j], ia), T(-1));
+      else if (j == p) v = cmul(colp[i], ia);
+      else v = csub(A[i][j], cmul(colp[i], cmul(rowp[j], ia)));
+      A[i][j] = v;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < 32 * 32; e += 256) P[e] = A[e >> 5][e & 31];
+  if (bad && tid == 0) atomicOr(&w.ctl[8 * b + C_STATUS], WBRZF_STATUS_NOT_PD);
+}
+
+// Write the exchanged pivot rows / columns back: X[P,P] = Pb^{-1}, X[i,P] = U[i] (i not in P),
+// X[P,j] = -V[j] (j not in P); the rest of X already holds X - U R.
+template <class T>
+__global__ void fixup_kernel(const StepArgs<T> a, const Bufs<T> w, int p, int bs) {
+  const int b = blockIdx.y;
+  if (!gate_ok(w.ctl, b, C_BRANCH, kDirectMask)) return;
+  const int K = a.K, e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K * 32) return;
+  const int i = e >> 5, c = e & 31;
+  if (c >= bs) return;
+  cx<T>* X = a.Xs + (size_t)b * K * K;
+  const int P0 = 32 * p;
+  const bool inP = i >= P0 && i < P0 + bs;
+  // column entry (i, P0 + c)
+  X[(size_t)i * K + P0 + c] = inP ? w.Pb[(size_t)b * w.L.sPb + (size_t)(i - P0) * 32 + c]
+                                  : w.PU[(size_t)b * w.L.sPC + (size_t)i * 32 + c];
+  // row entry (P0 + c, i)
+  if (!inP) X[(size_t)(P0 + c) * K + i] = cscale(w.PV[(size_t)b * w.L.sPR + (size_t)c * K + i], T(-1));
+}
+
+// On entry D = M = (G - alpha I) X = H H^H X: scale s, per-user SINR and the sum-rate (eq. 15)
+template <class T>
+__global__ void __launch_bounds__(256) sinr_kernel(const StepArgs<T> a, const Bufs<T> w) {
+  __shared__ T red[40];
+  const int b = blockIdx.x, tid = threadIdx.x, K = a.K, KK = K * K;
+  const cx<T>* M = w.D + (size_t)b * w.L.sD;
+  const cx<T>* X = a.Xs + (size_t)b * KK;
+  const T sigma2 = a.sigma2[b];
+  T part = 0;
+  for (int idx = tid; idx < KK; idx += 256) {
+    const cx<T> x = X[idx], m = M[idx];
+    part += x.re * m.re + x.im * m.im;
+  }
+  const T wn2 = block_sum(part, red);
+  const T s = sqrt(a.p_t / wn2);
+  T rate = 0;
+  for (int n = tid; n < K; n += 256) {
+    const T sig = s * s * cabs2(M[(size_t)n * K + n]);
+    T intf = 0;
+    for (int i = 0; i < K; ++i)
+      if (i != n) intf += cabs2(M[(size_t)n * K + i]);
+    intf *= s * s;
+    const T sn = sig / (intf + sigma2);
+    a.sinr[(size_t)b * K + n] = (float)sn;
+    rate += log2(T(1) + sn);
+  }
+  const T R = block_sum(rate, red);
+  if (tid == 0) {
+    const int* ctl = w.ctl + 8 * b;
+    int status = ctl[C_STATUS];
+    if (!isfinite(s) || !isfinite(R)) status |= WBRZF_STATUS_NONFINITE;
+    wbrzf_step_info inf;
+    inf.branch = ctl[C_BRANCH];
+    inf.r = ctl[C_R];
+    inf.iters = ctl[C_ITERS];
+    inf.d = ctl[C_D];
+    inf.dg_fro2 = (float)w.nrm[2 * b];
+    inf.scale = (float)s;
+    inf.sum_rate = (float)R;
+    inf.status = status;
+    a.info[b] = inf;
+    w.ws[b] = s;
+  }
+}
+
+// ---------------------------------------------------------------- the snapshot sequence
+template <class T>
+cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t s, int* launches) {
+  const int B = a.batch, K = a.K, N = a.N, dmax = a.dmax, rcap = a.rcap;
+  const Bufs<T> w = make_bufs<T>(base, B, K, dmax, rcap);
+  const BlockedLayout& L = w.L;
+  const size_t KK = (size_t)K * K;
+  cudaError_t e;
+  int nl = 0;
+  *launches = 0;
+#define WB_TRY(x) do { e = (x); if (e != cudaSuccess) return e; ++nl; } while (0)
+  const BlockedSmem sm = blocked_smem(dmax, rcap, sizeof(cx<T>), sizeof(T));
+  const size_t js = sm.jacobi, cs = sm.cholesky, ps = sm.capinv;
+  e = cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)js);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(cholesky_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(capinv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+  if (e != cudaSuccess) return e;
+  const T one = T(1), zero = T(0);
+  // Gram H H^H into D, then G_t, dG
+  WB_TRY(gemm<T>(s, B, K, K, N, a.H, N, (size_t)K * N, 0, a.H, N, (size_t)K * N, 1, w.D, K, L.sD,
+                 one, nullptr, zero, nullptr, 0, 0));
+  finish_gram_kernel<T><<<B, 256, 0, s>>>(a, w);
+  WB_TRY(cudaGetLastError());
+  if (a.mode == MODE_UPDATE) {
+    long long k0 = a.k_init;
+    for (int it = 0; it < a.i_max; ++it) {
+      const int d = (int)(k0 + a.p < K ? k0 + a.p : K);
+      const int last = it == a.i_max - 1;
+      const int nq = (dmax + 1) / 2;
+      omega_kernel<T><<<dim3((K * nq + 255) / 256, B), 256, 0, s>>>(a, w, it, d);
+      WB_TRY(cudaGetLastError());
+      WB_TRY(gemm<T>(s, B, K, dmax, K, w.D, K, L.sD, 0, w.Om, dmax, L.sOm, 0, w.Q, dmax, L.sOm,
+                     one, nullptr, zero, w.ctl, C_ACTIVE, 2));
+      for (int pass = 0; pass < 2; ++pass) {
+        WB_TRY(gemm<T>(s, B, d, d, K, w.Q, dmax, L.sOm, 1, w.Q, dmax, L.sOm, 0, w.Gy, dmax,
+                       L.sGy, one, nullptr, zero, w.ctl, C_ACTIVE, 2));
+        cholesky_kernel<T><<<B, 256, cs, s>>>(w, d, pass);
+        WB_TRY(cudaGetLastError());
+        fwdsubst_kernel<T><<<dim3((K + 127) / 128, B), 128, 0, s>>>(a, w, d);
+        WB_TRY(cudaGetLastError());
+      }
+      WB_TRY(gemm<T>(s, B, dmax, K, K, w.Q, dmax, L.sOm, 1, w.D, K, L.sD, 0, w.Bm, K, L.sBm,
+                     one, nullptr, zero, w.ctl, C_ACTIVE, 2));
+      WB_TRY(gemm<T>(s, B, d, d, K, w.Bm, K, L.sBm, 0, w.Bm, K, L.sBm, 1, w.E, dmax, L.sGy,
+                     one, nullptr, zero, w.ctl, C_ACTIVE, 2));
+      jacobi_kernel<T><<<B, 256, js, s>>>(w, d);
+      WB_TRY(cudaGetLastError());
+      rank_kernel<T><<<B, 256, 0, s>>>(a, w, it, d, last);
+      WB_TRY(cudaGetLastError());
+      if (k0 < K) k0 *= 2;
+    }
+    const int g = 1 << WBRZF_BRANCH_WOODBURY;
+    // L = Q U_r, R^H = nu U_r^H B (nu undoes the scaling of dG), T = X L, Z = R^H X, C = Z L
+    WB_TRY(gemm<T>(s, B, K, rcap, dmax, w.Q, dmax, L.sOm, 0, w.Ur, rcap, L.sUr, 0, w.Lm, rcap,
+                   L.sL, one, nullptr, zero, w.ctl, C_BRANCH, g));
+    WB_TRY(gemm<T>(s, B, rcap, K, dmax, w.Ur, rcap, L.sUr, 1, w.Bm, K, L.sBm, 0, w.Rh, K,
+                   L.sRh, one, w.nu, zero, w.ctl, C_BRANCH, g));
+    if (a.trace != nullptr) {
+      trace_lr_kernel<T><<<dim3((unsigned)((K * (size_t)rcap + 255) / 256), B), 256, 0, s>>>(a, w);
+      WB_TRY(cudaGetLastError());
+    }
+    WB_TRY(gemm<T>(s, B, K, rcap, K, a.Xs, K, KK, 0, w.Lm, rcap, L.sL, 0, w.Tm, rcap, L.sL,
+                   one, nullptr, zero, w.ctl, C_BRANCH, g));
+    WB_TRY(gemm<T>(s, B, rcap, K, K, w.Rh, K, L.sRh, 0, a.Xs, K, KK, 0, w.Z, K, L.sRh, one,
+                   nullptr, zero, w.ctl, C_BRANCH, g));
+    WB_TRY(gemm<T>(s, B, rcap, rcap, K, w.Z, K, L.sRh, 0, w.Lm, rcap, L.sL, 0, w.Cm, rcap,
+                   L.sCm, one, nullptr, zero, w.ctl, C_BRANCH, g));
+    capinv_kernel<T><<<B, 256, ps, s>>>(w);
+    WB_TRY(cudaGetLastError());
+    WB_TRY(gemm<T>(s, B, rcap, K, rcap, w.Cm, rcap, L.sCm, 0, w.Z, K, L.sRh, 0, w.CZ, K, L.sRh,
+                   one, nullptr, zero, w.ctl, C_BRANCH, g));
+    WB_TRY(gemm<T>(s, B, K, K, rcap, w.Tm, rcap, L.sL, 0, w.CZ, K, L.sRh, 0, a.Xs, K, KK,
+                   T(-1), nullptr, one, w.ctl, C_BRANCH, g));
+  }
+  // direct inverse by block exchange steps (instances whose branch asks for it)
+  copy_gx_kernel<T><<<dim3((unsigned)((KK + 255) / 256), B), 256, 0, s>>>(a, w);
+  WB_TRY(cudaGetLastError());
+  const int nb = (K + 31) / 32;
+  for (int p = 0; p < nb; ++p) {
+    const int bs = (K - 32 * p) < 32 ? (K - 32 * p) : 32;
+    panel_kernel<T><<<dim3((K * 32 + 255) / 256, B), 256, 0, s>>>(a, w, p, bs);
+    WB_TRY(cudaGetLastError());
+    blockinv_kernel<T><<<B, 256, 0, s>>>(w, bs);
+    WB_TRY(cudaGetLastError());
+    WB_TRY(gemm<T>(s, B, K, bs, bs, w.PC, 32, L.sPC, 0, w.Pb, 32, L.sPb, 0, w.PU, 32, L.sPC,
+                   one, nullptr, zero, w.ctl, C_BRANCH, kDirectMask));
+    WB_TRY(gemm<T>(s, B, bs, K, bs, w.Pb, 32, L.sPb, 0, w.PR, K, L.sPR, 0, w.PV, K, L.sPR, one,
+                   nullptr, zero, w.ctl, C_BRANCH, kDirectMask));
+    WB_TRY(gemm<T>(s, B, K, K, bs, w.PU, 32, L.sPC, 0, w.PR, K, L.sPR, 0, a.Xs, K, KK, T(-1),
+                   nullptr, one, w.ctl, C_BRANCH, kDirectMask));
+    fixup_kernel<T><<<dim3((K * 32 + 255) / 256, B), 256, 0, s>>>(a, w, p, bs);
+    WB_TRY(cudaGetLastError());
+  }
+  // SINR and scale, then W = s H^H X.  M = (G - alpha I) X: the shift is applied to G before
+  // the product, since G X - alpha X cancels to about I - I when alpha dominates H H^H.
+  WB_TRY(gemm<T>(s, B, K, K, K, a.Gs, K, KK, 0, a.Xs, K, KK, 0, w.D, K, L.sD, one, nullptr,
+                 zero, nullptr, 0, 0, a.alpha));
+  sinr_kernel<T><<<B, 256, 0, s>>>(a, w);
+  WB_TRY(cudaGetLastError());
+  WB_TRY(gemm<T>(s, B, N, K, K, a.H, N, (size_t)K * N, 1, a.Xs, K, KK, 0, a.W, K, (size_t)N * K,
+                 one, w.ws, zero, nullptr, 0, 0));
+#undef WB_TRY
+  *launches = nl;
+  return cudaSuccess;
+}
+}  // namespace
+}  // namespace wbk
+
+namespace wbk {
+cudaError_t run_blocked_f32(const StepArgs<float>& a, unsigned char* base, cudaStream_t s,
+                            int* launches) {
+  return run_blocked<float>(a, base, s, launches);
+}
+cudaError_t run_blocked_f64(const StepArgs<double>& a, unsigned char* base, cudaStream_t s,
+                            int* launches) {
+  return run_blocked<double>(a, base, s, launches);
+}
+}  // namespace wbk

@@ -126,6 +126,69 @@ __host__ __device__ inline size_t tc_smem_bytes(int K, int dmax, int rcap) {
   return tc_layout(K, dmax, rcap).bytes_unpadded + 1024;
 }
 
+// ---------------------------------------------------------------- blocked (any-K) engine
+// Per-instance scratch of the multi-kernel engine, carved after the common workspace.  Every
+// buffer is batch-strided; `ld` values are the leading dimensions the kernels use.
+struct BlockedLayout {
+  // complex buffers (offsets in bytes from the blocked base, per-instance strides in elements)
+  size_t oD, oOm, oQ, oGy, oBm, oE, oUh, oUr, oL, oT, oRh, oZ, oCm, oCZ, oPC, oPR, oPU, oPV, oPb;
+  size_t sD, sOm, sGy, sBm, sUr, sL, sRh, sCm, sPC, sPR, sPb;
+  // real / double / int arrays
+  size_t oLam, oRinv, oWs, oNu, oEt, oNrm, oCtl, oPerm, oDrop;
+  size_t bytes;
+};
+
+__host__ __device__ inline BlockedLayout blocked_layout(int batch, int K, int dmax, int rcap,
+                                                       size_t cxb, size_t tb) {
+  BlockedLayout L;
+  const size_t B = (size_t)batch;
+  size_t o = 0;
+  auto take = [&](size_t elems, size_t esz) {
+    const size_t at = o;
+    o = align_up(o + B * elems * esz, 256);
+    return at;
+  };
+  L.sD = (size_t)K * K;          L.oD = take(L.sD, cxb);
+  L.sOm = (size_t)K * dmax;      L.oOm = take(L.sOm, cxb);   L.oQ = take(L.sOm, cxb);
+  L.sGy = (size_t)dmax * dmax;   L.oGy = take(L.sGy, cxb);   L.oE = take(L.sGy, cxb);
+                                 L.oUh = take(L.sGy, cxb);
+  L.sBm = (size_t)dmax * K;      L.oBm = take(L.sBm, cxb);
+  L.sUr = (size_t)dmax * rcap;   L.oUr = take(L.sUr, cxb);
+  L.sL = (size_t)K * rcap;       L.oL = take(L.sL, cxb);     L.oT = take(L.sL, cxb);
+  L.sRh = (size_t)rcap * K;      L.oRh = take(L.sRh, cxb);   L.oZ = take(L.sRh, cxb);
+                                 L.oCZ = take(L.sRh, cxb);
+  L.sCm = (size_t)rcap * rcap;   L.oCm = take(L.sCm, cxb);
+  L.sPC = (size_t)K * 32;        L.oPC = take(L.sPC, cxb);   L.oPU = take(L.sPC, cxb);
+  L.sPR = (size_t)32 * K;        L.oPR = take(L.sPR, cxb);   L.oPV = take(L.sPR, cxb);
+  L.sPb = 32 * 32;               L.oPb = take(L.sPb, cxb);
+  L.oLam = take((size_t)dmax, tb);
+  L.oRinv = take((size_t)dmax, tb);
+  L.oWs = take(1, tb);
+  L.oNu = take(1, tb);
+  L.oEt = take(1, 8);
+  L.oNrm = take(2, 8);
+  L.oCtl = take(8, 4);
+  L.oPerm = take((size_t)dmax, 4);
+  L.oDrop = take((size_t)dmax, 4);
+  L.bytes = o;
+  return L;
+}
+
+// Dynamic shared memory of the blocked engine's per-instance kernels: the Jacobi sweep holds
+// E and U_hat (dmax x dmax each) plus per-pair rotations, the Cholesky kernel the d x d Gram
+// matrix, the capacitance kernel [C | I] (rcap x 2 rcap).
+struct BlockedSmem {
+  size_t jacobi, cholesky, capinv;
+};
+__host__ __device__ inline BlockedSmem blocked_smem(int dmax, int rcap, size_t cxb, size_t tb) {
+  BlockedSmem s;
+  s.jacobi = 2 * (size_t)dmax * dmax * cxb + (size_t)dmax * cxb + (2 * (size_t)dmax + 40) * tb +
+             2 * (size_t)dmax * sizeof(int) + 64;
+  s.cholesky = (size_t)dmax * dmax * cxb + 2 * (size_t)dmax * tb + (size_t)dmax * sizeof(int) + 64;
+  s.capinv = 2 * (size_t)rcap * rcap * cxb + (size_t)rcap * cxb + 8 * tb + 64;
+  return s;
+}
+
 // Trace record of one instance: sigma_hat^2 [dmax] (T), L [K][rcap] and R^H [rcap][K] (cx<T>).
 __host__ __device__ inline size_t trace_record_bytes(int K, int dmax, int rcap, size_t cx_bytes,
                                                      size_t t_bytes) {
@@ -135,6 +198,13 @@ __host__ __device__ inline size_t trace_record_bytes(int K, int dmax, int rcap, 
 // Launch wrappers, one per real type (defined in step_f32.cu / step_f64.cu).
 cudaError_t launch_step_f32(const StepArgs<float>& a, size_t smem, cudaStream_t s);
 cudaError_t launch_step_f64(const StepArgs<double>& a, size_t smem, cudaStream_t s);
+// Blocked engine (any K): a fixed sequence of batched kernels on `stream`; `base` is the
+// blocked scratch (blocked_layout) of the workspace (blocked.cu).
+// *launches receives the number of kernels enqueued.
+cudaError_t run_blocked_f32(const StepArgs<float>& a, unsigned char* base, cudaStream_t s,
+                            int* launches);
+cudaError_t run_blocked_f64(const StepArgs<double>& a, unsigned char* base, cudaStream_t s,
+                            int* launches);
 // Tensor-core kernel (complex64, K <= 32, even N); hmap: H as a 2-D FP32 tensor map
 // {2N, batch K}, box {64, K} (step_tc.cu).  `hmap` points to a CUtensorMap.
 cudaError_t launch_step_tc(const StepArgs<float>& a, const void* hmap, size_t smem,

@@ -750,7 +750,10 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
   }
 
   // ---------------------------------------------------------------- 6. scale and SINR
-  // M = G X - alpha X = H H^H X  (into D)
+  // M = (G - alpha I) X = H H^H X  (into D).  The shift goes into G first (G is dead after
+  // this product): G X - alpha X would cancel to about I - I where alpha dominates H H^H.
+  if (tid < K) G[tid * K + tid].re -= alpha;
+  __syncthreads();
   if (K <= 32) {
     // warp w: rows w, w + 8, w + 16, w + 24; lane: column.  G rows are warp-uniform loads,
     // each X[k][lane] is loaded once and used for all four rows.
@@ -758,10 +761,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
     if (j < K) {
       cx<T> acc[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = w8 + 8 * q;
-        acc[q] = (i < K) ? cscale(X[i * K + j], -alpha) : cmk<T>(0, 0);
-      }
+      for (int q = 0; q < 4; ++q) acc[q] = cmk<T>(0, 0);
       for (int k = 0; k < K; ++k) {
         const cx<T> xk = X[k * K + j];
 #pragma unroll
@@ -779,7 +779,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
   } else {
     for (int idx = tid; idx < KK; idx += kThreads) {
       const int i = idx / K, j = idx - i * K;
-      cx<T> acc = cscale(X[idx], -alpha);
+      cx<T> acc = cmk<T>(0, 0);
       for (int k = 0; k < K; ++k) cfma(acc, G[i * K + k], X[k * K + j]);
       D[idx] = acc;
     }

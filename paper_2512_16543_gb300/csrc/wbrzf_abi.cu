@@ -94,6 +94,29 @@ bool resolve_rule(const wbrzf_rank_rule* rule, int K, Resolved* out) {
   return true;
 }
 
+bool simt_fits(int K, const Resolved& r, wbrzf_precision prec) {
+  return K <= kMaxK && simt_smem_bytes(K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec)) <=
+                           227 * 1024;
+}
+
+bool blocked_fits(int batch, const Resolved& r, wbrzf_precision prec) {
+  const BlockedSmem s = blocked_smem(r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec));
+  const size_t lim = 227 * 1024;
+  return batch <= 65535 && r.dmax <= 512 && s.jacobi <= lim && s.cholesky <= lim &&
+         s.capinv <= lim;
+}
+
+// Workspace: the common layout, then (blocked engine only) its scratch, 256-byte aligned.
+size_t blocked_offset(int batch, int K, wbrzf_precision prec) {
+  return align_up(ws_layout(batch, K, prec).bytes, 256);
+}
+
+size_t engine_bytes(int batch, int K, wbrzf_precision prec, const Resolved& r, bool blocked) {
+  if (!blocked) return ws_layout(batch, K, prec).bytes;
+  return blocked_offset(batch, K, prec) +
+         blocked_layout(batch, K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec)).bytes;
+}
+
 }  // namespace
 
 // cuTensorMapEncodeTiled from the driver, looked up once.
@@ -129,6 +152,9 @@ struct wbrzf {
   int engine;            // WBRZF_ENGINE_* requested
   int last_engine;       // kernel of the last launch
   size_t smem_tc;        // dynamic shared memory of the tensor-core kernel (0: not eligible)
+  size_t ws_bytes;       // workspace size given at creation
+  bool simt_ok;          // the single-CTA kernel fits (K <= kMaxK and its shared memory)
+  bool blocked_ok;       // the blocked engine's limits hold (workspace checked separately)
 };
 
 namespace {
@@ -187,11 +213,28 @@ bool encode_hmap(const wbrzf* h, const void* H, CUtensorMap* map) {
          CUDA_SUCCESS;
 }
 
+bool use_blocked(const wbrzf* h) {
+  return h->engine == WBRZF_ENGINE_BLOCKED || (h->engine == WBRZF_ENGINE_AUTO && !h->simt_ok);
+}
+
 wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
   if (!h || !H || !W) return WBRZF_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(H) | reinterpret_cast<uintptr_t>(W)) % cx_bytes(h->prec))
     return WBRZF_ERR_INVALID_ARG;
   cudaError_t e;
+  if (use_blocked(h)) {
+    unsigned char* base = h->ws + blocked_offset(h->batch, h->K, h->prec);
+    int nl = 0;
+    if (h->prec == WBRZF_C128)
+      e = run_blocked_f64(make_args<double>(h, H, W, mode, h->t), base, h->stream, &nl);
+    else
+      e = run_blocked_f32(make_args<float>(h, H, W, mode, h->t), base, h->stream, &nl);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->last_engine = WBRZF_ENGINE_BLOCKED;
+    h->launches += nl;
+    h->t += 1;
+    return WBRZF_OK;
+  }
   bool use_tc = h->engine != WBRZF_ENGINE_SIMT && tc_eligible(h) &&
                 (reinterpret_cast<uintptr_t>(H) % 16) == 0;
   alignas(64) CUtensorMap map;
@@ -215,13 +258,33 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
 
 extern "C" {
 
+size_t wbrzf_workspace_bytes_engine(int batch, int N, int K, wbrzf_precision prec,
+                                    const wbrzf_rank_rule* rule, int engine) {
+  Resolved r;
+  if (batch < 1 || batch > (1 << 28) || N < 1 || K < 1) return 0;
+  if (prec != WBRZF_C128 && prec != WBRZF_C64) return 0;
+  if (engine < WBRZF_ENGINE_AUTO || engine > WBRZF_ENGINE_BLOCKED) return 0;
+  if (!resolve_rule(rule, K, &r)) return 0;
+  const bool simt = simt_fits(K, r, prec), blocked = blocked_fits(batch, r, prec);
+  switch (engine) {
+    case WBRZF_ENGINE_AUTO:
+      if (simt) return engine_bytes(batch, K, prec, r, false);
+      return blocked ? engine_bytes(batch, K, prec, r, true) : 0;
+    case WBRZF_ENGINE_SIMT:
+      return simt ? engine_bytes(batch, K, prec, r, false) : 0;
+    case WBRZF_ENGINE_TENSOR:
+      return (simt && prec == WBRZF_C64 && K <= 32 && (N % 2) == 0 &&
+              tc_smem_bytes(K, r.dmax, r.rcap) <= 227 * 1024)
+                 ? engine_bytes(batch, K, prec, r, false)
+                 : 0;
+    default:
+      return blocked ? engine_bytes(batch, K, prec, r, true) : 0;
+  }
+}
+
 size_t wbrzf_workspace_bytes(int batch, int N, int K, wbrzf_precision prec,
                              const wbrzf_rank_rule* rule) {
-  Resolved r;
-  if (batch < 1 || N < 1 || K < 1 || K > kMaxK) return 0;
-  if (prec != WBRZF_C128 && prec != WBRZF_C64) return 0;
-  if (!resolve_rule(rule, K, &r)) return 0;
-  return ws_layout(batch, K, prec).bytes;
+  return wbrzf_workspace_bytes_engine(batch, N, K, prec, rule, WBRZF_ENGINE_AUTO);
 }
 
 wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const double* sigma2,
@@ -236,7 +299,6 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   if (method != WBRZF_METHOD_WB_ARSVD && method != WBRZF_METHOD_FULL_INVERSE)
     return WBRZF_ERR_INVALID_ARG;
   if (prec != WBRZF_C128 && prec != WBRZF_C64) return WBRZF_ERR_INVALID_ARG;
-  if (K > kMaxK) return WBRZF_ERR_UNSUPPORTED;
   if (reinterpret_cast<uintptr_t>(workspace) % 256) return WBRZF_ERR_INVALID_ARG;
   for (int b = 0; b < batch; ++b) {
     if (!(alpha[b] >= 0.0) || !(sigma2[b] > 0.0) || !isfinite(alpha[b]) || !isfinite(sigma2[b]))
@@ -245,9 +307,11 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   Resolved r;
   if (!resolve_rule(rule, K, &r)) return WBRZF_ERR_INVALID_ARG;
   const WsLayout wl = ws_layout(batch, K, prec);
-  if (workspace_bytes < wl.bytes) return WBRZF_ERR_WORKSPACE;
-  const size_t smem = simt_smem_bytes(K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec));
-  if (smem > 227 * 1024) return WBRZF_ERR_UNSUPPORTED;
+  const bool simt_ok = simt_fits(K, r, prec), blocked_ok = blocked_fits(batch, r, prec);
+  if (!simt_ok && !blocked_ok) return WBRZF_ERR_UNSUPPORTED;
+  if (workspace_bytes < engine_bytes(batch, K, prec, r, !simt_ok)) return WBRZF_ERR_WORKSPACE;
+  const size_t smem =
+      simt_ok ? simt_smem_bytes(K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec)) : 0;
 
   wbrzf* h = new (std::nothrow) wbrzf;
   if (!h) return WBRZF_ERR_INVALID_ARG;
@@ -269,9 +333,12 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   h->launches = 0;
   h->engine = WBRZF_ENGINE_AUTO;
   h->last_engine = 0;
+  h->ws_bytes = workspace_bytes;
+  h->simt_ok = simt_ok;
+  h->blocked_ok = blocked_ok;
   {
     const size_t tc = tc_smem_bytes(K, r.dmax, r.rcap);
-    h->smem_tc = (prec == WBRZF_C64 && K <= 32 && tc <= 227 * 1024) ? tc : 0;
+    h->smem_tc = (simt_ok && prec == WBRZF_C64 && K <= 32 && tc <= 227 * 1024) ? tc : 0;
   }
 
   // per-instance parameters in the kernel's real type
@@ -381,9 +448,15 @@ wbrzf_status wbrzf_set_instance_ids(wbrzf* h, const uint32_t* ids, int count) {
 }
 
 wbrzf_status wbrzf_set_engine(wbrzf* h, int engine) {
-  if (!h || engine < WBRZF_ENGINE_AUTO || engine > WBRZF_ENGINE_TENSOR)
+  if (!h || engine < WBRZF_ENGINE_AUTO || engine > WBRZF_ENGINE_BLOCKED)
     return WBRZF_ERR_INVALID_ARG;
   if (engine == WBRZF_ENGINE_TENSOR && !tc_eligible(h)) return WBRZF_ERR_UNSUPPORTED;
+  if (engine == WBRZF_ENGINE_SIMT && !h->simt_ok) return WBRZF_ERR_UNSUPPORTED;
+  if (engine == WBRZF_ENGINE_BLOCKED) {
+    if (!h->blocked_ok) return WBRZF_ERR_UNSUPPORTED;
+    if (h->ws_bytes < engine_bytes(h->batch, h->K, h->prec, h->rule, true))
+      return WBRZF_ERR_WORKSPACE;
+  }
   h->engine = engine;
   return WBRZF_OK;
 }

@@ -41,8 +41,21 @@ def test_host_side_validation_without_gpu(libpath):
     L = binding.lib()
     rule = binding.RankRule().to_c()
     assert L.wbrzf_workspace_bytes(0, 8, 8, binding.C64, ctypes.byref(rule)) == 0
-    assert L.wbrzf_workspace_bytes(4, 8, 65, binding.C64, ctypes.byref(rule)) == 0   # K > 64
     assert L.wbrzf_workspace_bytes(4, 64, 8, binding.C64, ctypes.byref(rule)) > 0
+    # K > 64 runs only on the blocked engine, which needs the sketch width within its limit:
+    # the default rule at K = 512 lets d grow to K (refused), r_max = 64 keeps d <= 72
+    eng = L.wbrzf_workspace_bytes_engine
+    simt, blocked = binding.ENGINES["simt"], binding.ENGINES["blocked"]
+    assert L.wbrzf_workspace_bytes(4, 8, 65, binding.C64, ctypes.byref(rule)) > 0
+    assert eng(4, 8, 65, binding.C64, ctypes.byref(rule), simt) == 0
+    assert L.wbrzf_workspace_bytes(1, 4096, 512, binding.C64, ctypes.byref(rule)) == 0
+    r64 = binding.RankRule(k_init=2, p=8, r_max=64).to_c()
+    assert L.wbrzf_workspace_bytes(1, 4096, 512, binding.C64, ctypes.byref(r64)) == \
+        eng(1, 4096, 512, binding.C64, ctypes.byref(r64), blocked) > 0
+    assert eng(4, 64, 8, binding.C64, ctypes.byref(rule), blocked) > \
+        L.wbrzf_workspace_bytes(4, 64, 8, binding.C64, ctypes.byref(rule))
+    assert eng(4, 64, 8, binding.C64, ctypes.byref(rule), 4) == 0           # no such engine
+    assert eng(4, 63, 8, binding.C64, ctypes.byref(rule), binding.ENGINES["tensor"]) == 0
     bad = binding.RankRule(eta=1.5).to_c()
     assert L.wbrzf_workspace_bytes(4, 64, 8, binding.C64, ctypes.byref(bad)) == 0
     a = (ctypes.c_double * 1)(0.8)

@@ -1,0 +1,166 @@
+"""Parity of the blocked engine (each step of the path a batched kernel of its own, any K) with
+the FP64 oracle, through the C ABI.
+
+Tolerances are those of the FMA engine (the arithmetic is the same, only the blocking and
+the order of the sums differ): complex128 X and W within 1e-10, sum-rate within 1e-9; complex64
+X and W within 1e-4, sum-rate within 1e-3 bit/s/Hz (K <= 128).  For the large array
+(N = 4096, K = 512) the FP32 Gram matrix is a sum of 4096 products per entry: its rounding
+error (about sqrt(N) u |G_ij|, 4e-6 per entry) is a sizeable fraction of dG (1.6e-5 of ||G||
+per 10 ms step), so the rank of eq. 14 on that nearly flat spectrum may move by a few
+components; X then moves by at most the dropped components' share of dG, far below the 1e-4
+bound on X and W that still holds.  The sum-rate of 512 users is held to 1e-5 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+from gpu_harness import relerr, run_gpu, run_oracle
+from oracle import rzf
+from paper_2512_16543_gb300 import binding, channel
+from test_gpu_parity import _check, _traj
+
+pytestmark = pytest.mark.gpu
+
+
+def test_blocked_complex128_single_trajectory():
+    """8x8 UPA, K = 8: every branch (init, Woodbury, periodic re-inverse) against the oracle."""
+    sc = channel.scenario_single_small()
+    Hs = _traj(sc, 2, 45, seed=101)
+    rule = binding.RankRule(eta=0.9, k_init=2, p=1, reinverse_period=20, seed=11)
+    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c128",
+                        engine="blocked")
+    assert meta["engine"] == "blocked"
+    assert meta["launches"] > 45                 # several kernels per snapshot
+    _check(gpu, Hs, sc, rule, "c128", engine="blocked")
+    branches = {g["info"][b]["branch"] for g in gpu for b in range(2)}
+    assert {1, 2, 3} <= branches
+
+
+@pytest.mark.parametrize("eta", [0.65, 0.99])
+def test_blocked_lowrank_factors_match_oracle(eta):
+    sc = channel.scenario_single_small()
+    Hs = _traj(sc, 2, 12, seed=202)
+    rule = binding.RankRule(eta=eta, k_init=2, p=1, reinverse_period=0, seed=3)
+    gpu, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c128", trace=True,
+                     engine="blocked")
+    nwb = 0
+    for b in range(2):
+        ref = run_oracle(Hs[:, b].numpy(), sc.alpha, sc.sigma2, sc.p_t, rule, instance=b)
+        for t in range(1, 12):
+            inf = gpu[t]["info"][b]
+            assert inf["branch"] == ref[t].branch and inf["r"] == ref[t].r
+            sig = gpu[t]["sig"][b][:inf["d"]]
+            np.testing.assert_allclose(sig, np.asarray(ref[t].sigma_hat) ** 2,
+                                       rtol=1e-9, atol=1e-12 * sig[0])
+            if inf["branch"] == 1:
+                nwb += 1
+                r = inf["r"]
+                prod = gpu[t]["L"][b][:, :r] @ gpu[t]["Rh"][b][:r]
+                assert relerr(prod, ref[t].lowrank_product) < 1e-9
+    assert nwb > 5
+
+
+def test_blocked_complex64_batched():
+    """16x16 UPA, K = 32, p = 8, r <= 16 on the blocked engine against the oracle."""
+    sc = channel.scenario_batched_256x32()
+    Hs = _traj(sc, 3, 25, seed=303)
+    rule = binding.RankRule(eta=0.9, k_init=2, p=8, r_max=16, reinverse_period=20, seed=5)
+    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64",
+                        engine="blocked")
+    assert meta["engine"] == "blocked"
+    assert _check(gpu, Hs, sc, rule, "c64", engine="blocked") <= 3
+
+
+def test_blocked_agrees_with_fma_engine():
+    """Same snapshots on the one-CTA FMA kernel and on the blocked engine: in FP64 the same
+    branches and ranks and X to 1e-12; in FP32 X to 1e-4."""
+    sc = channel.LeoScenario(n_x=25, n_y=4, K=17, disc_radius=50e3)
+    Hs = _traj(sc, 3, 12, seed=77)
+    rule = binding.RankRule(eta=0.85, k_init=2, p=3, r_max=8, reinverse_period=5, seed=8)
+    for prec, tol in (("c128", 1e-12), ("c64", 1e-4)):
+        a, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec, engine="simt")
+        b, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec, engine="blocked")
+        for ga, gb in zip(a, b):
+            for i in range(3):
+                if prec == "c128":
+                    assert ga["info"][i]["branch"] == gb["info"][i]["branch"]
+                    assert ga["info"][i]["r"] == gb["info"][i]["r"]
+                assert relerr(gb["X"][i], ga["X"][i]) < tol
+                assert relerr(gb["W"][i], ga["W"][i]) < tol
+
+
+@pytest.mark.parametrize("K,N,prec", [(100, 300, "c128"), (128, 512, "c64"), (65, 97, "c64"),
+                                      (64, 96, "c128")])
+def test_blocked_beyond_one_cta(K, N, prec):
+    """K above the one-CTA limit (and K = 64 in complex128, whose one-CTA footprint exceeds
+    shared memory): the automatic choice is the blocked engine; ragged last pivot block
+    (K not a multiple of 32) and ragged N."""
+    sc = channel.LeoScenario(n_x=N, n_y=1, K=K, disc_radius=100e3)
+    Hs = _traj(sc, 2, 6, seed=500 + K)
+    rule = binding.RankRule(eta=0.9, k_init=2, p=4, r_max=32, reinverse_period=4, seed=2)
+    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec)
+    assert meta["engine"] == "blocked"
+    _check(gpu, Hs, sc, rule, prec, engine="blocked")
+
+
+def test_blocked_full_inversion_method():
+    sc = channel.LeoScenario(n_x=50, n_y=4, K=96, disc_radius=100e3)
+    Hs = _traj(sc, 2, 3, seed=9)
+    rule = binding.RankRule()
+    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64", method="full",
+                        keep_state=False, engine="blocked")
+    assert all(g["info"][b]["branch"] == 5 for g in gpu for b in range(2))
+    _check(gpu, Hs, sc, rule, "c64", method="full", engine="blocked")
+
+
+def test_blocked_batch_invariance_with_instance_ids():
+    sc = channel.scenario_batched_256x32()
+    Hs = _traj(sc, 4, 5, seed=12).to(torch.complex64)
+    rule = binding.RankRule(eta=0.8, k_init=2, p=8, r_max=16, seed=9)
+    ids = [70, 71, 72, 73]
+    batch, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, ids=ids, engine="blocked")
+    alone, _ = run_gpu(Hs[:, 2:3].contiguous(), sc.alpha, sc.sigma2, sc.p_t, rule, ids=[72],
+                       engine="blocked")
+    for t in range(5):
+        np.testing.assert_array_equal(batch[t]["W"][2], alone[t]["W"][0])
+        np.testing.assert_array_equal(batch[t]["X"][2], alone[t]["X"][0])
+
+
+def test_blocked_not_positive_definite_is_reported():
+    K, N = 70, 80
+    H = np.ones((K, N), dtype=np.complex128) * 0.1
+    H[5] = 0.0
+    h = binding.WBRZF(1, N, K, [0.0], [0.1], precision="c128")
+    h.full_inverse(torch.from_numpy(H[None].copy()).cuda())
+    assert h.last_engine == "blocked"
+    assert h.step_info()[0]["status"] & 1
+    h.close()
+
+
+def test_large_array_against_oracle():
+    """64x64 UPA (N = 4096), K = 512, adaptive rank up to 64, complex64: one instance, the
+    initial inverse and three updates against the oracle.  dG's spectrum is nearly flat here
+    (the leading 64 of 512 singular values hold about half its energy) and a sketch of
+    d = 72 columns captures about a third of it, so eta = 0.25 is met at a rank in the 40s
+    and the updates take the Woodbury branch, while at eta = 0.9 Algorithm 1 ends unmet at
+    r = d = 72 > r_max and every update is a direct inverse (branch RANK), as in the oracle."""
+    sc = channel.scenario_large_4096x512()
+    Hs = _traj(sc, 1, 4, seed=7)
+    H64 = Hs[:, 0].numpy().astype(np.complex64).astype(np.complex128)
+    for eta, branch in ((0.25, 1), (0.9, 4)):
+        rule = binding.RankRule(eta=eta, k_init=2, p=8, r_max=64, reinverse_period=20, seed=5)
+        gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64")
+        assert meta["engine"] == "blocked"
+        ref = run_oracle(H64, sc.alpha, sc.sigma2, sc.p_t, rule)
+        for t in range(4):
+            inf = gpu[t]["info"][0]
+            assert inf["status"] == 0
+            assert inf["branch"] == ref[t].branch == (2 if t == 0 else branch)
+            if branch == 1 and t > 0:
+                assert abs(inf["r"] - ref[t].r) <= 4, (inf["r"], ref[t].r)
+            assert relerr(gpu[t]["X"][0], ref[t].X) < 1e-4
+            assert relerr(gpu[t]["W"][0], ref[t].W) < 1e-4
+            assert abs(gpu[t]["rate"][0] - ref[t].sum_rate) < 1e-5 * abs(ref[t].sum_rate)
+        if branch == 4:                           # direct inverse: X G = I to FP32 level
+            G = rzf.gram(H64[3], sc.alpha)
+            assert np.max(np.abs(gpu[3]["X"][0] @ G - np.eye(sc.K))) < 1e-4

@@ -138,19 +138,21 @@ def test_engines_agree():
 
 @pytest.mark.parametrize("K,N", [(1, 5), (3, 1), (5, 37), (17, 100), (32, 33), (64, 96),
                                  (8, 1000), (2, 2), (31, 290), (32, 160)])
-@pytest.mark.parametrize("prec,engine", [("c128", "simt"), ("c64", "simt"), ("c64", "tensor")])
+@pytest.mark.parametrize("prec,engine", [("c128", "simt"), ("c64", "simt"), ("c64", "tensor"),
+                                         ("c128", "blocked"), ("c64", "blocked")])
 def test_edge_shapes(K, N, prec, engine):
     """Ragged N (not a multiple of the 32-column staging chunk or of the 128-antenna tile),
-    K > N, K = 1, K = 64; the tensor engine needs K <= 32 and even N and must refuse others."""
+    K > N, K = 1, K = 64; the tensor engine needs K <= 32 and even N and must refuse others;
+    the blocked engine takes every shape."""
     sc = channel.LeoScenario(n_x=N, n_y=1, K=K, disc_radius=50e3)
     Hs = _traj(sc, 2, 6, seed=400 + K + N)
     rule = binding.RankRule(eta=0.9, k_init=2, p=2, r_max=min(K, 16), reinverse_period=4,
                             seed=1)
-    if K == 64 and prec == "c128":
+    if K == 64 and prec == "c128" and engine == "simt":
         # three resident 64 x 64 complex128 matrices plus workspaces exceed one CTA's
-        # shared memory: the library must refuse the shape instead of running it
+        # shared memory: the one-CTA kernel must refuse the shape instead of running it
         with pytest.raises(binding.WbrzfError) as e:
-            run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec)
+            run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec, engine=engine)
         assert e.value.code == 6
         return
     if engine == "tensor" and (K > 32 or N % 2):
