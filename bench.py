@@ -8,6 +8,10 @@ snapshot covers all 1024 instances.  Inputs are synthetic (seeded) and resident 
 the timed region; L2 is flushed between timed snapshots (outside the per-snapshot events).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batched_256x32|large_4096x512]
+
+The second workload (one 64x64-UPA array, N = 4096, K = 512) runs on the blocked engine and
+reports the library's per-stage event times beside the step time.
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own 1024 trajectories
 (weak scaling, no collective on the data path); the time is the max over ranks.
@@ -30,9 +34,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "precoder updates/s, WB-arSVD vs full-inverse RZF at fixed rate gap; p99 ms"
-WORKLOAD = ("batched_256x32: 1024 trajectories x (16x16 UPA, N=256, K=32), complex64/FP32, "
-            "p=8, k_init=2, r_max=16, re-inverse every 20 snapshots, 10 ms snapshots")
-BATCH, NX, K_USERS = 1024, 16, 32
+WORKLOADS = {
+    # the default line: 1024 independent trajectories, one launch per snapshot
+    "batched_256x32": {
+        "desc": ("batched_256x32: 1024 trajectories x (16x16 UPA, N=256, K=32), complex64/FP32, "
+                 "p=8, k_init=2, r_max=16, re-inverse every 20 snapshots, 10 ms snapshots"),
+        "scenario": "scenario_batched_256x32", "batch": 1024, "r_max": 16,
+        "cpu_sample": (32, 40)},
+    # one large array on the blocked engine (K > 64)
+    "large_4096x512": {
+        "desc": ("large_4096x512: 1 array x (64x64 UPA, N=4096, K=512, 300 km disc), "
+                 "complex64/FP32, p=8, k_init=2, r_max=64, re-inverse every 20 snapshots, "
+                 "10 ms snapshots, blocked engine"),
+        "scenario": "scenario_large_4096x512", "batch": 1, "r_max": 64,
+        "cpu_sample": (1, 4)},
+}
 ETA_GRID = (0.65, 0.8, 0.9, 0.95, 0.99)
 RATE_GAP_BOUND = 0.05        # bit/s/Hz, mean |R_WB - R_full|
 
@@ -59,6 +75,31 @@ def algorithmic_bytes_per_update(N: int, K: int, method: str) -> int:
     if method == "wb":
         b += 8 * 4 * K * K
     return b
+
+
+# FP32 FMA peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz (maximum
+# SM clock); the blocked engine's products run on these lanes.
+FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def blocked_roofline(stage_ms: dict, B: int, N: int, K: int) -> dict:
+    """Roofline of the blocked engine's dominant stage.  Algorithmic flops per instance:
+    Gram matrix (Hermitian half) 4 K^2 N; precoder W = H^H X 8 N K^2 plus M = (G - alpha I) X
+    8 K^3."""
+    flops = {"gram": 4.0 * K * K * N, "precoder": 8.0 * N * K * K + 8.0 * K ** 3}
+    stage = max((k for k in stage_ms if k != "total"), key=lambda k: stage_ms[k])
+    out = {"bound": "alu", "unit": "TFLOP/s", "peak": FP32_FMA_TFLOPS,
+           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+           "kernel": f"blocked engine stage '{stage}'", "traffic": None,
+           "stage_share": stage_ms[stage] / stage_ms["total"]}
+    if stage in flops:
+        out["achieved"] = B * flops[stage] / (stage_ms[stage] / 1e3) / 1e12
+        out["frac"] = out["achieved"] / out["peak"]
+        out["algorithmic_flops_per_launch"] = B * flops[stage]
+    else:
+        out["achieved"] = None
+        out["frac"] = None
+    return out
 
 
 def measured_peaks() -> dict:
@@ -177,7 +218,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--eta", type=float, default=None, help="energy fraction (default: grid)")
-    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--batch", type=int, default=None,
+                    help="instances (default: the workload's)")
+    ap.add_argument("--workload", default="batched_256x32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=2512)
@@ -208,20 +251,23 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2512_16543_gb300 import channel
-    sc = channel.scenario_batched_256x32()
-    params = channel.draw_trajectories(sc, args.batch, seed=args.seed)
-    rule_kw = dict(eta=args.eta or 0.65, k_init=2, p=8, r_max=16, reinverse_period=20,
+    wl = WORKLOADS[args.workload]
+    sc = getattr(channel, wl["scenario"])()
+    B = args.batch or wl["batch"]
+    params = channel.draw_trajectories(sc, B, seed=args.seed)
+    rule_kw = dict(eta=args.eta or 0.65, k_init=2, p=8, r_max=wl["r_max"], reinverse_period=20,
                    seed=77)
-    n_inst = 32
-    res = cpu_oracle_baseline(params, sc, rule_kw, n_inst, args.warmup + args.steps)
+    n_inst = min(wl["cpu_sample"][0], B)
+    n_steps = args.warmup + args.steps if B > 1 else wl["cpu_sample"][1]
+    res = cpu_oracle_baseline(params, sc, rule_kw, n_inst, n_steps)
     value = res["value"]
-    sample = (f"{n_inst} of {args.batch} trajectories x {args.warmup + args.steps} snapshots, "
+    sample = (f"{n_inst} of {B} trajectories x {n_steps} snapshots, "
               f"WB-arSVD eta={rule_kw['eta']}, FP64 numpy oracle, spawn pool")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * args.batch / value, "higher_is_better": True,
+            "ms_per_step": 1e3 * B / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "eta": rule_kw["eta"]},
+            "config": {"workload": wl["desc"], "eta": rule_kw["eta"]},
             "cpu_baseline": {"value": value, "unit": "updates/s", "cores": res["cores"],
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
@@ -242,8 +288,10 @@ def main():
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    sc = channel.scenario_batched_256x32()
-    B = args.batch
+    wl = WORKLOADS[args.workload]
+    sc = getattr(channel, wl["scenario"])()
+    B = args.batch or wl["batch"]
+    r_max = wl["r_max"]
     W_, K_ = args.warmup, args.steps
     assert W_ >= 3, "at least 3 warm-up steps"
     params = channel.draw_trajectories(sc, B, seed=args.seed + 7919 * rank)
@@ -256,19 +304,23 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def make(method, eta):
-        rule = binding.RankRule(eta=eta, k_init=2, p=8, r_max=16, reinverse_period=20,
+        rule = binding.RankRule(eta=eta, k_init=2, p=8, r_max=r_max, reinverse_period=20,
                                 seed=77)
         h = binding.WBRZF(B, sc.N, sc.K, sc.alpha, sc.sigma2, p_t=sc.p_t, rule=rule,
                           method=method, device=dev)
         h.set_instance_ids(ids)
         return h
 
-    def timed_run(h, collect_rates=False):
+    def timed_run(h, collect_rates=False, stages=None):
+        """Time K_ snapshots; `stages` (a dict) collects the library's per-stage event times
+        of every timed snapshot when given."""
         Wout = torch.empty(B, sc.N, sc.K, dtype=torch.complex64, device=dev)
         h.full_inverse(Hs[0], Wout)
         for t in range(1, 1 + W_):
             h.update(Hs[t], Wout)
         torch.cuda.synchronize()
+        if stages is not None:
+            h.set_stage_timing(True)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(K_)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(K_)]
         rates = []
@@ -283,6 +335,10 @@ def main():
             ends[i].record(stream)
             if collect_rates:
                 rates.append(h.sum_rate()[1].clone())
+            if stages is not None:
+                for k, v in h.stage_times().items():
+                    if v is not None:
+                        stages.setdefault(k, []).append(v)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -290,8 +346,10 @@ def main():
         return ms, h.launches - launches0, rates
 
     # ---- method gap on the eta grid (rates of both methods on the same snapshots)
+    blocked = sc.K > 64                   # the blocked engine: per-stage events from the library
+    stages_full = {} if blocked else None
     full = make("full", 0.9)
-    ms_full, _, rates_full = timed_run(full, collect_rates=True)
+    ms_full, _, rates_full = timed_run(full, collect_rates=True, stages=stages_full)
     full.close()
     grid = [args.eta] if args.eta else list(ETA_GRID)
     chosen, gaps, wb_runs = None, {}, {}
@@ -300,12 +358,13 @@ def main():
         h = make("wb", eta)
         if chosen is None and eta == grid[0]:
             clock.start()
-        ms, launches, rates = timed_run(h, collect_rates=True)
+        stg = {} if blocked else None
+        ms, launches, rates = timed_run(h, collect_rates=True, stages=stg)
         info = h.step_info()
         h.close()
         gap = float(torch.stack([(a - b).abs() for a, b in zip(rates, rates_full)]).mean())
         gaps[eta] = gap
-        wb_runs[eta] = (ms, launches, info)
+        wb_runs[eta] = (ms, launches, info, stg)
         if chosen is None:
             clk = clock.stop()
             if gap <= RATE_GAP_BOUND:
@@ -313,7 +372,7 @@ def main():
                 break
     if chosen is None:
         chosen = grid[-1]
-    ms_wb, launches, info = wb_runs[chosen]
+    ms_wb, launches, info, stages_wb = wb_runs[chosen]
 
     tot_wb = barrier_max(sum(ms_wb) / 1e3, world)
     tot_full = barrier_max(sum(ms_full) / 1e3, world)
@@ -322,17 +381,25 @@ def main():
     p50, p99 = float(np.percentile(ms_wb, 50)), float(np.percentile(ms_wb, 99))
     f50, f99 = float(np.percentile(ms_full, 50)), float(np.percentile(ms_full, 99))
 
-    # ---- roofline of the step kernel (one launch per snapshot)
     peaks = measured_peaks()
     abytes = B * algorithmic_bytes_per_update(sc.N, sc.K, "wb")
-    achieved = abytes / (statistics.mean(ms_wb) / 1e3) / 1e9
-    traffic = (NCU_TRAFFIC["bytes_per_launch"]
-               if NCU_TRAFFIC["source_sha"] == kernel_source_sha() else None)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": abytes}
     abytes_full = B * algorithmic_bytes_per_update(sc.N, sc.K, "full")
     ach_full = abytes_full / (statistics.mean(ms_full) / 1e3) / 1e9
+    stage_ms = None
+    if not blocked:
+        # ---- roofline of the step kernel (one launch per snapshot)
+        achieved = abytes / (statistics.mean(ms_wb) / 1e3) / 1e9
+        traffic = (NCU_TRAFFIC["bytes_per_launch"]
+                   if NCU_TRAFFIC["source_sha"] == kernel_source_sha() else None)
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "peak_source": peaks["source"], "kernel": "wbrzf_step_tc_kernel",
+                    "algorithmic_bytes_per_launch": abytes}
+    else:
+        # ---- blocked engine: the stage that takes the most time, against FP32 FMA peak
+        stage_ms = {"wb": {k: statistics.mean(v) for k, v in stages_wb.items()},
+                    "full": {k: statistics.mean(v) for k, v in stages_full.items()}}
+        roofline = blocked_roofline(stage_ms["wb"], B, sc.N, sc.K)
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -370,8 +437,8 @@ def main():
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N = 1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rule_kw = dict(eta=chosen, k_init=2, p=8, r_max=16, reinverse_period=20, seed=77)
-        n_inst, n_steps = 32, 40
+        rule_kw = dict(eta=chosen, k_init=2, p=8, r_max=r_max, reinverse_period=20, seed=77)
+        n_inst, n_steps = wl["cpu_sample"]
         res = cpu_oracle_baseline(params, sc, rule_kw, n_inst, n_steps)
         cpu = {"value": res["value"], "unit": "updates/s", "cores": res["cores"],
                "kind": "oracle",
@@ -388,7 +455,7 @@ def main():
             "steps": K_, "warmup": W_, "ms_per_step": statistics.mean(ms_wb),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": world * B, "eta": chosen,
+            "config": {"workload": wl["desc"], "global_batch": world * B, "eta": chosen,
                        "eta_grid_gaps_bits": gaps, "rate_gap_bound_bits": RATE_GAP_BOUND,
                        "l2": "flushed (512 MB write) between timed snapshots",
                        "parallelism": f"instances sharded over {world} GPU(s)"},
@@ -398,6 +465,7 @@ def main():
             "wb_over_full": value / value_full,
             "last_step_branches": branches,
             "roofline": roofline,
+            "stage_ms": stage_ms,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

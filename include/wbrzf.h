@@ -208,6 +208,18 @@ wbrzf_status wbrzf_set_instance_ids(wbrzf* h, const uint32_t* ids, int count);
 wbrzf_status wbrzf_set_engine(wbrzf* h, int engine);
 int wbrzf_last_engine(const wbrzf* h);
 
+/*
+ * Stage timing (not part of the paper's method; for profiling).  When enabled, each snapshot
+ * records CUDA events on the handle's stream at its stage boundaries.  wbrzf_stage_times
+ * waits for the last snapshot's events and writes six durations in milliseconds to the host
+ * array ms_out: [0] Gram matrix and dG, [1] Algorithm 1, [2] Woodbury update, [3] direct
+ * inverse, [4] SINR, sum-rate and precoder, [5] the whole snapshot.  On the single-CTA
+ * engines every stage runs inside one kernel: [0]-[4] are -1 and only [5] is measured.
+ * wbrzf_stage_times returns WBRZF_ERR_INVALID_ARG when timing is off or nothing has run.
+ */
+wbrzf_status wbrzf_set_stage_timing(wbrzf* h, int enable);
+wbrzf_status wbrzf_stage_times(wbrzf* h, float* ms_out);
+
 /* Rebind the handle to another stream (cudaStream_t; NULL = legacy default stream). */
 wbrzf_status wbrzf_set_stream(wbrzf* h, void* cuda_stream);
 

@@ -102,6 +102,10 @@ def lib() -> ctypes.CDLL:
     L.wbrzf_set_trace.argtypes = [vp, vp, sz]
     L.wbrzf_set_instance_ids.restype = i32
     L.wbrzf_set_instance_ids.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), i32]
+    L.wbrzf_set_stage_timing.restype = i32
+    L.wbrzf_set_stage_timing.argtypes = [vp, i32]
+    L.wbrzf_stage_times.restype = i32
+    L.wbrzf_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     L.wbrzf_set_engine.restype = i32
     L.wbrzf_set_engine.argtypes = [vp, i32]
     L.wbrzf_last_engine.restype = i32
@@ -262,6 +266,18 @@ class WBRZF:
         names = {v: k for k, v in ENGINES.items()}
         names[0] = "none"
         return names[int(lib().wbrzf_last_engine(self._h))]
+
+    STAGES = ("gram", "lowrank", "woodbury", "inverse", "precoder", "total")
+
+    def set_stage_timing(self, enable: bool = True) -> None:
+        _check(lib().wbrzf_set_stage_timing(self._h, int(enable)), "wbrzf_set_stage_timing")
+
+    def stage_times(self) -> dict:
+        """Milliseconds per stage of the last snapshot (waits for it); None where the engine
+        runs the stage inside one kernel."""
+        buf = (ctypes.c_float * 6)()
+        _check(lib().wbrzf_stage_times(self._h, buf), "wbrzf_stage_times")
+        return {k: (None if v < 0 else float(v)) for k, v in zip(self.STAGES, buf)}
 
     def set_stream(self, stream: torch.cuda.Stream) -> None:
         self.stream = stream

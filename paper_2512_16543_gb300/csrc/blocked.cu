@@ -696,7 +696,8 @@ __global__ void __launch_bounds__(256) sinr_kernel(const StepArgs<T> a, const Bu
 
 // ---------------------------------------------------------------- the snapshot sequence
 template <class T>
-cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t s, int* launches) {
+cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t s, int* launches,
+                        cudaEvent_t* ev) {
   const int B = a.batch, K = a.K, N = a.N, dmax = a.dmax, rcap = a.rcap;
   const Bufs<T> w = make_bufs<T>(base, B, K, dmax, rcap);
   const BlockedLayout& L = w.L;
@@ -714,11 +715,17 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
     e = cudaFuncSetAttribute(capinv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
   if (e != cudaSuccess) return e;
   const T one = T(1), zero = T(0);
+  // stage boundaries for the optional timing events (ev[0..5])
+  auto mark = [&](int i) -> cudaError_t {
+    return ev != nullptr ? cudaEventRecord(ev[i], s) : cudaSuccess;
+  };
+  if ((e = mark(0)) != cudaSuccess) return e;
   // Gram H H^H into D, then G_t, dG
   WB_TRY(gemm<T>(s, B, K, K, N, a.H, N, (size_t)K * N, 0, a.H, N, (size_t)K * N, 1, w.D, K, L.sD,
                  one, nullptr, zero, nullptr, 0, 0));
   finish_gram_kernel<T><<<B, 256, 0, s>>>(a, w);
   WB_TRY(cudaGetLastError());
+  if ((e = mark(1)) != cudaSuccess) return e;
   if (a.mode == MODE_UPDATE) {
     long long k0 = a.k_init;
     for (int it = 0; it < a.i_max; ++it) {
@@ -747,6 +754,7 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
       WB_TRY(cudaGetLastError());
       if (k0 < K) k0 *= 2;
     }
+    if ((e = mark(2)) != cudaSuccess) return e;
     const int g = 1 << WBRZF_BRANCH_WOODBURY;
     // L = Q U_r, R^H = nu U_r^H B (nu undoes the scaling of dG), T = X L, Z = R^H X, C = Z L
     WB_TRY(gemm<T>(s, B, K, rcap, dmax, w.Q, dmax, L.sOm, 0, w.Ur, rcap, L.sUr, 0, w.Lm, rcap,
@@ -770,6 +778,8 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
     WB_TRY(gemm<T>(s, B, K, K, rcap, w.Tm, rcap, L.sL, 0, w.CZ, K, L.sRh, 0, a.Xs, K, KK,
                    T(-1), nullptr, one, w.ctl, C_BRANCH, g));
   }
+  if (a.mode != MODE_UPDATE && (e = mark(2)) != cudaSuccess) return e;
+  if ((e = mark(3)) != cudaSuccess) return e;
   // direct inverse by block exchange steps (instances whose branch asks for it)
   copy_gx_kernel<T><<<dim3((unsigned)((KK + 255) / 256), B), 256, 0, s>>>(a, w);
   WB_TRY(cudaGetLastError());
@@ -789,6 +799,7 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
     fixup_kernel<T><<<dim3((K * 32 + 255) / 256, B), 256, 0, s>>>(a, w, p, bs);
     WB_TRY(cudaGetLastError());
   }
+  if ((e = mark(4)) != cudaSuccess) return e;
   // SINR and scale, then W = s H^H X.  M = (G - alpha I) X: the shift is applied to G before
   // the product, since G X - alpha X cancels to about I - I when alpha dominates H H^H.
   WB_TRY(gemm<T>(s, B, K, K, K, a.Gs, K, KK, 0, a.Xs, K, KK, 0, w.D, K, L.sD, one, nullptr,
@@ -798,6 +809,7 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
   WB_TRY(gemm<T>(s, B, N, K, K, a.H, N, (size_t)K * N, 1, a.Xs, K, KK, 0, a.W, K, (size_t)N * K,
                  one, w.ws, zero, nullptr, 0, 0));
 #undef WB_TRY
+  if ((e = mark(5)) != cudaSuccess) return e;
   *launches = nl;
   return cudaSuccess;
 }
@@ -806,11 +818,11 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
 
 namespace wbk {
 cudaError_t run_blocked_f32(const StepArgs<float>& a, unsigned char* base, cudaStream_t s,
-                            int* launches) {
-  return run_blocked<float>(a, base, s, launches);
+                            int* launches, cudaEvent_t* ev) {
+  return run_blocked<float>(a, base, s, launches, ev);
 }
 cudaError_t run_blocked_f64(const StepArgs<double>& a, unsigned char* base, cudaStream_t s,
-                            int* launches) {
-  return run_blocked<double>(a, base, s, launches);
+                            int* launches, cudaEvent_t* ev) {
+  return run_blocked<double>(a, base, s, launches, ev);
 }
 }  // namespace wbk

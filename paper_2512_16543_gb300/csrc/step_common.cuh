@@ -200,11 +200,13 @@ cudaError_t launch_step_f32(const StepArgs<float>& a, size_t smem, cudaStream_t 
 cudaError_t launch_step_f64(const StepArgs<double>& a, size_t smem, cudaStream_t s);
 // Blocked engine (any K): a fixed sequence of batched kernels on `stream`; `base` is the
 // blocked scratch (blocked_layout) of the workspace (blocked.cu).
-// *launches receives the number of kernels enqueued.
+// *launches receives the number of kernels enqueued.  ev: NULL, or six events recorded on the
+// stream at the stage boundaries (start, after the Gram matrix and dG, after Algorithm 1,
+// after the Woodbury update, after the direct inverse, end).
 cudaError_t run_blocked_f32(const StepArgs<float>& a, unsigned char* base, cudaStream_t s,
-                            int* launches);
+                            int* launches, cudaEvent_t* ev);
 cudaError_t run_blocked_f64(const StepArgs<double>& a, unsigned char* base, cudaStream_t s,
-                            int* launches);
+                            int* launches, cudaEvent_t* ev);
 // Tensor-core kernel (complex64, K <= 32, even N); hmap: H as a 2-D FP32 tensor map
 // {2N, batch K}, box {64, K} (step_tc.cu).  `hmap` points to a CUtensorMap.
 cudaError_t launch_step_tc(const StepArgs<float>& a, const void* hmap, size_t smem,

@@ -155,6 +155,8 @@ struct wbrzf {
   size_t ws_bytes;       // workspace size given at creation
   bool simt_ok;          // the single-CTA kernel fits (K <= kMaxK and its shared memory)
   bool blocked_ok;       // the blocked engine's limits hold (workspace checked separately)
+  bool timing;           // stage events recorded (wbrzf_set_stage_timing)
+  cudaEvent_t ev[6];
 };
 
 namespace {
@@ -225,10 +227,11 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
   if (use_blocked(h)) {
     unsigned char* base = h->ws + blocked_offset(h->batch, h->K, h->prec);
     int nl = 0;
+    cudaEvent_t* ev = h->timing ? h->ev : nullptr;
     if (h->prec == WBRZF_C128)
-      e = run_blocked_f64(make_args<double>(h, H, W, mode, h->t), base, h->stream, &nl);
+      e = run_blocked_f64(make_args<double>(h, H, W, mode, h->t), base, h->stream, &nl, ev);
     else
-      e = run_blocked_f32(make_args<float>(h, H, W, mode, h->t), base, h->stream, &nl);
+      e = run_blocked_f32(make_args<float>(h, H, W, mode, h->t), base, h->stream, &nl, ev);
     if (e != cudaSuccess) return cuda_fail(e);
     h->last_engine = WBRZF_ENGINE_BLOCKED;
     h->launches += nl;
@@ -240,6 +243,7 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
   alignas(64) CUtensorMap map;
   if (use_tc && !encode_hmap(h, H, &map)) use_tc = false;
   if (h->engine == WBRZF_ENGINE_TENSOR && !use_tc) return WBRZF_ERR_UNSUPPORTED;
+  if (h->timing && (e = cudaEventRecord(h->ev[0], h->stream)) != cudaSuccess) return cuda_fail(e);
   if (use_tc) {
     e = launch_step_tc(make_args<float>(h, H, W, mode, h->t), &map, h->smem_tc, h->stream);
   } else if (h->prec == WBRZF_C128) {
@@ -248,6 +252,7 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
     e = launch_step_f32(make_args<float>(h, H, W, mode, h->t), h->smem, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(e);
+  if (h->timing && (e = cudaEventRecord(h->ev[5], h->stream)) != cudaSuccess) return cuda_fail(e);
   h->last_engine = use_tc ? WBRZF_ENGINE_TENSOR : WBRZF_ENGINE_SIMT;
   h->launches += 1;
   h->t += 1;
@@ -336,6 +341,7 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   h->ws_bytes = workspace_bytes;
   h->simt_ok = simt_ok;
   h->blocked_ok = blocked_ok;
+  h->timing = false;
   {
     const size_t tc = tc_smem_bytes(K, r.dmax, r.rcap);
     h->smem_tc = (simt_ok && prec == WBRZF_C64 && K <= 32 && tc <= 227 * 1024) ? tc : 0;
@@ -471,7 +477,44 @@ wbrzf_status wbrzf_set_stream(wbrzf* h, void* cuda_stream) {
 
 long long wbrzf_launch_count(const wbrzf* h) { return h ? h->launches : 0; }
 
-void wbrzf_destroy(wbrzf* h) { delete h; }
+wbrzf_status wbrzf_set_stage_timing(wbrzf* h, int enable) {
+  if (!h) return WBRZF_ERR_INVALID_ARG;
+  if (enable && !h->timing) {
+    for (int i = 0; i < 6; ++i) {
+      cudaError_t e = cudaEventCreate(&h->ev[i]);
+      if (e != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(h->ev[j]);
+        return cuda_fail(e);
+      }
+    }
+    h->timing = true;
+  } else if (!enable && h->timing) {
+    for (int i = 0; i < 6; ++i) cudaEventDestroy(h->ev[i]);
+    h->timing = false;
+  }
+  return WBRZF_OK;
+}
+
+wbrzf_status wbrzf_stage_times(wbrzf* h, float* ms_out) {
+  if (!h || !ms_out || !h->timing || h->last_engine == 0) return WBRZF_ERR_INVALID_ARG;
+  cudaError_t e = cudaEventSynchronize(h->ev[5]);
+  if (e != cudaSuccess) return cuda_fail(e);
+  for (int i = 0; i < 5; ++i) ms_out[i] = -1.0f;
+  if (h->last_engine == WBRZF_ENGINE_BLOCKED) {
+    for (int i = 0; i < 5; ++i) {
+      e = cudaEventElapsedTime(&ms_out[i], h->ev[i], h->ev[i + 1]);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+  }
+  e = cudaEventElapsedTime(&ms_out[5], h->ev[0], h->ev[5]);
+  return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
+}
+
+void wbrzf_destroy(wbrzf* h) {
+  if (h && h->timing)
+    for (int i = 0; i < 6; ++i) cudaEventDestroy(h->ev[i]);
+  delete h;
+}
 
 const char* wbrzf_status_string(wbrzf_status s) {
   switch (s) {
