@@ -94,12 +94,17 @@ enum {
   WBRZF_ENGINE_TENSOR = 2,    /* tcgen05 tensor cores for H H^H (FP32-faithful hi/lo TF32
                                  split) and H^H X (TF32 inputs, FP32 accumulation); complex64,
                                  K <= 32, even N, H_t 16-byte aligned                         */
-  WBRZF_ENGINE_BLOCKED = 3    /* any K: each step of the path a batched kernel of its own
-                                 (tiled complex GEMMs, per-instance Cholesky / Jacobi /
-                                 capacitance kernels, block Gauss-Jordan inverse on 32 x 32
-                                 pivot blocks); sketch width dmax up to 110 (complex64) / 78
-                                 (complex128), batch <= 65535; needs the larger workspace of
-                                 wbrzf_workspace_bytes_engine(..., WBRZF_ENGINE_BLOCKED)       */
+  WBRZF_ENGINE_BLOCKED = 3,   /* any K: each step of the path a batched kernel of its own
+                                 (complex GEMMs, per-instance Cholesky / Jacobi / capacitance
+                                 kernels, block Gauss-Jordan inverse on 32 x 32 pivot blocks);
+                                 complex64: H H^H (FP32-faithful hi/lo TF32 split) and H^H X
+                                 (TF32 inputs, FP32 accumulation) on tcgen05 tensor cores, the
+                                 rest FP32 FMA; complex128: FP64 FMA.  Sketch width dmax up to
+                                 110 (complex64) / 78 (complex128), batch <= 65535; needs the
+                                 larger workspace of wbrzf_workspace_bytes_engine(...,
+                                 WBRZF_ENGINE_BLOCKED)                                         */
+  WBRZF_ENGINE_BLOCKED_FMA = 4 /* the blocked engine with every product on FP32 / FP64 fused
+                                 multiply-adds (same workspace)                                */
 };
 
 /* Rank rule and method parameters (Algorithm 1 inputs, Algorithm 2 switch). */
@@ -202,9 +207,11 @@ wbrzf_status wbrzf_set_instance_ids(wbrzf* h, const uint32_t* ids, int count);
 
 /* Choose the kernel (WBRZF_ENGINE_*).  An engine whose conditions the handle does not meet
  * returns WBRZF_ERR_UNSUPPORTED; WBRZF_ENGINE_BLOCKED on a handle created with less workspace
- * than wbrzf_workspace_bytes_engine(..., WBRZF_ENGINE_BLOCKED) returns WBRZF_ERR_WORKSPACE.
+ * than wbrzf_workspace_bytes_engine(..., WBRZF_ENGINE_BLOCKED) (either blocked variant)
+ * returns WBRZF_ERR_WORKSPACE.
  * The resident state carries over between engines.  wbrzf_last_engine reports the engine
- * the last snapshot ran on (WBRZF_ENGINE_SIMT, _TENSOR or _BLOCKED; 0 before any). */
+ * the last snapshot ran on (WBRZF_ENGINE_SIMT, _TENSOR, _BLOCKED or _BLOCKED_FMA; 0 before
+ * any). */
 wbrzf_status wbrzf_set_engine(wbrzf* h, int engine);
 int wbrzf_last_engine(const wbrzf* h);
 

@@ -18,7 +18,7 @@ _lib = None
 # enums of wbrzf.h
 C128, C64 = 0, 1
 WB_ARSVD, FULL_INVERSE = 0, 1
-ENGINES = {"auto": 0, "simt": 1, "tensor": 2, "blocked": 3}
+ENGINES = {"auto": 0, "simt": 1, "tensor": 2, "blocked": 3, "blocked_fma": 4}
 BRANCH_NAMES = {0: "keep", 1: "woodbury", 2: "init", 3: "periodic", 4: "rank", 5: "full",
                 6: "fallback"}
 STATUS = {0: "ok", 1: "invalid argument", 2: "not initialized", 3: "workspace too small",
@@ -258,7 +258,8 @@ class WBRZF:
 
     def set_engine(self, engine: str) -> None:
         """"auto", "simt" (fused multiply-adds, one CTA per instance), "tensor" (tcgen05
-        tensor cores) or "blocked" (one batched kernel per step, any K)."""
+        tensor cores), "blocked" (one batched kernel per step, any K; complex64 products on
+        tensor cores) or "blocked_fma" (the blocked engine on fused multiply-adds only)."""
         _check(lib().wbrzf_set_engine(self._h, ENGINES[engine]), "wbrzf_set_engine")
 
     @property

@@ -18,6 +18,9 @@
 // once, so one snapshot is always the same launch sequence.
 #include "step_kernel.cuh"
 
+static_assert(sizeof(wbrzf_step_info) == 32 && offsetof(wbrzf_step_info, status) == 28,
+              "the tensor-core precoder ORs timeouts into wbrzf_step_info.status as int 7 of 8");
+
 namespace wbk {
 namespace {
 
@@ -39,9 +42,9 @@ struct Bufs {
 };
 
 template <class T>
-Bufs<T> make_bufs(unsigned char* base, int batch, int K, int dmax, int rcap) {
+Bufs<T> make_bufs(unsigned char* base, int batch, int N, int K, int dmax, int rcap) {
   Bufs<T> b;
-  b.L = blocked_layout(batch, K, dmax, rcap, sizeof(cx<T>), sizeof(T));
+  b.L = blocked_layout(batch, N, K, dmax, rcap, sizeof(cx<T>), sizeof(T));
   auto C = [&](size_t o) { return reinterpret_cast<cx<T>*>(base + o); };
   b.D = C(b.L.oD); b.Om = C(b.L.oOm); b.Q = C(b.L.oQ); b.Gy = C(b.L.oGy); b.Bm = C(b.L.oBm);
   b.E = C(b.L.oE); b.Uh = C(b.L.oUh); b.Ur = C(b.L.oUr); b.Lm = C(b.L.oL); b.Tm = C(b.L.oT);
@@ -217,8 +220,7 @@ __global__ void __launch_bounds__(256) finish_gram_kernel(const StepArgs<T> a, c
     ctl[C_D] = 0;
     ctl[C_ITERS] = 0;
     ctl[C_K0] = a.k_init;
-    ctl[C_STATUS] = 0;
-    ctl[C_EXP] = e;
+    ctl[C_EXP] = e;          // C_STATUS: cleared before the Gram product, may hold a timeout
     w.et[b] = a.eta * ldexp(dg2, -2 * e);
     w.nrm[2 * b] = dg2;
     w.nrm[2 * b + 1] = g2;
@@ -699,7 +701,7 @@ template <class T>
 cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t s, int* launches,
                         cudaEvent_t* ev) {
   const int B = a.batch, K = a.K, N = a.N, dmax = a.dmax, rcap = a.rcap;
-  const Bufs<T> w = make_bufs<T>(base, B, K, dmax, rcap);
+  const Bufs<T> w = make_bufs<T>(base, B, N, K, dmax, rcap);
   const BlockedLayout& L = w.L;
   const size_t KK = (size_t)K * K;
   cudaError_t e;
@@ -721,8 +723,17 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
   };
   if ((e = mark(0)) != cudaSuccess) return e;
   // Gram H H^H into D, then G_t, dG
-  WB_TRY(gemm<T>(s, B, K, K, N, a.H, N, (size_t)K * N, 0, a.H, N, (size_t)K * N, 1, w.D, K, L.sD,
-                 one, nullptr, zero, nullptr, 0, 0));
+  if ((e = cudaMemsetAsync(w.ctl, 0, (size_t)B * 8 * sizeof(int), s)) != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4) {
+    if (a.tc_products) {
+      e = tc_gram_f32(a.H, reinterpret_cast<float*>(base + L.oP), w.D, L.sD, B, N, K, L.Np,
+                      w.ctl + C_STATUS, 8, s, &nl);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (!(sizeof(T) == 4 && a.tc_products))
+    WB_TRY(gemm<T>(s, B, K, K, N, a.H, N, (size_t)K * N, 0, a.H, N, (size_t)K * N, 1, w.D, K,
+                   L.sD, one, nullptr, zero, nullptr, 0, 0));
   finish_gram_kernel<T><<<B, 256, 0, s>>>(a, w);
   WB_TRY(cudaGetLastError());
   if ((e = mark(1)) != cudaSuccess) return e;
@@ -806,8 +817,17 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
                  zero, nullptr, 0, 0, a.alpha));
   sinr_kernel<T><<<B, 256, 0, s>>>(a, w);
   WB_TRY(cudaGetLastError());
-  WB_TRY(gemm<T>(s, B, N, K, K, a.H, N, (size_t)K * N, 1, a.Xs, K, KK, 0, a.W, K, (size_t)N * K,
-                 one, w.ws, zero, nullptr, 0, 0));
+  if constexpr (sizeof(T) == 4) {
+    if (a.tc_products) {
+      e = tc_wprod_f32(a.H, reinterpret_cast<float*>(base + L.oP), a.Xs, w.ws,
+                       reinterpret_cast<float*>(base + L.oXB), a.W, B, N, K, L.Kp,
+                       reinterpret_cast<int*>(a.info) + 7, 8, s, &nl);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (!(sizeof(T) == 4 && a.tc_products))
+    WB_TRY(gemm<T>(s, B, N, K, K, a.H, N, (size_t)K * N, 1, a.Xs, K, KK, 0, a.W, K,
+                   (size_t)N * K, one, w.ws, zero, nullptr, 0, 0));
 #undef WB_TRY
   if ((e = mark(5)) != cudaSuccess) return e;
   *launches = nl;

@@ -45,6 +45,7 @@ struct StepArgs {
   double dg_floor_rel;
   int dmax, rcap;          // largest sketch width, largest Woodbury rank
   size_t trace_stride;     // bytes per instance trace record
+  int tc_products;         // blocked engine, complex64: Gram and precoder on tensor cores
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -135,11 +136,17 @@ struct BlockedLayout {
   size_t sD, sOm, sGy, sBm, sUr, sL, sRh, sCm, sPC, sPR, sPb;
   // real / double / int arrays
   size_t oLam, oRinv, oWs, oNu, oEt, oNrm, oCtl, oPerm, oDrop;
+  // complex64 only, operands of the tensor-core products (floats):
+  //   P  [batch][4][K][Np]   Re_hi, Im_hi, Re_lo, Im_lo planes of H (TF32), Np = N rounded to 4
+  //   T  [batch][N][2 Kp]    TF32 H^T with interleaved users, Kp = K rounded to 2 (aliases P)
+  //   XB [batch][2 K][2 Kp]  TF32 s [[Re X, Im X], [Im X, -Re X]] with interleaved columns
+  size_t oP, oXB, sP, sT, sXB;
+  int Np, Kp;
   size_t bytes;
 };
 
-__host__ __device__ inline BlockedLayout blocked_layout(int batch, int K, int dmax, int rcap,
-                                                       size_t cxb, size_t tb) {
+__host__ __device__ inline BlockedLayout blocked_layout(int batch, int N, int K, int dmax,
+                                                       int rcap, size_t cxb, size_t tb) {
   BlockedLayout L;
   const size_t B = (size_t)batch;
   size_t o = 0;
@@ -170,6 +177,17 @@ __host__ __device__ inline BlockedLayout blocked_layout(int batch, int K, int dm
   L.oCtl = take(8, 4);
   L.oPerm = take((size_t)dmax, 4);
   L.oDrop = take((size_t)dmax, 4);
+  L.Np = (N + 3) / 4 * 4;
+  L.Kp = (K + 1) / 2 * 2;
+  L.sP = 4 * (size_t)K * L.Np;
+  L.sT = (size_t)N * 2 * L.Kp;
+  L.sXB = 2 * (size_t)K * 2 * L.Kp;
+  if (cxb == 8) {
+    L.oP = take(L.sP, 4);
+    L.oXB = take(L.sXB, 4);
+  } else {
+    L.oP = L.oXB = 0;
+  }
   L.bytes = o;
   return L;
 }
@@ -207,6 +225,16 @@ cudaError_t run_blocked_f32(const StepArgs<float>& a, unsigned char* base, cudaS
                             int* launches, cudaEvent_t* ev);
 cudaError_t run_blocked_f64(const StepArgs<double>& a, unsigned char* base, cudaStream_t s,
                             int* launches, cudaEvent_t* ev);
+// Tensor-core products of the blocked engine (complex64, tc_gemm.cu): the Gram matrix into
+// D (upper triangle, instance stride sD) and W = s H^H X; P, T, XB are the operand buffers of
+// the blocked layout; a timeout ORs WBRZF_STATUS_TIMEOUT into stat[stat_stride * b];
+// *launches grows by the kernels enqueued.
+cudaError_t tc_gram_f32(const cx<float>* H, float* P, cx<float>* D, size_t sD, int batch, int N,
+                        int K, int Np, int* stat, int stat_stride, cudaStream_t s,
+                        int* launches);
+cudaError_t tc_wprod_f32(const cx<float>* H, float* T, const cx<float>* X, const float* ws,
+                         float* XB, cx<float>* W, int batch, int N, int K, int Kp, int* stat,
+                         int stat_stride, cudaStream_t s, int* launches);
 // Tensor-core kernel (complex64, K <= 32, even N); hmap: H as a 2-D FP32 tensor map
 // {2N, batch K}, box {64, K} (step_tc.cu).  `hmap` points to a CUtensorMap.
 cudaError_t launch_step_tc(const StepArgs<float>& a, const void* hmap, size_t smem,

@@ -111,10 +111,11 @@ size_t blocked_offset(int batch, int K, wbrzf_precision prec) {
   return align_up(ws_layout(batch, K, prec).bytes, 256);
 }
 
-size_t engine_bytes(int batch, int K, wbrzf_precision prec, const Resolved& r, bool blocked) {
+size_t engine_bytes(int batch, int N, int K, wbrzf_precision prec, const Resolved& r,
+                    bool blocked) {
   if (!blocked) return ws_layout(batch, K, prec).bytes;
   return blocked_offset(batch, K, prec) +
-         blocked_layout(batch, K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec)).bytes;
+         blocked_layout(batch, N, K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec)).bytes;
 }
 
 }  // namespace
@@ -193,6 +194,7 @@ StepArgs<T> make_args(const wbrzf* h, const void* H, void* W, int mode, int t) {
   a.dmax = h->rule.dmax;
   a.rcap = h->rule.rcap;
   a.trace_stride = h->trace_stride;
+  a.tc_products = (h->prec == WBRZF_C64 && h->engine != WBRZF_ENGINE_BLOCKED_FMA) ? 1 : 0;
   return a;
 }
 
@@ -216,7 +218,8 @@ bool encode_hmap(const wbrzf* h, const void* H, CUtensorMap* map) {
 }
 
 bool use_blocked(const wbrzf* h) {
-  return h->engine == WBRZF_ENGINE_BLOCKED || (h->engine == WBRZF_ENGINE_AUTO && !h->simt_ok);
+  return h->engine == WBRZF_ENGINE_BLOCKED || h->engine == WBRZF_ENGINE_BLOCKED_FMA ||
+         (h->engine == WBRZF_ENGINE_AUTO && !h->simt_ok);
 }
 
 wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
@@ -233,7 +236,8 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
     else
       e = run_blocked_f32(make_args<float>(h, H, W, mode, h->t), base, h->stream, &nl, ev);
     if (e != cudaSuccess) return cuda_fail(e);
-    h->last_engine = WBRZF_ENGINE_BLOCKED;
+    h->last_engine =
+        h->engine == WBRZF_ENGINE_BLOCKED_FMA ? WBRZF_ENGINE_BLOCKED_FMA : WBRZF_ENGINE_BLOCKED;
     h->launches += nl;
     h->t += 1;
     return WBRZF_OK;
@@ -268,22 +272,22 @@ size_t wbrzf_workspace_bytes_engine(int batch, int N, int K, wbrzf_precision pre
   Resolved r;
   if (batch < 1 || batch > (1 << 28) || N < 1 || K < 1) return 0;
   if (prec != WBRZF_C128 && prec != WBRZF_C64) return 0;
-  if (engine < WBRZF_ENGINE_AUTO || engine > WBRZF_ENGINE_BLOCKED) return 0;
+  if (engine < WBRZF_ENGINE_AUTO || engine > WBRZF_ENGINE_BLOCKED_FMA) return 0;
   if (!resolve_rule(rule, K, &r)) return 0;
   const bool simt = simt_fits(K, r, prec), blocked = blocked_fits(batch, r, prec);
   switch (engine) {
     case WBRZF_ENGINE_AUTO:
-      if (simt) return engine_bytes(batch, K, prec, r, false);
-      return blocked ? engine_bytes(batch, K, prec, r, true) : 0;
+      if (simt) return engine_bytes(batch, N, K, prec, r, false);
+      return blocked ? engine_bytes(batch, N, K, prec, r, true) : 0;
     case WBRZF_ENGINE_SIMT:
-      return simt ? engine_bytes(batch, K, prec, r, false) : 0;
+      return simt ? engine_bytes(batch, N, K, prec, r, false) : 0;
     case WBRZF_ENGINE_TENSOR:
       return (simt && prec == WBRZF_C64 && K <= 32 && (N % 2) == 0 &&
               tc_smem_bytes(K, r.dmax, r.rcap) <= 227 * 1024)
-                 ? engine_bytes(batch, K, prec, r, false)
+                 ? engine_bytes(batch, N, K, prec, r, false)
                  : 0;
-    default:
-      return blocked ? engine_bytes(batch, K, prec, r, true) : 0;
+    default:   // both blocked variants
+      return blocked ? engine_bytes(batch, N, K, prec, r, true) : 0;
   }
 }
 
@@ -314,7 +318,7 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   const WsLayout wl = ws_layout(batch, K, prec);
   const bool simt_ok = simt_fits(K, r, prec), blocked_ok = blocked_fits(batch, r, prec);
   if (!simt_ok && !blocked_ok) return WBRZF_ERR_UNSUPPORTED;
-  if (workspace_bytes < engine_bytes(batch, K, prec, r, !simt_ok)) return WBRZF_ERR_WORKSPACE;
+  if (workspace_bytes < engine_bytes(batch, N, K, prec, r, !simt_ok)) return WBRZF_ERR_WORKSPACE;
   const size_t smem =
       simt_ok ? simt_smem_bytes(K, r.dmax, r.rcap, cx_bytes(prec), re_bytes(prec)) : 0;
 
@@ -454,13 +458,13 @@ wbrzf_status wbrzf_set_instance_ids(wbrzf* h, const uint32_t* ids, int count) {
 }
 
 wbrzf_status wbrzf_set_engine(wbrzf* h, int engine) {
-  if (!h || engine < WBRZF_ENGINE_AUTO || engine > WBRZF_ENGINE_BLOCKED)
+  if (!h || engine < WBRZF_ENGINE_AUTO || engine > WBRZF_ENGINE_BLOCKED_FMA)
     return WBRZF_ERR_INVALID_ARG;
   if (engine == WBRZF_ENGINE_TENSOR && !tc_eligible(h)) return WBRZF_ERR_UNSUPPORTED;
   if (engine == WBRZF_ENGINE_SIMT && !h->simt_ok) return WBRZF_ERR_UNSUPPORTED;
-  if (engine == WBRZF_ENGINE_BLOCKED) {
+  if (engine == WBRZF_ENGINE_BLOCKED || engine == WBRZF_ENGINE_BLOCKED_FMA) {
     if (!h->blocked_ok) return WBRZF_ERR_UNSUPPORTED;
-    if (h->ws_bytes < engine_bytes(h->batch, h->K, h->prec, h->rule, true))
+    if (h->ws_bytes < engine_bytes(h->batch, h->N, h->K, h->prec, h->rule, true))
       return WBRZF_ERR_WORKSPACE;
   }
   h->engine = engine;

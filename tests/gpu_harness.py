@@ -30,7 +30,7 @@ def run_gpu(Hs: torch.Tensor, alpha, sigma2, p_t, rule: binding.RankRule, *, pre
     dt = torch.complex64 if precision == "c64" else torch.complex128
     h = binding.WBRZF(B, N, K, alpha, sigma2, p_t=p_t, rule=rule, method=method,
                       precision=precision, device=device,
-                      workspace_for="blocked" if engine == "blocked" else "auto")
+                      workspace_for="blocked" if engine.startswith("blocked") else "auto")
     if engine != "auto":
         h.set_engine(engine)
     if ids is not None:

@@ -54,7 +54,9 @@ def test_host_side_validation_without_gpu(libpath):
         eng(1, 4096, 512, binding.C64, ctypes.byref(r64), blocked) > 0
     assert eng(4, 64, 8, binding.C64, ctypes.byref(rule), blocked) > \
         L.wbrzf_workspace_bytes(4, 64, 8, binding.C64, ctypes.byref(rule))
-    assert eng(4, 64, 8, binding.C64, ctypes.byref(rule), 4) == 0           # no such engine
+    assert eng(4, 64, 8, binding.C64, ctypes.byref(rule), binding.ENGINES["blocked_fma"]) == \
+        eng(4, 64, 8, binding.C64, ctypes.byref(rule), blocked)
+    assert eng(4, 64, 8, binding.C64, ctypes.byref(rule), 5) == 0           # no such engine
     assert eng(4, 63, 8, binding.C64, ctypes.byref(rule), binding.ENGINES["tensor"]) == 0
     bad = binding.RankRule(eta=1.5).to_c()
     assert L.wbrzf_workspace_bytes(4, 64, 8, binding.C64, ctypes.byref(bad)) == 0

@@ -1,14 +1,16 @@
 """Parity of the blocked engine (each step of the path a batched kernel of its own, any K) with
 the FP64 oracle, through the C ABI.
 
-Tolerances are those of the FMA engine (the arithmetic is the same, only the blocking and
+Tolerances are those of the one-CTA engines (the arithmetic is the same, only the blocking and
 the order of the sums differ): complex128 X and W within 1e-10, sum-rate within 1e-9; complex64
-X and W within 1e-4, sum-rate within 1e-3 bit/s/Hz (K <= 128).  For the large array
+X within 1e-4 and sum-rate within 1e-3 bit/s/Hz (K <= 128); complex64 W within 1e-4 on
+"blocked_fma" (FP32 FMA) and 2e-3 on "blocked", whose precoder product takes TF32 inputs (unit
+roundoff 2^-11 per operand) while its Gram matrix keeps FP32 accuracy through the hi/lo split.  For the large array
 (N = 4096, K = 512) the FP32 Gram matrix is a sum of 4096 products per entry: its rounding
 error (about sqrt(N) u |G_ij|, 4e-6 per entry) is a sizeable fraction of dG (1.6e-5 of ||G||
 per 10 ms step), so the rank of eq. 14 on that nearly flat spectrum may move by a few
 components; X then moves by at most the dropped components' share of dG, far below the 1e-4
-bound on X and W that still holds.  The sum-rate of 512 users is held to 1e-5 relative.
+bound on X that still holds; the sum-rate keeps the 1e-3 bit/s/Hz bound.
 """
 import numpy as np
 import pytest
@@ -60,15 +62,15 @@ def test_blocked_lowrank_factors_match_oracle(eta):
     assert nwb > 5
 
 
-def test_blocked_complex64_batched():
+@pytest.mark.parametrize("engine", ["blocked", "blocked_fma"])
+def test_blocked_complex64_batched(engine):
     """16x16 UPA, K = 32, p = 8, r <= 16 on the blocked engine against the oracle."""
     sc = channel.scenario_batched_256x32()
     Hs = _traj(sc, 3, 25, seed=303)
     rule = binding.RankRule(eta=0.9, k_init=2, p=8, r_max=16, reinverse_period=20, seed=5)
-    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64",
-                        engine="blocked")
-    assert meta["engine"] == "blocked"
-    assert _check(gpu, Hs, sc, rule, "c64", engine="blocked") <= 3
+    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64", engine=engine)
+    assert meta["engine"] == engine
+    assert _check(gpu, Hs, sc, rule, "c64", engine=engine) <= 3
 
 
 def test_blocked_agrees_with_fma_engine():
@@ -79,7 +81,8 @@ def test_blocked_agrees_with_fma_engine():
     rule = binding.RankRule(eta=0.85, k_init=2, p=3, r_max=8, reinverse_period=5, seed=8)
     for prec, tol in (("c128", 1e-12), ("c64", 1e-4)):
         a, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec, engine="simt")
-        b, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec, engine="blocked")
+        b, _ = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec,
+                       engine="blocked_fma")
         for ga, gb in zip(a, b):
             for i in range(3):
                 if prec == "c128":
@@ -89,18 +92,21 @@ def test_blocked_agrees_with_fma_engine():
                 assert relerr(gb["W"][i], ga["W"][i]) < tol
 
 
-@pytest.mark.parametrize("K,N,prec", [(100, 300, "c128"), (128, 512, "c64"), (65, 97, "c64"),
-                                      (64, 96, "c128")])
-def test_blocked_beyond_one_cta(K, N, prec):
+@pytest.mark.parametrize("K,N,prec,engine", [(100, 300, "c128", "auto"),
+                                             (128, 512, "c64", "auto"),
+                                             (128, 512, "c64", "blocked_fma"),
+                                             (65, 97, "c64", "auto"), (64, 96, "c128", "auto"),
+                                             (200, 250, "c64", "auto")])
+def test_blocked_beyond_one_cta(K, N, prec, engine):
     """K above the one-CTA limit (and K = 64 in complex128, whose one-CTA footprint exceeds
     shared memory): the automatic choice is the blocked engine; ragged last pivot block
     (K not a multiple of 32) and ragged N."""
     sc = channel.LeoScenario(n_x=N, n_y=1, K=K, disc_radius=100e3)
     Hs = _traj(sc, 2, 6, seed=500 + K)
     rule = binding.RankRule(eta=0.9, k_init=2, p=4, r_max=32, reinverse_period=4, seed=2)
-    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec)
-    assert meta["engine"] == "blocked"
-    _check(gpu, Hs, sc, rule, prec, engine="blocked")
+    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision=prec, engine=engine)
+    assert meta["engine"] == ("blocked" if engine == "auto" else engine)
+    _check(gpu, Hs, sc, rule, prec, engine=meta["engine"])
 
 
 def test_blocked_full_inversion_method():
@@ -109,6 +115,7 @@ def test_blocked_full_inversion_method():
     rule = binding.RankRule()
     gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64", method="full",
                         keep_state=False, engine="blocked")
+    assert meta["engine"] == "blocked"
     assert all(g["info"][b]["branch"] == 5 for g in gpu for b in range(2))
     _check(gpu, Hs, sc, rule, "c64", method="full", engine="blocked")
 
@@ -159,8 +166,8 @@ def test_large_array_against_oracle():
             if branch == 1 and t > 0:
                 assert abs(inf["r"] - ref[t].r) <= 4, (inf["r"], ref[t].r)
             assert relerr(gpu[t]["X"][0], ref[t].X) < 1e-4
-            assert relerr(gpu[t]["W"][0], ref[t].W) < 1e-4
-            assert abs(gpu[t]["rate"][0] - ref[t].sum_rate) < 1e-5 * abs(ref[t].sum_rate)
+            assert relerr(gpu[t]["W"][0], ref[t].W) < 2e-3      # TF32 precoder product
+            assert abs(gpu[t]["rate"][0] - ref[t].sum_rate) < 1e-3
         if branch == 4:                           # direct inverse: X G = I to FP32 level
             G = rzf.gram(H64[3], sc.alpha)
             assert np.max(np.abs(gpu[3]["X"][0] @ G - np.eye(sc.K))) < 1e-4
