@@ -2,9 +2,10 @@
 //
 // Used for K above the single-CTA limit (the large array: K = 512, N = 4096) and on request
 // for smaller K.  Each step of the path is its own kernel over all instances:
-//   Gram / dG     batched complex GEMM H H^H (FP32/FP64 FMA), then a per-instance kernel that
-//                 adds alpha I, symmetrises, forms dG = G_t - G_{t-1}, its norm and the scaled
-//                 copy used by the low-rank step (Section II eq. 5, Section III eqs. 7-9)
+//   Gram / dG     batched complex GEMM H H^H (tensor cores for complex64, else FMA), then a
+//                 tiled kernel that adds alpha I, symmetrises and forms dG = G_t - G_{t-1},
+//                 and a decision kernel with the norms, the branch and dG's power-of-two
+//                 scale for the low-rank step (Section II eq. 5, Section III eqs. 7-9)
 //   Algorithm 1   per iteration: Omega (Philox), Y = dG Omega, CholQR2 (Gram GEMM, per-instance
 //                 Cholesky with column drop, row-parallel triangular solve), B = Q^H dG,
 //                 E = B B^H, per-instance Jacobi eigendecomposition, energy rule (eq. 14)
@@ -34,8 +35,8 @@ constexpr int kPending = 15;   // branch code while the low-rank step has not de
 template <class T>
 struct Bufs {
   cx<T>*D, *Om, *Q, *Gy, *Bm, *E, *Uh, *Ur, *Lm, *Tm, *Rh, *Z, *Cm, *CZ, *PC, *PR, *PU, *PV, *Pb;
-  T *lam, *rinv, *ws, *nu;
-  double *et, *nrm;
+  T *lam, *rinv, *ws, *nu, *rows, *dsc;
+  double *et, *nrm, *gpart;
   int *ctl, *perm, *drop;
   BlockedLayout L;
   int dmax, rcap;
@@ -59,6 +60,9 @@ Bufs<T> make_bufs(unsigned char* base, int batch, int N, int K, int dmax, int rc
   b.ctl = reinterpret_cast<int*>(base + b.L.oCtl);
   b.perm = reinterpret_cast<int*>(base + b.L.oPerm);
   b.drop = reinterpret_cast<int*>(base + b.L.oDrop);
+  b.rows = reinterpret_cast<T*>(base + b.L.oRows);
+  b.dsc = reinterpret_cast<T*>(base + b.L.oDsc);
+  b.gpart = reinterpret_cast<double*>(base + b.L.oGpart);
   b.dmax = dmax;
   b.rcap = rcap;
   return b;
@@ -168,21 +172,25 @@ cudaError_t gemm(cudaStream_t s, int batch, int m, int n, int k, const cx<T>* A,
 
 
 // ---------------------------------------------------------------- per-instance kernels
-// Gram epilogue: D holds H H^H on entry.  G_t = that + alpha I, exactly Hermitian (upper
-// triangle wins), into the resident Gs; in update mode D becomes dG = G_t - G_{t-1}, scaled by
-// an exact power of two to unit Frobenius norm when the low-rank step will run.
+// Gram epilogue, kGramTile entries of the K x K matrix per CTA: D holds H H^H (upper triangle)
+// on entry.  G_t = that + alpha I, exactly Hermitian (upper triangle wins), into the resident
+// Gs; in update mode D becomes dG = G_t - G_{t-1}.  Each CTA leaves its partial sums of
+// |dG|^2 and |G_t|^2 for the decision kernel (fixed-order reduction: results do not depend on
+// the batch or on scheduling).
 template <class T>
-__global__ void __launch_bounds__(256) finish_gram_kernel(const StepArgs<T> a, const Bufs<T> w) {
+__global__ void __launch_bounds__(256) gram_tiles_kernel(const StepArgs<T> a, const Bufs<T> w) {
   __shared__ T red[40];
-  const int b = blockIdx.x, tid = threadIdx.x, K = a.K, KK = K * K;
+  const int b = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x, K = a.K;
+  const size_t KK = (size_t)K * K;
   cx<T>* D = w.D + (size_t)b * w.L.sD;
   cx<T>* Gs = a.Gs + (size_t)b * KK;
-  int* ctl = w.ctl + 8 * b;
   const T alpha = a.alpha[b];
   const bool upd = a.mode == MODE_UPDATE;
   T s_dg = 0, s_g = 0;
-  for (int idx = tid; idx < KK; idx += 256) {
-    const int k = idx / K, l = idx - k * K;
+  const size_t i0 = (size_t)tile * kGramTile;
+  const size_t i1 = i0 + kGramTile < KK ? i0 + kGramTile : KK;
+  for (size_t idx = i0 + tid; idx < i1; idx += 256) {
+    const int k = (int)(idx / K), l = (int)(idx - (size_t)k * K);
     if (k > l) continue;
     cx<T> g = D[idx];
     if (k == l) g = cmk(g.re + alpha, T(0));
@@ -192,40 +200,57 @@ __global__ void __launch_bounds__(256) finish_gram_kernel(const StepArgs<T> a, c
       s_dg += cabs2(d);
       s_g += cabs2(g);
       if (k != l) {
-        const cx<T> dl = csub(cconj(g), Gs[l * K + k]);
-        D[l * K + k] = dl;
+        const cx<T> dl = csub(cconj(g), Gs[(size_t)l * K + k]);
+        D[(size_t)l * K + k] = dl;
         s_dg += cabs2(dl);
         s_g += cabs2(g);
       }
     }
     Gs[idx] = g;
-    if (k != l) Gs[l * K + k] = cconj(g);
+    if (k != l) Gs[(size_t)l * K + k] = cconj(g);
   }
-  const double dg2 = (double)block_sum(s_dg, red);
-  const double g2 = (double)block_sum(s_g, red);
+  const T dg = block_sum(s_dg, red);
+  const T gg = block_sum(s_g, red);
+  if (tid == 0) {
+    w.gpart[2 * ((size_t)b * w.L.gtiles + tile)] = (double)dg;
+    w.gpart[2 * ((size_t)b * w.L.gtiles + tile) + 1] = (double)gg;
+  }
+}
+
+// Branch of Algorithm 2 before the low-rank step (one thread per instance): keep, periodic
+// re-inverse, or the low-rank step with dG's exact power-of-two down-scale 2^-e (which brings
+// ||dG||_F into [1/2, 1) for the sketch, CholQR and Jacobi steps) and E_target = eta ||dG||_F^2
+// in the same scale.
+template <class T>
+__global__ void decide_kernel(const StepArgs<T> a, const Bufs<T> w) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.batch) return;
+  double dg2 = 0.0, g2 = 0.0;
+  if (a.mode == MODE_UPDATE) {
+    for (int t = 0; t < w.L.gtiles; ++t) {
+      dg2 += w.gpart[2 * ((size_t)b * w.L.gtiles + t)];
+      g2 += w.gpart[2 * ((size_t)b * w.L.gtiles + t) + 1];
+    }
+  }
   int branch, active = 0, e = 0;
   if (a.mode == MODE_INIT) branch = WBRZF_BRANCH_INIT;
   else if (a.mode == MODE_FULL) branch = WBRZF_BRANCH_FULL;
   else if (a.period > 0 && (a.t % a.period) == 0) branch = WBRZF_BRANCH_PERIODIC;
   else if (sqrt(dg2) <= a.dg_floor_rel * sqrt(g2)) branch = WBRZF_BRANCH_KEEP;
   else { branch = kPending; active = 1; frexp(sqrt(dg2), &e); }
-  if (active) {
-    const T down = (T)ldexp(1.0, -e);
-    for (int idx = tid; idx < KK; idx += 256) D[idx] = cscale(D[idx], down);
-  }
-  if (tid == 0) {
-    ctl[C_ACTIVE] = active;
-    ctl[C_BRANCH] = branch;
-    ctl[C_R] = 0;
-    ctl[C_D] = 0;
-    ctl[C_ITERS] = 0;
-    ctl[C_K0] = a.k_init;
-    ctl[C_EXP] = e;          // C_STATUS: cleared before the Gram product, may hold a timeout
-    w.et[b] = a.eta * ldexp(dg2, -2 * e);
-    w.nrm[2 * b] = dg2;
-    w.nrm[2 * b + 1] = g2;
-    w.nu[b] = (T)ldexp(1.0, e);
-  }
+  int* ctl = w.ctl + 8 * b;
+  ctl[C_ACTIVE] = active;
+  ctl[C_BRANCH] = branch;
+  ctl[C_R] = 0;
+  ctl[C_D] = 0;
+  ctl[C_ITERS] = 0;
+  ctl[C_K0] = a.k_init;
+  ctl[C_EXP] = e;            // C_STATUS: cleared before the Gram product, may hold a timeout
+  w.et[b] = a.eta * ldexp(dg2, -2 * e);
+  w.nrm[2 * b] = dg2;
+  w.nrm[2 * b + 1] = g2;
+  w.nu[b] = (T)ldexp(1.0, e);
+  w.dsc[b] = (T)ldexp(1.0, -e);
 }
 
 // Omega (K x d, zero-padded to dmax columns) of iteration `it`: entry (i, j) from Philox
@@ -322,10 +347,35 @@ __global__ void fwdsubst_kernel(const StepArgs<T> a, const Bufs<T> w, int d) {
   }
 }
 
+// Sum over a CTA of NT threads (NT a multiple of 32, at most 1024); red holds 33 values.
+template <int NT, class T>
+__device__ T block_sum_n(T v, T* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    T r = (l < NT / 32) ? red[l] : T(0);
+    r = warp_sum(r);
+    if (l == 0) red[32] = r;
+  }
+  __syncthreads();
+  const T out = red[32];
+  __syncthreads();
+  return out;
+}
+
 // Cyclic Jacobi eigendecomposition of E (d x d Hermitian, ld dmax): eigenvalues to lam,
-// eigenvectors (columns) to Uh.  Round-robin pairs, one CTA per instance.
-template <class T>
-__global__ void __launch_bounds__(256) jacobi_kernel(const Bufs<T> w, int d) {
+// eigenvectors (columns) to Uh.  Each round rotates the disjoint pairs of the round-robin
+// ordering at once, E <- J^H E J with J the product of the pairs' plane rotations.  Because
+// the pairs are disjoint, every 2 x 2 block (rows of pair k, columns of pair l) of J^H E J
+// depends only on the same block of E and the two rotations, so one phase updates all blocks
+// (and U <- U J) after one phase that computes the rotations: two barriers per round.  The
+// rotation of a pair zeroes its off-diagonal entry: with E_pq = |E_pq| e^{i phi},
+// tan(2 theta) = 2 |E_pq| / (E_qq - E_pp), t = tan(theta) the smaller root, c = 1/sqrt(1+t^2),
+// s = t c, and columns p, q of J are (c, -s e^{-i phi}) and (s, c e^{-i phi}).
+template <int NT, class T>
+__global__ void __launch_bounds__(NT) jacobi_kernel(const Bufs<T> w, int d) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int b = blockIdx.x, tid = threadIdx.x, dmax = w.dmax;
   if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
@@ -338,7 +388,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const Bufs<T> w, int d) {
   int* pp = reinterpret_cast<int*>(red + 40);
   int* pq = pp + dmax;
   const cx<T>* Eg = w.E + (size_t)b * w.L.sGy;
-  for (int e = tid; e < d * d; e += 256) {
+  for (int e = tid; e < d * d; e += NT) {
     const int i = e / d, j = e - i * d;
     E[i * dmax + j] = Eg[i * dmax + j];
     U[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
@@ -348,17 +398,19 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const Bufs<T> w, int d) {
   const T eps = (sizeof(T) == 4) ? T(1e-10) : T(1e-26);
   for (int sweep = 0; sweep < ((sizeof(T) == 4) ? 12 : 20); ++sweep) {
     T off = 0, tot = 0;
-    for (int e = tid; e < d * d; e += 256) {
+    for (int e = tid; e < d * d; e += NT) {
       const int i = e / d, j = e - i * d;
       const T v = cabs2(E[i * dmax + j]);
       tot += v;
       if (i != j) off += v;
     }
-    off = block_sum(off, red);
-    tot = block_sum(tot, red);
+    off = block_sum_n<NT>(off, red);
+    tot = block_sum_n<NT>(tot, red);
     if (!(off > eps * tot)) break;
     for (int rnd = 0; rnd < dm1; ++rnd) {
-      for (int k = tid; k < npairs; k += 256) {
+      // phase 1: the rotation of every pair (circle method: x_i = 1 + ((i + rnd) mod (dd-1));
+      // pairs (0, x_0), (x_k, x_{dd-1-k}))
+      for (int k = tid; k < npairs; k += NT) {
         int p0, q0;
         if (k == 0) { p0 = 0; q0 = 1 + rnd; }
         else {
@@ -370,7 +422,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const Bufs<T> w, int d) {
         }
         const int p1 = min(p0, q0), q1 = max(p0, q0);
         bool act = false;
-        T c = 1, s = 0;
+        T c = 1, sn = 0;
         cx<T> f = cmk<T>(1, 0);
         if (q1 < d) {
           const cx<T> bpq = E[p1 * dmax + q1];
@@ -381,50 +433,74 @@ __global__ void __launch_bounds__(256) jacobi_kernel(const Bufs<T> w, int d) {
             const T tau = (E[q1 * dmax + q1].re - E[p1 * dmax + p1].re) * (T(0.5) * inv);
             const T t = copysign(T(1), tau) / (fabs(tau) + sqrt(T(1) + tau * tau));
             c = T(1) / sqrt(T(1) + t * t);
-            s = t * c;
+            sn = t * c;
             act = true;
           }
         }
-        pp[k] = act ? p1 : -1;
+        pp[k] = act ? p1 : -1 - p1;       // inactive: -1 - p (p still needed as a row/column)
         pq[k] = q1;
         rc[k] = c;
-        rs[k] = s;
+        rs[k] = sn;
         ph[k] = f;
       }
       __syncthreads();
-      for (int e = tid; e < npairs * d; e += 256) {
-        const int k = e / d, i = e - k * d;
-        const int p1 = pp[k];
-        if (p1 < 0) continue;
-        const int q1 = pq[k];
-        const T c = rc[k], s = rs[k];
-        const cx<T> ep = E[i * dmax + p1], eq = cmul(ph[k], E[i * dmax + q1]);
-        E[i * dmax + p1] = csub(cscale(ep, c), cscale(eq, s));
-        E[i * dmax + q1] = cadd(cscale(ep, s), cscale(eq, c));
-        const cx<T> up = U[i * dmax + p1], uq = cmul(ph[k], U[i * dmax + q1]);
-        U[i * dmax + p1] = csub(cscale(up, c), cscale(uq, s));
-        U[i * dmax + q1] = cadd(cscale(up, s), cscale(uq, c));
+      // phase 2a: E's 2 x 2 blocks (rows of pair k, columns of pair l) <- J_k^H block J_l
+      for (int e = tid; e < npairs * npairs; e += NT) {
+        const int k = e / npairs, l = e - k * npairs;
+        const int pk = pp[k], pl = pp[l];
+        if (pk < 0 && pl < 0) continue;                 // both identity: block unchanged
+        const int rp = pk < 0 ? -1 - pk : pk, rq = pq[k];
+        const int cp = pl < 0 ? -1 - pl : pl, cq = pq[l];
+        const bool rq_ok = rq < d, cq_ok = cq < d;
+        cx<T> a00 = E[rp * dmax + cp];
+        cx<T> a01 = cq_ok ? E[rp * dmax + cq] : cmk<T>(0, 0);
+        cx<T> a10 = rq_ok ? E[rq * dmax + cp] : cmk<T>(0, 0);
+        cx<T> a11 = (rq_ok && cq_ok) ? E[rq * dmax + cq] : cmk<T>(0, 0);
+        if (pl >= 0) {          // columns: col_p <- c col_p - s f col_q; col_q <- s col_p + c f col_q
+          const T c = rc[l], sn = rs[l];
+          const cx<T> f = ph[l];
+          const cx<T> q0 = cmul(f, a01), q1v = cmul(f, a11);
+          const cx<T> n00 = csub(cscale(a00, c), cscale(q0, sn));
+          const cx<T> n01 = cadd(cscale(a00, sn), cscale(q0, c));
+          const cx<T> n10 = csub(cscale(a10, c), cscale(q1v, sn));
+          const cx<T> n11 = cadd(cscale(a10, sn), cscale(q1v, c));
+          a00 = n00; a01 = n01; a10 = n10; a11 = n11;
+        }
+        if (pk >= 0) {          // rows: row_p <- c row_p - s conj(f) row_q; row_q <- s row_p + c conj(f) row_q
+          const T c = rc[k], sn = rs[k];
+          const cx<T> fc = cconj(ph[k]);
+          const cx<T> q0 = cmul(fc, a10), q1v = cmul(fc, a11);
+          const cx<T> n00 = csub(cscale(a00, c), cscale(q0, sn));
+          const cx<T> n10 = cadd(cscale(a00, sn), cscale(q0, c));
+          const cx<T> n01 = csub(cscale(a01, c), cscale(q1v, sn));
+          const cx<T> n11 = cadd(cscale(a01, sn), cscale(q1v, c));
+          a00 = n00; a01 = n01; a10 = n10; a11 = n11;
+        }
+        E[rp * dmax + cp] = a00;
+        if (cq_ok) E[rp * dmax + cq] = a01;
+        if (rq_ok) E[rq * dmax + cp] = a10;
+        if (rq_ok && cq_ok) E[rq * dmax + cq] = a11;
       }
-      __syncthreads();
-      for (int e = tid; e < npairs * d; e += 256) {
-        const int k = e / d, j = e - k * d;
-        const int p1 = pp[k];
-        if (p1 < 0) continue;
-        const int q1 = pq[k];
-        const T c = rc[k], s = rs[k];
-        const cx<T> ep = E[p1 * dmax + j], eq = cmul(cconj(ph[k]), E[q1 * dmax + j]);
-        E[p1 * dmax + j] = csub(cscale(ep, c), cscale(eq, s));
-        E[q1 * dmax + j] = cadd(cscale(ep, s), cscale(eq, c));
+      // phase 2b: U <- U J (columns of the active pairs)
+      for (int e = tid; e < npairs * d; e += NT) {
+        const int l = e / d, i = e - l * d;
+        const int pl = pp[l];
+        if (pl < 0) continue;
+        const int ql = pq[l];
+        const T c = rc[l], sn = rs[l];
+        const cx<T> up = U[i * dmax + pl], uq = cmul(ph[l], U[i * dmax + ql]);
+        U[i * dmax + pl] = csub(cscale(up, c), cscale(uq, sn));
+        U[i * dmax + ql] = cadd(cscale(up, sn), cscale(uq, c));
       }
       __syncthreads();
     }
   }
   cx<T>* Ug = w.Uh + (size_t)b * w.L.sGy;
-  for (int e = tid; e < d * d; e += 256) {
+  for (int e = tid; e < d * d; e += NT) {
     const int i = e / d, j = e - i * d;
     Ug[i * dmax + j] = U[i * dmax + j];
   }
-  for (int j = tid; j < d; j += 256) w.lam[(size_t)b * dmax + j] = fmax(E[j * dmax + j].re, T(0));
+  for (int j = tid; j < d; j += NT) w.lam[(size_t)b * dmax + j] = fmax(E[j * dmax + j].re, T(0));
 }
 
 // Energy rule (eq. 14) and Algorithm 1's loop control; on exit the branch of Algorithm 2 and,
@@ -651,29 +727,48 @@ __global__ void fixup_kernel(const StepArgs<T> a, const Bufs<T> w, int p, int bs
   if (!inP) X[(size_t)(P0 + c) * K + i] = cscale(w.PV[(size_t)b * w.L.sPR + (size_t)c * K + i], T(-1));
 }
 
-// On entry D = M = (G - alpha I) X = H H^H X: scale s, per-user SINR and the sum-rate (eq. 15)
+// Row sums of M = (G - alpha I) X = H H^H X (in D), one warp per user n: Re sum_i conj(X_ni)
+// M_ni (its sum over n is ||H^H X||_F^2), the interference sum_{i != n} |M_ni|^2 and the
+// signal |M_nn|^2 (Section VI eq. 15; user n's gain on beam i is (H W)_{n i} = s M_{n i}).
 template <class T>
-__global__ void __launch_bounds__(256) sinr_kernel(const StepArgs<T> a, const Bufs<T> w) {
+__global__ void __launch_bounds__(256) sinr_rows_kernel(const StepArgs<T> a, const Bufs<T> w) {
+  const int b = blockIdx.y, K = a.K;
+  const int n = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (n >= K) return;
+  const cx<T>* M = w.D + (size_t)b * w.L.sD + (size_t)n * K;
+  const cx<T>* X = a.Xs + (size_t)b * K * K + (size_t)n * K;
+  T part = 0, intf = 0, sig = 0;
+  for (int i = lane; i < K; i += 32) {
+    const cx<T> m = M[i], x = X[i];
+    part += x.re * m.re + x.im * m.im;
+    if (i == n) sig = cabs2(m);
+    else intf += cabs2(m);
+  }
+  part = warp_sum(part);
+  intf = warp_sum(intf);
+  sig = warp_sum(sig);
+  if (lane == 0) {
+    T* r = w.rows + 3 * ((size_t)b * K + n);
+    r[0] = part;
+    r[1] = intf;
+    r[2] = sig;
+  }
+}
+
+// Scale s = sqrt(P_t / ||H^H X||_F^2), SINR_n and R_sum = sum_n log2(1 + SINR_n) per instance
+template <class T>
+__global__ void __launch_bounds__(256) sinr_final_kernel(const StepArgs<T> a, const Bufs<T> w) {
   __shared__ T red[40];
-  const int b = blockIdx.x, tid = threadIdx.x, K = a.K, KK = K * K;
-  const cx<T>* M = w.D + (size_t)b * w.L.sD;
-  const cx<T>* X = a.Xs + (size_t)b * KK;
+  const int b = blockIdx.x, tid = threadIdx.x, K = a.K;
+  const T* rows = w.rows + 3 * (size_t)b * K;
   const T sigma2 = a.sigma2[b];
   T part = 0;
-  for (int idx = tid; idx < KK; idx += 256) {
-    const cx<T> x = X[idx], m = M[idx];
-    part += x.re * m.re + x.im * m.im;
-  }
+  for (int n = tid; n < K; n += 256) part += rows[3 * n];
   const T wn2 = block_sum(part, red);
   const T s = sqrt(a.p_t / wn2);
   T rate = 0;
   for (int n = tid; n < K; n += 256) {
-    const T sig = s * s * cabs2(M[(size_t)n * K + n]);
-    T intf = 0;
-    for (int i = 0; i < K; ++i)
-      if (i != n) intf += cabs2(M[(size_t)n * K + i]);
-    intf *= s * s;
-    const T sn = sig / (intf + sigma2);
+    const T sn = (s * s * rows[3 * n + 2]) / (s * s * rows[3 * n + 1] + sigma2);
     a.sinr[(size_t)b * K + n] = (float)sn;
     rate += log2(T(1) + sn);
   }
@@ -710,7 +805,11 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
 #define WB_TRY(x) do { e = (x); if (e != cudaSuccess) return e; ++nl; } while (0)
   const BlockedSmem sm = blocked_smem(dmax, rcap, sizeof(cx<T>), sizeof(T));
   const size_t js = sm.jacobi, cs = sm.cholesky, ps = sm.capinv;
-  e = cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)js);
+  e = cudaFuncSetAttribute(jacobi_kernel<256, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)js);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(jacobi_kernel<1024, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)js);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(cholesky_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
   if (e == cudaSuccess)
@@ -734,7 +833,9 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
   if (!(sizeof(T) == 4 && a.tc_products))
     WB_TRY(gemm<T>(s, B, K, K, N, a.H, N, (size_t)K * N, 0, a.H, N, (size_t)K * N, 1, w.D, K,
                    L.sD, one, nullptr, zero, nullptr, 0, 0));
-  finish_gram_kernel<T><<<B, 256, 0, s>>>(a, w);
+  gram_tiles_kernel<T><<<dim3(L.gtiles, B), 256, 0, s>>>(a, w);
+  WB_TRY(cudaGetLastError());
+  decide_kernel<T><<<(B + 127) / 128, 128, 0, s>>>(a, w);
   WB_TRY(cudaGetLastError());
   if ((e = mark(1)) != cudaSuccess) return e;
   if (a.mode == MODE_UPDATE) {
@@ -745,8 +846,10 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
       const int nq = (dmax + 1) / 2;
       omega_kernel<T><<<dim3((K * nq + 255) / 256, B), 256, 0, s>>>(a, w, it, d);
       WB_TRY(cudaGetLastError());
+      // Y = (2^-e dG) Omega: the power-of-two scale is exact, so applying it to the product
+      // gives the same values as scaling dG first
       WB_TRY(gemm<T>(s, B, K, dmax, K, w.D, K, L.sD, 0, w.Om, dmax, L.sOm, 0, w.Q, dmax, L.sOm,
-                     one, nullptr, zero, w.ctl, C_ACTIVE, 2));
+                     one, w.dsc, zero, w.ctl, C_ACTIVE, 2));
       for (int pass = 0; pass < 2; ++pass) {
         WB_TRY(gemm<T>(s, B, d, d, K, w.Q, dmax, L.sOm, 1, w.Q, dmax, L.sOm, 0, w.Gy, dmax,
                        L.sGy, one, nullptr, zero, w.ctl, C_ACTIVE, 2));
@@ -756,10 +859,11 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
         WB_TRY(cudaGetLastError());
       }
       WB_TRY(gemm<T>(s, B, dmax, K, K, w.Q, dmax, L.sOm, 1, w.D, K, L.sD, 0, w.Bm, K, L.sBm,
-                     one, nullptr, zero, w.ctl, C_ACTIVE, 2));
+                     one, w.dsc, zero, w.ctl, C_ACTIVE, 2));
       WB_TRY(gemm<T>(s, B, d, d, K, w.Bm, K, L.sBm, 0, w.Bm, K, L.sBm, 1, w.E, dmax, L.sGy,
                      one, nullptr, zero, w.ctl, C_ACTIVE, 2));
-      jacobi_kernel<T><<<B, 256, js, s>>>(w, d);
+      if (d > 32) jacobi_kernel<1024, T><<<B, 1024, js, s>>>(w, d);
+      else jacobi_kernel<256, T><<<B, 256, js, s>>>(w, d);
       WB_TRY(cudaGetLastError());
       rank_kernel<T><<<B, 256, 0, s>>>(a, w, it, d, last);
       WB_TRY(cudaGetLastError());
@@ -815,7 +919,9 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
   // the product, since G X - alpha X cancels to about I - I when alpha dominates H H^H.
   WB_TRY(gemm<T>(s, B, K, K, K, a.Gs, K, KK, 0, a.Xs, K, KK, 0, w.D, K, L.sD, one, nullptr,
                  zero, nullptr, 0, 0, a.alpha));
-  sinr_kernel<T><<<B, 256, 0, s>>>(a, w);
+  sinr_rows_kernel<T><<<dim3((K + 7) / 8, B), 256, 0, s>>>(a, w);
+  WB_TRY(cudaGetLastError());
+  sinr_final_kernel<T><<<B, 256, 0, s>>>(a, w);
   WB_TRY(cudaGetLastError());
   if constexpr (sizeof(T) == 4) {
     if (a.tc_products) {

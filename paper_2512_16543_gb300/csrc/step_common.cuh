@@ -130,12 +130,18 @@ __host__ __device__ inline size_t tc_smem_bytes(int K, int dmax, int rcap) {
 // ---------------------------------------------------------------- blocked (any-K) engine
 // Per-instance scratch of the multi-kernel engine, carved after the common workspace.  Every
 // buffer is batch-strided; `ld` values are the leading dimensions the kernels use.
+constexpr int kGramTile = 2048;   // Gram-epilogue entries per CTA of the blocked engine
+
 struct BlockedLayout {
   // complex buffers (offsets in bytes from the blocked base, per-instance strides in elements)
   size_t oD, oOm, oQ, oGy, oBm, oE, oUh, oUr, oL, oT, oRh, oZ, oCm, oCZ, oPC, oPR, oPU, oPV, oPb;
   size_t sD, sOm, sGy, sBm, sUr, sL, sRh, sCm, sPC, sPR, sPb;
   // real / double / int arrays
   size_t oLam, oRinv, oWs, oNu, oEt, oNrm, oCtl, oPerm, oDrop;
+  // multi-CTA reductions: Gram tiles' partial sums of |dG|^2 and |G|^2 (double, kGramTile
+  // entries per tile), the per-user SINR row sums (3 reals per user), the dG down-scale 2^-e
+  size_t oGpart, oRows, oDsc;
+  int gtiles;
   // complex64 only, operands of the tensor-core products (floats):
   //   P  [batch][4][K][Np]   Re_hi, Im_hi, Re_lo, Im_lo planes of H (TF32), Np = N rounded to 4
   //   T  [batch][N][2 Kp]    TF32 H^T with interleaved users, Kp = K rounded to 2 (aliases P)
@@ -177,6 +183,10 @@ __host__ __device__ inline BlockedLayout blocked_layout(int batch, int N, int K,
   L.oCtl = take(8, 4);
   L.oPerm = take((size_t)dmax, 4);
   L.oDrop = take((size_t)dmax, 4);
+  L.gtiles = (int)(((size_t)K * K + kGramTile - 1) / kGramTile);
+  L.oGpart = take(2 * (size_t)L.gtiles, 8);
+  L.oRows = take(3 * (size_t)K, tb);
+  L.oDsc = take(1, tb);
   L.Np = (N + 3) / 4 * 4;
   L.Kp = (K + 1) / 2 * 2;
   L.sP = 4 * (size_t)K * L.Np;
