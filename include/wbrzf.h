@@ -175,6 +175,25 @@ wbrzf_status wbrzf_full_inverse(wbrzf* h, const void* H_t, void* W_out);
 wbrzf_status wbrzf_update(wbrzf* h, const void* H_t, void* W_out);
 
 /*
+ * Masked variants (not part of the paper's method; for serving many states whose requests
+ * arrive at different times).  active: device array of `batch` bytes, or NULL for all
+ * instances.  Only instances with a nonzero byte take the step: their state, W_out rows,
+ * SINR, sum-rate, step info and snapshot index advance; every other instance's state, step
+ * info, snapshot index and W_out rows are left as they were (its rows of H_t are not read
+ * for results).  Each instance keeps its own snapshot index t (0 after a full inverse, + 1
+ * per update it takes), which sets its Philox counters and its periodic re-inversion, so an
+ * instance's results do not depend on which other instances share its steps.  The caller
+ * must not update an instance before its first full inverse.
+ */
+wbrzf_status wbrzf_full_inverse_masked(wbrzf* h, const void* H_t, void* W_out,
+                                       const uint8_t* active);
+wbrzf_status wbrzf_update_masked(wbrzf* h, const void* H_t, void* W_out, const uint8_t* active);
+
+/* Copy the snapshot indices t of the first `count` instances to host memory (synchronises
+ * the stream). */
+wbrzf_status wbrzf_get_steps(wbrzf* h, int* host_out, int count);
+
+/*
  * Copy the last call's per-user SINR (device float[batch*K], may be NULL) and per-instance
  * sum-rate R_sum (device float[batch], may be NULL) into caller buffers, on the stream.
  */

@@ -90,6 +90,12 @@ def lib() -> ctypes.CDLL:
         f = getattr(L, name)
         f.restype = i32
         f.argtypes = [vp, vp, vp]
+    for name in ("wbrzf_full_inverse_masked", "wbrzf_update_masked"):
+        f = getattr(L, name)
+        f.restype = i32
+        f.argtypes = [vp, vp, vp, vp]
+    L.wbrzf_get_steps.restype = i32
+    L.wbrzf_get_steps.argtypes = [vp, ctypes.POINTER(ctypes.c_int), i32]
     L.wbrzf_sum_rate.restype = i32
     L.wbrzf_sum_rate.argtypes = [vp, vp, vp]
     L.wbrzf_step_info_get.restype = i32
@@ -196,15 +202,36 @@ class WBRZF:
         return W
 
     # ------------------------------------------------------------------ API
-    def full_inverse(self, H: torch.Tensor, W: torch.Tensor | None = None) -> torch.Tensor:
+    def _mask(self, active: torch.Tensor | None):
+        if active is None:
+            return None
+        if active.dtype != torch.uint8 or active.device != self.device or \
+                not active.is_contiguous() or active.numel() != self.batch:
+            raise ValueError("active must be a contiguous uint8 tensor of batch entries on the "
+                             "handle's device")
+        return _ptr(active)
+
+    def full_inverse(self, H: torch.Tensor, W: torch.Tensor | None = None,
+                     active: torch.Tensor | None = None) -> torch.Tensor:
+        """Direct inverse of every instance (or of those with active != 0)."""
         W = self._out(W)
-        _check(lib().wbrzf_full_inverse(self._h, _ptr(self._in(H)), _ptr(W)), "wbrzf_full_inverse")
+        _check(lib().wbrzf_full_inverse_masked(self._h, _ptr(self._in(H)), _ptr(W),
+                                               self._mask(active)), "wbrzf_full_inverse")
         return W
 
-    def update(self, H: torch.Tensor, W: torch.Tensor | None = None) -> torch.Tensor:
+    def update(self, H: torch.Tensor, W: torch.Tensor | None = None,
+               active: torch.Tensor | None = None) -> torch.Tensor:
+        """One snapshot of every instance (or of those with active != 0)."""
         W = self._out(W)
-        _check(lib().wbrzf_update(self._h, _ptr(self._in(H)), _ptr(W)), "wbrzf_update")
+        _check(lib().wbrzf_update_masked(self._h, _ptr(self._in(H)), _ptr(W),
+                                         self._mask(active)), "wbrzf_update")
         return W
+
+    def steps(self) -> list[int]:
+        """Per-instance snapshot index t (synchronises the stream)."""
+        buf = (ctypes.c_int * self.batch)()
+        _check(lib().wbrzf_get_steps(self._h, buf, self.batch), "wbrzf_get_steps")
+        return list(buf)
 
     def sum_rate(self) -> tuple[torch.Tensor, torch.Tensor]:
         sinr = torch.empty(self.batch, self.K, dtype=torch.float32, device=self.device)

@@ -31,6 +31,8 @@ constexpr int kDirectMask = (1 << WBRZF_BRANCH_INIT) | (1 << WBRZF_BRANCH_PERIOD
                             (1 << WBRZF_BRANCH_FALLBACK);
 
 constexpr int kPending = 15;   // branch code while the low-rank step has not decided
+constexpr int kInactive = 14;  // branch code of an instance that sits this step out
+constexpr int kLiveMask = ~(1 << kInactive);
 
 template <class T>
 struct Bufs {
@@ -181,6 +183,7 @@ template <class T>
 __global__ void __launch_bounds__(256) gram_tiles_kernel(const StepArgs<T> a, const Bufs<T> w) {
   __shared__ T red[40];
   const int b = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x, K = a.K;
+  if (!instance_active(a, b)) return;
   const size_t KK = (size_t)K * K;
   cx<T>* D = w.D + (size_t)b * w.L.sD;
   cx<T>* Gs = a.Gs + (size_t)b * KK;
@@ -225,6 +228,12 @@ template <class T>
 __global__ void decide_kernel(const StepArgs<T> a, const Bufs<T> w) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.batch) return;
+  if (!instance_active(a, b)) {
+    w.ctl[8 * b + C_ACTIVE] = 0;
+    w.ctl[8 * b + C_BRANCH] = kInactive;
+    return;
+  }
+  const int t = step_index(a, b);
   double dg2 = 0.0, g2 = 0.0;
   if (a.mode == MODE_UPDATE) {
     for (int t = 0; t < w.L.gtiles; ++t) {
@@ -235,7 +244,7 @@ __global__ void decide_kernel(const StepArgs<T> a, const Bufs<T> w) {
   int branch, active = 0, e = 0;
   if (a.mode == MODE_INIT) branch = WBRZF_BRANCH_INIT;
   else if (a.mode == MODE_FULL) branch = WBRZF_BRANCH_FULL;
-  else if (a.period > 0 && (a.t % a.period) == 0) branch = WBRZF_BRANCH_PERIODIC;
+  else if (a.period > 0 && (t % a.period) == 0) branch = WBRZF_BRANCH_PERIODIC;
   else if (sqrt(dg2) <= a.dg_floor_rel * sqrt(g2)) branch = WBRZF_BRANCH_KEEP;
   else { branch = kPending; active = 1; frexp(sqrt(dg2), &e); }
   int* ctl = w.ctl + 8 * b;
@@ -270,7 +279,7 @@ __global__ void omega_kernel(const StepArgs<T> a, const Bufs<T> w, int it, int d
     return;
   }
   const uint4 x = philox4x32_10(
-      make_uint4((uint32_t)i, (uint32_t)q, (uint32_t)a.t, 16u * a.ids[b] + (uint32_t)it),
+      make_uint4((uint32_t)i, (uint32_t)q, (uint32_t)step_index(a, b), 16u * a.ids[b] + (uint32_t)it),
       a.seed_lo, a.seed_hi);
   Om[2 * q] = box_muller(x.x, x.y, T(0));
   if (2 * q + 1 < dmax) Om[2 * q + 1] = (2 * q + 1 < d) ? box_muller(x.z, x.w, T(0)) : cmk<T>(0, 0);
@@ -734,7 +743,7 @@ template <class T>
 __global__ void __launch_bounds__(256) sinr_rows_kernel(const StepArgs<T> a, const Bufs<T> w) {
   const int b = blockIdx.y, K = a.K;
   const int n = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (n >= K) return;
+  if (n >= K || !instance_active(a, b)) return;
   const cx<T>* M = w.D + (size_t)b * w.L.sD + (size_t)n * K;
   const cx<T>* X = a.Xs + (size_t)b * K * K + (size_t)n * K;
   T part = 0, intf = 0, sig = 0;
@@ -760,6 +769,7 @@ template <class T>
 __global__ void __launch_bounds__(256) sinr_final_kernel(const StepArgs<T> a, const Bufs<T> w) {
   __shared__ T red[40];
   const int b = blockIdx.x, tid = threadIdx.x, K = a.K;
+  if (!instance_active(a, b)) return;
   const T* rows = w.rows + 3 * (size_t)b * K;
   const T sigma2 = a.sigma2[b];
   T part = 0;
@@ -788,6 +798,7 @@ __global__ void __launch_bounds__(256) sinr_final_kernel(const StepArgs<T> a, co
     inf.status = status;
     a.info[b] = inf;
     w.ws[b] = s;
+    advance_step(a, b, step_index(a, b));   // the last kernel that reads t in this step
   }
 }
 
@@ -826,7 +837,7 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
   if constexpr (sizeof(T) == 4) {
     if (a.tc_products) {
       e = tc_gram_f32(a.H, reinterpret_cast<float*>(base + L.oP), w.D, L.sD, B, N, K, L.Np,
-                      w.ctl + C_STATUS, 8, s, &nl);
+                      w.ctl + C_STATUS, 8, a.active, s, &nl);
       if (e != cudaSuccess) return e;
     }
   }
@@ -927,13 +938,13 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
     if (a.tc_products) {
       e = tc_wprod_f32(a.H, reinterpret_cast<float*>(base + L.oP), a.Xs, w.ws,
                        reinterpret_cast<float*>(base + L.oXB), a.W, B, N, K, L.Kp,
-                       reinterpret_cast<int*>(a.info) + 7, 8, s, &nl);
+                       reinterpret_cast<int*>(a.info) + 7, 8, a.active, s, &nl);
       if (e != cudaSuccess) return e;
     }
   }
   if (!(sizeof(T) == 4 && a.tc_products))
     WB_TRY(gemm<T>(s, B, N, K, K, a.H, N, (size_t)K * N, 1, a.Xs, K, KK, 0, a.W, K,
-                   (size_t)N * K, one, w.ws, zero, nullptr, 0, 0));
+                   (size_t)N * K, one, w.ws, zero, w.ctl, C_BRANCH, kLiveMask));
 #undef WB_TRY
   if ((e = mark(5)) != cudaSuccess) return e;
   *launches = nl;

@@ -112,7 +112,9 @@ wbrzf_status run_noalloc(int batch, int N, int K, const void* H, double alpha, d
   a.N = N;
   a.K = K;
   a.mode = MODE_FULL;
-  a.t = 0;
+  a.tvec = nullptr;        // no step counters: every instance takes the step as snapshot 0
+  a.active = nullptr;
+  a.tc_products = 0;
   a.eta = 1.0;
   a.k_init = 1;
   a.p = 0;

@@ -35,7 +35,10 @@ struct StepArgs {
   T p_t;
   int batch, N, K;
   int mode;                // StepMode
-  int t;                   // snapshot index (Philox step counter)
+  int* tvec;               // [batch] per-instance snapshot index t (Philox step counter);
+                           // read at the start of a step, t + 1 written at its end (NULL: 0)
+  const unsigned char* active;   // [batch] nonzero: the instance takes this step (NULL: all);
+                                 // an inactive instance's state, outputs and t are untouched
   // rank rule
   double eta;
   int k_init, p, i_max, r_max;
@@ -49,6 +52,23 @@ struct StepArgs {
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+#ifdef __CUDACC__
+// Snapshot index of instance b: 0 for a (re)initialising or full-inversion step
+template <class T>
+__device__ __forceinline__ int step_index(const StepArgs<T>& a, int b) {
+  return (a.mode == MODE_UPDATE && a.tvec != nullptr) ? a.tvec[b] : 0;
+}
+template <class T>
+__device__ __forceinline__ bool instance_active(const StepArgs<T>& a, int b) {
+  return a.active == nullptr || a.active[b] != 0;
+}
+// Called once per instance, after every read of its t in this step.
+template <class T>
+__device__ __forceinline__ void advance_step(const StepArgs<T>& a, int b, int t) {
+  if (a.tvec != nullptr) a.tvec[b] = t + 1;
+}
+#endif
 
 // Bytes of the small-matrix workspace of the phases between the Gram matrix and the
 // precoder: optionally G, X, dG (K x K), the sketch buffers (width dmax), the Woodbury buffers
@@ -239,12 +259,14 @@ cudaError_t run_blocked_f64(const StepArgs<double>& a, unsigned char* base, cuda
 // D (upper triangle, instance stride sD) and W = s H^H X; P, T, XB are the operand buffers of
 // the blocked layout; a timeout ORs WBRZF_STATUS_TIMEOUT into stat[stat_stride * b];
 // *launches grows by the kernels enqueued.
+// active: NULL or the per-instance mask (inactive instances are skipped).
 cudaError_t tc_gram_f32(const cx<float>* H, float* P, cx<float>* D, size_t sD, int batch, int N,
-                        int K, int Np, int* stat, int stat_stride, cudaStream_t s,
-                        int* launches);
+                        int K, int Np, int* stat, int stat_stride, const unsigned char* active,
+                        cudaStream_t s, int* launches);
 cudaError_t tc_wprod_f32(const cx<float>* H, float* T, const cx<float>* X, const float* ws,
                          float* XB, cx<float>* W, int batch, int N, int K, int Kp, int* stat,
-                         int stat_stride, cudaStream_t s, int* launches);
+                         int stat_stride, const unsigned char* active, cudaStream_t s,
+                         int* launches);
 // Tensor-core kernel (complex64, K <= 32, even N); hmap: H as a 2-D FP32 tensor map
 // {2N, batch K}, box {64, K} (step_tc.cu).  `hmap` points to a CUtensorMap.
 cudaError_t launch_step_tc(const StepArgs<float>& a, const void* hmap, size_t smem,

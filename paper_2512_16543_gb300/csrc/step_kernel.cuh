@@ -258,6 +258,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
   const uint32_t inst_id = a.ids[b];
   const T alpha = a.alpha[b];
   const T sigma2 = a.sigma2[b];
+  const int t = step_index(a, b);
   int status = WBRZF_STATUS_OK;
 
   // ---------------------------------------------------------------- 2. perturbation, state
@@ -278,7 +279,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
     const T dgs = block_sum(s_dg, red);
     const T gs = block_sum(s_g, red);
     dg2 = (double)dgs;
-    if (a.period > 0 && (a.t % a.period) == 0) branch = WBRZF_BRANCH_PERIODIC;
+    if (a.period > 0 && (t % a.period) == 0) branch = WBRZF_BRANCH_PERIODIC;
     else if (sqrt(dg2) <= a.dg_floor_rel * sqrt((double)gs)) branch = WBRZF_BRANCH_KEEP;
     else branch = -1;   // decided by the low-rank step
   } else {
@@ -310,7 +311,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
         for (int e = tid; e < K * nq; e += kThreads) {
           const int i = e / nq, q = e - i * nq;
           const uint4 x = philox4x32_10(
-              make_uint4((uint32_t)i, (uint32_t)q, (uint32_t)a.t, 16u * inst_id + (uint32_t)it),
+              make_uint4((uint32_t)i, (uint32_t)q, (uint32_t)t, 16u * inst_id + (uint32_t)it),
               a.seed_lo, a.seed_hi);
           Om[i * dmax + 2 * q] = box_muller(x.x, x.y, T(0));
           if (2 * q + 1 < d) Om[i * dmax + 2 * q + 1] = box_muller(x.z, x.w, T(0));
@@ -830,8 +831,10 @@ __global__ void __launch_bounds__(kThreads, 2) wbrzf_step_kernel(const StepArgs<
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
   const int tid = threadIdx.x;
+  if (!instance_active(a, b)) return;
   const int K = a.K, N = a.N, KK = K * K;
   const int KP = K + 1;
+  const int t_step = step_index(a, b);
   cx<T>* const Hbuf0 = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* const Hbuf1 = Hbuf0 + kChunk * KP;
   const Work<T> w = carve_work<T>(smem_raw + align_up(2 * (size_t)kChunk * KP * sizeof(cx<T>), 16),
@@ -919,6 +922,7 @@ __global__ void __launch_bounds__(kThreads, 2) wbrzf_step_kernel(const StepArgs<
       __syncthreads();
     }
   }
+  if (tid == 0) advance_step(a, b, t_step);
 }
 
 }  // namespace wbk

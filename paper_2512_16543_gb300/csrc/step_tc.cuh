@@ -36,7 +36,9 @@ __global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
   unsigned char* const sm = smem_raw + ((1024 - (raw_u & 1023)) & 1023);
   const int b = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (!instance_active(a, b)) return;
   const int K = a.K, N = a.N, KK = K * K;
+  const int t_step = step_index(a, b);
   const TcLayout Ly = tc_layout(K, a.dmax, a.rcap);
   cx<float>* const G = reinterpret_cast<cx<float>*>(sm + Ly.oGXD);
   cx<float>* const Dm = G + KK;
@@ -277,6 +279,7 @@ __global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
 
   // ------------------------------------------------------------ teardown
   if (*abort_flag && tid == 0) a.info[b].status |= WBRZF_STATUS_TIMEOUT;
+  if (tid == 0) advance_step(a, b, t_step);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {

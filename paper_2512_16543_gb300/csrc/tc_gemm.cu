@@ -49,6 +49,7 @@ struct TcArgs {
   size_t sOut;
   int* stat;              // instance b's status word at stat[stat_stride * b]
   int stat_stride;
+  const unsigned char* active;   // NULL or per-instance mask: inactive instances are skipped
 };
 
 __device__ __forceinline__ bool mbar_wait_drain(uint32_t a, uint32_t parity) {
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = g.K, N = g.N;
   if (g.mode == TC_GRAM && 64 * tn + 63 < 32 * tm) return;   // wholly below the diagonal
+  if (g.active != nullptr && g.active[b] == 0) return;
 
   uint64_t* const bars = reinterpret_cast<uint64_t*>(sm + (size_t)kTcStages * kStageBytes);
   const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + kTcStages),
@@ -329,8 +331,8 @@ cudaError_t set_tc_smem() {
 bool tc_products_supported(int batch) { return batch <= 65535; }
 
 cudaError_t tc_gram_f32(const cx<float>* H, float* P, cx<float>* D, size_t sD, int batch, int N,
-                        int K, int Np, int* stat, int stat_stride, cudaStream_t s,
-                        int* launches) {
+                        int K, int Np, int* stat, int stat_stride, const unsigned char* active,
+                        cudaStream_t s, int* launches) {
   cudaError_t e = set_tc_smem();
   if (e != cudaSuccess) return e;
   const size_t total = (size_t)batch * K * N;
@@ -351,6 +353,7 @@ cudaError_t tc_gram_f32(const cx<float>* H, float* P, cx<float>* D, size_t sD, i
   g.sOut = sD;
   g.stat = stat;
   g.stat_stride = stat_stride;
+  g.active = active;
   const int tiles_m = (K + 31) / 32;
   tc_gemm_kernel<<<dim3(tiles_m * g.tiles_n, batch), kTcThreads, kTcSmem, s>>>(g, ma, mb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -360,7 +363,8 @@ cudaError_t tc_gram_f32(const cx<float>* H, float* P, cx<float>* D, size_t sD, i
 
 cudaError_t tc_wprod_f32(const cx<float>* H, float* T, const cx<float>* X, const float* ws,
                          float* XB, cx<float>* W, int batch, int N, int K, int Kp, int* stat,
-                         int stat_stride, cudaStream_t s, int* launches) {
+                         int stat_stride, const unsigned char* active, cudaStream_t s,
+                         int* launches) {
   cudaError_t e = set_tc_smem();
   if (e != cudaSuccess) return e;
   transpose_h_kernel<<<dim3((N + 31) / 32, (K + 31) / 32, batch), dim3(32, 8), 0, s>>>(H, T, N,
@@ -384,6 +388,7 @@ cudaError_t tc_wprod_f32(const cx<float>* H, float* T, const cx<float>* X, const
   g.sOut = (size_t)N * K;
   g.stat = stat;
   g.stat_stride = stat_stride;
+  g.active = active;
   const int tiles_m = (N + 127) / 128;
   tc_gemm_kernel<<<dim3(tiles_m * g.tiles_n, batch), kTcThreads, kTcSmem, s>>>(g, ma, mb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

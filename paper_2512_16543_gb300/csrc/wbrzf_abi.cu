@@ -25,7 +25,7 @@ wbrzf_status cuda_fail(cudaError_t e) {
 }
 
 struct WsLayout {
-  size_t oG, oX, oInfo, oSinr, oAlpha, oSigma2, oIds, bytes;
+  size_t oG, oX, oInfo, oSinr, oAlpha, oSigma2, oIds, oTvec, bytes;
 };
 
 size_t cx_bytes(wbrzf_precision p) { return p == WBRZF_C128 ? 16 : 8; }
@@ -42,6 +42,7 @@ WsLayout ws_layout(int batch, int K, wbrzf_precision prec) {
   w.oAlpha = o;  o = align_up(o + B * re_bytes(prec), 256);
   w.oSigma2 = o; o = align_up(o + B * re_bytes(prec), 256);
   w.oIds = o;    o = align_up(o + B * sizeof(uint32_t), 256);
+  w.oTvec = o;   o = align_up(o + B * sizeof(int), 256);
   w.bytes = o;
   return w;
 }
@@ -163,7 +164,8 @@ struct wbrzf {
 namespace {
 
 template <class T>
-StepArgs<T> make_args(const wbrzf* h, const void* H, void* W, int mode, int t) {
+StepArgs<T> make_args(const wbrzf* h, const void* H, void* W, int mode,
+                      const unsigned char* active) {
   StepArgs<T> a;
   a.H = static_cast<const cx<T>*>(H);
   a.W = static_cast<cx<T>*>(W);
@@ -180,7 +182,8 @@ StepArgs<T> make_args(const wbrzf* h, const void* H, void* W, int mode, int t) {
   a.N = h->N;
   a.K = h->K;
   a.mode = mode;
-  a.t = t;
+  a.tvec = reinterpret_cast<int*>(h->ws + h->wl.oTvec);
+  a.active = active;
   a.eta = h->rule.eta;
   a.k_init = h->rule.k_init;
   a.p = h->rule.p;
@@ -222,7 +225,8 @@ bool use_blocked(const wbrzf* h) {
          (h->engine == WBRZF_ENGINE_AUTO && !h->simt_ok);
 }
 
-wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
+wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode,
+                      const unsigned char* active) {
   if (!h || !H || !W) return WBRZF_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(H) | reinterpret_cast<uintptr_t>(W)) % cx_bytes(h->prec))
     return WBRZF_ERR_INVALID_ARG;
@@ -232,9 +236,9 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
     int nl = 0;
     cudaEvent_t* ev = h->timing ? h->ev : nullptr;
     if (h->prec == WBRZF_C128)
-      e = run_blocked_f64(make_args<double>(h, H, W, mode, h->t), base, h->stream, &nl, ev);
+      e = run_blocked_f64(make_args<double>(h, H, W, mode, active), base, h->stream, &nl, ev);
     else
-      e = run_blocked_f32(make_args<float>(h, H, W, mode, h->t), base, h->stream, &nl, ev);
+      e = run_blocked_f32(make_args<float>(h, H, W, mode, active), base, h->stream, &nl, ev);
     if (e != cudaSuccess) return cuda_fail(e);
     h->last_engine =
         h->engine == WBRZF_ENGINE_BLOCKED_FMA ? WBRZF_ENGINE_BLOCKED_FMA : WBRZF_ENGINE_BLOCKED;
@@ -249,11 +253,11 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode) {
   if (h->engine == WBRZF_ENGINE_TENSOR && !use_tc) return WBRZF_ERR_UNSUPPORTED;
   if (h->timing && (e = cudaEventRecord(h->ev[0], h->stream)) != cudaSuccess) return cuda_fail(e);
   if (use_tc) {
-    e = launch_step_tc(make_args<float>(h, H, W, mode, h->t), &map, h->smem_tc, h->stream);
+    e = launch_step_tc(make_args<float>(h, H, W, mode, active), &map, h->smem_tc, h->stream);
   } else if (h->prec == WBRZF_C128) {
-    e = launch_step_f64(make_args<double>(h, H, W, mode, h->t), h->smem, h->stream);
+    e = launch_step_f64(make_args<double>(h, H, W, mode, active), h->smem, h->stream);
   } else {
-    e = launch_step_f32(make_args<float>(h, H, W, mode, h->t), h->smem, h->stream);
+    e = launch_step_f32(make_args<float>(h, H, W, mode, active), h->smem, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(e);
   if (h->timing && (e = cudaEventRecord(h->ev[5], h->stream)) != cudaSuccess) return cuda_fail(e);
@@ -367,8 +371,9 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
       reinterpret_cast<float*>(host)[batch + b] = (float)sigma2[b];
     }
   }
-  cudaError_t e = cudaMemcpyAsync(h->ws + wl.oAlpha, host, batch * rb, cudaMemcpyHostToDevice,
-                                  h->stream);
+  cudaError_t e = cudaMemsetAsync(h->ws + wl.oTvec, 0, (size_t)batch * sizeof(int), h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws + wl.oAlpha, host, batch * rb, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->ws + wl.oSigma2, host + batch * rb, batch * rb,
                         cudaMemcpyHostToDevice, h->stream);
@@ -382,20 +387,37 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   return WBRZF_OK;
 }
 
-wbrzf_status wbrzf_full_inverse(wbrzf* h, const void* H_t, void* W_out) {
+wbrzf_status wbrzf_full_inverse_masked(wbrzf* h, const void* H_t, void* W_out,
+                                       const uint8_t* active) {
   if (!h) return WBRZF_ERR_INVALID_ARG;
   h->t = 0;
   const int mode = (h->method == WBRZF_METHOD_FULL_INVERSE) ? MODE_FULL : MODE_INIT;
-  wbrzf_status s = run_step(h, H_t, W_out, mode);
+  wbrzf_status s = run_step(h, H_t, W_out, mode, active);
   if (s == WBRZF_OK) h->initialized = true;
   return s;
 }
 
-wbrzf_status wbrzf_update(wbrzf* h, const void* H_t, void* W_out) {
+wbrzf_status wbrzf_update_masked(wbrzf* h, const void* H_t, void* W_out, const uint8_t* active) {
   if (!h) return WBRZF_ERR_INVALID_ARG;
-  if (h->method == WBRZF_METHOD_FULL_INVERSE) return run_step(h, H_t, W_out, MODE_FULL);
+  if (h->method == WBRZF_METHOD_FULL_INVERSE) return run_step(h, H_t, W_out, MODE_FULL, active);
   if (!h->initialized) return WBRZF_ERR_NOT_INITIALIZED;
-  return run_step(h, H_t, W_out, MODE_UPDATE);
+  return run_step(h, H_t, W_out, MODE_UPDATE, active);
+}
+
+wbrzf_status wbrzf_full_inverse(wbrzf* h, const void* H_t, void* W_out) {
+  return wbrzf_full_inverse_masked(h, H_t, W_out, nullptr);
+}
+
+wbrzf_status wbrzf_update(wbrzf* h, const void* H_t, void* W_out) {
+  return wbrzf_update_masked(h, H_t, W_out, nullptr);
+}
+
+wbrzf_status wbrzf_get_steps(wbrzf* h, int* host_out, int count) {
+  if (!h || !host_out || count < 0 || count > h->batch) return WBRZF_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(host_out, h->ws + h->wl.oTvec, (size_t)count * sizeof(int),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
 }
 
 wbrzf_status wbrzf_sum_rate(wbrzf* h, float* sinr_out, float* sum_rate_out) {
