@@ -257,6 +257,47 @@ long long wbrzf_launch_count(const wbrzf* h);
 void wbrzf_destroy(wbrzf* h);
 
 /*
+ * CUDA-graph replay (not part of the paper's method).  With enable != 0 the next step is
+ * captured into a CUDA graph on a stream the handle owns and replayed, fork/joined with the
+ * handle's stream by events, for every later step with the same kind (full inverse or
+ * update), H_t, W_out and mask pointers; any other pointer recaptures.  Every input a step
+ * reads (H_t's contents, the per-instance snapshot index, the state) lives in device memory,
+ * so a replayed step computes exactly what an enqueued one would; what it saves is the host
+ * work and launch latency of the step's kernels (tens of launches on the blocked engine).
+ * wbrzf_set_engine, wbrzf_set_trace and wbrzf_set_stage_timing drop the captured graph.
+ */
+wbrzf_status wbrzf_set_graph(wbrzf* h, int enable);
+
+/*
+ * Groups: uneven batches (not part of the paper's method).  A group steps n handles at once
+ * -- typically one handle per (N, K) class of a mixed population -- each on a CUDA stream
+ * the group creates, forked from and joined back to cuda_stream by events, so the classes'
+ * kernels overlap on the GPU and the call is ordered on cuda_stream like a single step.
+ * The members keep their own workspaces, rules and methods; while the group exists their
+ * stream is the group's (wbrzf_set_stream on a member is not allowed), and
+ * wbrzf_group_destroy gives them cuda_stream back.  H[i] / W[i]: member i's H_t and W_out.
+ * With wbrzf_group_set_graph(g, 1) the whole group step is captured once into one CUDA graph
+ * (all members, their fork and join) and replayed while H[] and W[] stay the same.
+ *
+ * wbrzf_group_autotune picks each member's engine by measurement: for every engine in
+ * engine_mask (bit e = WBRZF_ENGINE_e) that the member accepts, a full inverse on H0[i] then
+ * `reps` updates on H1[i] are run and the fastest update (CUDA events) wins.  It finishes
+ * with a full inverse on H0[i] with the chosen engine (so the state is that of a fresh
+ * full inverse), synchronises, and returns WBRZF_ERR_UNSUPPORTED if a member accepts none of
+ * the engines.  wbrzf_group_engine returns member i's engine.
+ */
+typedef struct wbrzf_group wbrzf_group;
+wbrzf_status wbrzf_group_create(wbrzf* const* handles, int n, void* cuda_stream,
+                                wbrzf_group** out);
+wbrzf_status wbrzf_group_full_inverse(wbrzf_group* g, const void* const* H, void* const* W);
+wbrzf_status wbrzf_group_update(wbrzf_group* g, const void* const* H, void* const* W);
+wbrzf_status wbrzf_group_set_graph(wbrzf_group* g, int enable);
+wbrzf_status wbrzf_group_autotune(wbrzf_group* g, const void* const* H0, const void* const* H1,
+                                  void* const* W, unsigned engine_mask, int reps);
+int wbrzf_group_engine(const wbrzf_group* g, int i);
+void wbrzf_group_destroy(wbrzf_group* g);
+
+/*
  * Conventional (full-inversion) RZF precoders without any caller-provided device memory.
  * The paper has no counterpart: this entry point exists for callers that cannot allocate
  * device memory at all -- code being recorded into a CUDA graph by stream capture (allocation

@@ -94,6 +94,23 @@ def lib() -> ctypes.CDLL:
         f = getattr(L, name)
         f.restype = i32
         f.argtypes = [vp, vp, vp, vp]
+    L.wbrzf_set_graph.restype = i32
+    L.wbrzf_set_graph.argtypes = [vp, i32]
+    L.wbrzf_group_create.restype = i32
+    L.wbrzf_group_create.argtypes = [ctypes.POINTER(vp), i32, vp, ctypes.POINTER(vp)]
+    for name in ("wbrzf_group_full_inverse", "wbrzf_group_update"):
+        f = getattr(L, name)
+        f.restype = i32
+        f.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.wbrzf_group_set_graph.restype = i32
+    L.wbrzf_group_set_graph.argtypes = [vp, i32]
+    L.wbrzf_group_autotune.restype = i32
+    L.wbrzf_group_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(vp), ctypes.c_uint, i32]
+    L.wbrzf_group_engine.restype = i32
+    L.wbrzf_group_engine.argtypes = [vp, i32]
+    L.wbrzf_group_destroy.restype = None
+    L.wbrzf_group_destroy.argtypes = [vp]
     L.wbrzf_get_steps.restype = i32
     L.wbrzf_get_steps.argtypes = [vp, ctypes.POINTER(ctypes.c_int), i32]
     L.wbrzf_sum_rate.restype = i32
@@ -227,6 +244,10 @@ class WBRZF:
                                          self._mask(active)), "wbrzf_update")
         return W
 
+    def set_graph(self, enable: bool = True) -> None:
+        """Replay steps from a CUDA graph while H, W and the mask stay the same tensors."""
+        _check(lib().wbrzf_set_graph(self._h, int(enable)), "wbrzf_set_graph")
+
     def steps(self) -> list[int]:
         """Per-instance snapshot index t (synchronises the stream)."""
         buf = (ctypes.c_int * self.batch)()
@@ -316,6 +337,9 @@ class WBRZF:
         return int(lib().wbrzf_launch_count(self._h))
 
     def close(self) -> None:
+        grp = getattr(self, "_group", None)
+        if grp is not None:            # a group steps this handle: release the group first
+            grp.close()
         if getattr(self, "_h", None):
             lib().wbrzf_destroy(self._h)
             self._h = None
@@ -367,3 +391,70 @@ def rzf_noalloc(H: torch.Tensor, alpha: float, sigma2: float, p_t: float = 1.0,
     _check(f(B, N, K, prec, H.data_ptr(), alpha, sigma2, p_t, W.data_ptr(),
              sum_rate.data_ptr(), s.cuda_stream), "wbrzf_rzf_noalloc")
     return W, sum_rate
+
+
+class WBRZFGroup:
+    """Several handles (one per (N, K) class of an uneven population) stepped together, each on
+    a stream of its own, ordered on `stream` like a single step (see include/wbrzf.h)."""
+
+    def __init__(self, handles: list, stream: torch.cuda.Stream | None = None):
+        L = lib()
+        self.handles = list(handles)
+        self.stream = stream or torch.cuda.current_stream(self.handles[0].device)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h._h.value for h in self.handles])
+        g = ctypes.c_void_p()
+        _check(L.wbrzf_group_create(arr, len(self.handles), self.stream.cuda_stream,
+                                    ctypes.byref(g)), "wbrzf_group_create")
+        self._g = g
+        for h in self.handles:
+            h._group = self
+
+    def _arrays(self, Hs, Ws):
+        n = len(self.handles)
+        if len(Hs) != n or len(Ws) != n:
+            raise ValueError("one H and one W per member")
+        Ha = (ctypes.c_void_p * n)(*[_ptr(h_._in(H)) for h_, H in zip(self.handles, Hs)])
+        Wa = (ctypes.c_void_p * n)(*[_ptr(h_._out(W)) for h_, W in zip(self.handles, Ws)])
+        return Ha, Wa
+
+    def full_inverse(self, Hs, Ws) -> None:
+        Ha, Wa = self._arrays(Hs, Ws)
+        _check(lib().wbrzf_group_full_inverse(self._g, Ha, Wa), "wbrzf_group_full_inverse")
+
+    def update(self, Hs, Ws) -> None:
+        Ha, Wa = self._arrays(Hs, Ws)
+        _check(lib().wbrzf_group_update(self._g, Ha, Wa), "wbrzf_group_update")
+
+    def set_graph(self, enable: bool = True) -> None:
+        _check(lib().wbrzf_group_set_graph(self._g, int(enable)), "wbrzf_group_set_graph")
+
+    def autotune(self, H0s, H1s, Ws, engines=("tensor", "simt", "blocked", "blocked_fma"),
+                 reps: int = 3) -> list[str]:
+        """Pick each member's engine by timing updates; returns the chosen engine names."""
+        Ha0, Wa = self._arrays(H0s, Ws)
+        Ha1, _ = self._arrays(H1s, Ws)
+        mask = 0
+        for e in engines:
+            mask |= 1 << ENGINES[e]
+        _check(lib().wbrzf_group_autotune(self._g, Ha0, Ha1, Wa, mask, int(reps)),
+               "wbrzf_group_autotune")
+        return self.engines
+
+    @property
+    def engines(self) -> list[str]:
+        names = {v: k for k, v in ENGINES.items()}
+        return [names.get(int(lib().wbrzf_group_engine(self._g, i)), "auto")
+                for i in range(len(self.handles))]
+
+    def close(self) -> None:
+        if getattr(self, "_g", None):
+            lib().wbrzf_group_destroy(self._g)
+            self._g = None
+            for h in self.handles:
+                h._group = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

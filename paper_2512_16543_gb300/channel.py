@@ -97,14 +97,20 @@ class TrajectoryParams:
         return self.user_xy.shape[0]
 
 
-def draw_trajectories(scenario: LeoScenario, batch: int, seed: int) -> TrajectoryParams:
-    """Draw user positions, LOS phases and NLOS fields for `batch` independent trajectories."""
+def draw_trajectories(scenario: LeoScenario, batch: int, seed: int,
+                      radius: torch.Tensor | None = None) -> TrajectoryParams:
+    """Draw user positions, LOS phases and NLOS fields for `batch` independent trajectories.
+
+    radius: optional per-trajectory disc radius [batch] in metres (default: the scenario's).
+    """
     g = torch.Generator(device="cpu")
     g.manual_seed(int(seed))
     K, N = scenario.K, scenario.N
     u = torch.rand(batch, K, generator=g, dtype=torch.float64)
     ang = torch.rand(batch, K, generator=g, dtype=torch.float64) * (2.0 * math.pi)
-    rad = scenario.disc_radius * torch.sqrt(u)
+    r_disc = (scenario.disc_radius if radius is None
+              else radius.to(torch.float64).reshape(batch, 1))
+    rad = r_disc * torch.sqrt(u)
     user_xy = torch.stack([rad * torch.cos(ang), rad * torch.sin(ang)], dim=-1)
     psi = torch.rand(batch, K, generator=g, dtype=torch.float64) * (2.0 * math.pi)
     re = torch.randn(batch, K, N, generator=g, dtype=torch.float64)
@@ -169,3 +175,58 @@ def scenario_batched_256x32() -> LeoScenario:
 def scenario_large_4096x512() -> LeoScenario:
     """64x64 UPA (N=4096), K=512 users in a 300 km disc, SNR 10 dB."""
     return LeoScenario(n_x=64, n_y=64, K=512, disc_radius=300e3, snr_db=10.0)
+
+
+@dataclass
+class UnevenClass:
+    """The instances of one (N, K) class of an uneven population."""
+
+    scenario: LeoScenario        # array and K; its disc radius and SNR are not used
+    index: torch.Tensor          # [B_c] positions in the mixed population
+    radius: torch.Tensor         # [B_c] user-disc radius [m]
+    snr_db: torch.Tensor         # [B_c] P_t / sigma^2 [dB]
+    params: TrajectoryParams
+
+    @property
+    def batch(self) -> int:
+        return int(self.index.numel())
+
+    @property
+    def sigma2(self) -> list[float]:
+        return [self.scenario.p_t / 10.0 ** (float(x) / 10.0) for x in self.snr_db]
+
+    @property
+    def alpha(self) -> list[float]:
+        """Per-instance RZF regulariser K sigma^2 / P_t."""
+        return [self.scenario.K * s / self.scenario.p_t for s in self.sigma2]
+
+
+UNEVEN_ARRAYS = {256: (16, 16), 512: (32, 16), 1024: (32, 32)}
+
+
+def uneven_population(count: int, seed: int, *, n_choices=(256, 512, 1024),
+                      k_choices=(16, 32, 64, 128), radius_km=(20.0, 200.0),
+                      snr_db=(0.0, 20.0)) -> list[UnevenClass]:
+    """`count` instances, each with (N, K) drawn uniformly from the choices, its own user-disc
+    radius ~ U(radius_km) and SNR ~ U(snr_db); grouped by (N, K) class (classes in a fixed
+    order, instances in population order)."""
+    g = torch.Generator(device="cpu")
+    g.manual_seed(int(seed))
+    ni = torch.randint(len(n_choices), (count,), generator=g)
+    ki = torch.randint(len(k_choices), (count,), generator=g)
+    rad = (radius_km[0] + (radius_km[1] - radius_km[0]) *
+           torch.rand(count, generator=g, dtype=torch.float64)) * 1e3
+    snr = snr_db[0] + (snr_db[1] - snr_db[0]) * torch.rand(count, generator=g,
+                                                           dtype=torch.float64)
+    out = []
+    for a, N in enumerate(n_choices):
+        for b, K in enumerate(k_choices):
+            idx = torch.nonzero((ni == a) & (ki == b)).flatten()
+            if idx.numel() == 0:
+                continue
+            nx, ny = UNEVEN_ARRAYS[N]
+            sc = LeoScenario(n_x=nx, n_y=ny, K=K)
+            params = draw_trajectories(sc, int(idx.numel()), seed=seed * 1000 + 10 * a + b,
+                                       radius=rad[idx])
+            out.append(UnevenClass(sc, idx, rad[idx], snr[idx], params))
+    return out

@@ -10,6 +10,7 @@
 
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "step_common.cuh"
 
@@ -159,6 +160,19 @@ struct wbrzf {
   bool blocked_ok;       // the blocked engine's limits hold (workspace checked separately)
   bool timing;           // stage events recorded (wbrzf_set_stage_timing)
   cudaEvent_t ev[6];
+  // CUDA-graph replay of steps (wbrzf_set_graph): the step is captured on gstream once per
+  // (mode, H, W, mask) and replayed while those stay the same
+  bool graph;
+  cudaStream_t gstream;
+  cudaEvent_t gev_in, gev_out;
+  cudaGraphExec_t gexec;
+  const void* gH;
+  const void* gW;
+  const unsigned char* gactive;
+  int gmode;
+  long long glaunches;
+  int glast_engine;
+  bool in_group;         // stepped by a wbrzf_group (its stream belongs to the group)
 };
 
 namespace {
@@ -267,7 +281,84 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode,
   return WBRZF_OK;
 }
 
+void invalidate_graph(wbrzf* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+}
+
+// Capture the enqueue sequence of one step on `cap` (the handle's stream is rebound to `cap`
+// for the capture); on success *exec is the instantiated graph.
+wbrzf_status capture_step(wbrzf* h, cudaStream_t cap, const void* H, void* W, int mode,
+                          const unsigned char* active, cudaGraphExec_t* exec) {
+  cudaStream_t user = h->stream;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e);
+  h->stream = cap;
+  wbrzf_status st = run_step(h, H, W, mode, active);
+  h->stream = user;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cap, &graph);
+  if (st != WBRZF_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
+}
+
+// One step, replayed from a CUDA graph when graph mode is on.
+wbrzf_status run_any(wbrzf* h, const void* H, void* W, int mode, const unsigned char* active) {
+  if (!h->graph) return run_step(h, H, W, mode, active);
+  if (!H || !W) return WBRZF_ERR_INVALID_ARG;
+  if (!(h->gexec && h->gH == H && h->gW == W && h->gactive == active && h->gmode == mode)) {
+    invalidate_graph(h);
+    const long long l0 = h->launches;
+    cudaGraphExec_t ex = nullptr;
+    wbrzf_status st = capture_step(h, h->gstream, H, W, mode, active, &ex);
+    if (st != WBRZF_OK) return st;
+    h->gexec = ex;
+    h->gH = H;
+    h->gW = W;
+    h->gactive = active;
+    h->gmode = mode;
+    h->glaunches = h->launches - l0;
+    h->glast_engine = h->last_engine;
+  } else {
+    h->launches += h->glaunches;
+    h->last_engine = h->glast_engine;
+    h->t += 1;
+  }
+  cudaError_t e = cudaEventRecord(h->gev_in, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->gstream, h->gev_in, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(h->gexec, h->gstream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->gev_out, h->gstream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->gev_out, 0);
+  return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
+}
+
 }  // namespace
+
+// Uneven batches: several handles (one per (N, K) class) stepped together, each on a stream
+// of its own, fork/join with the caller's stream by events; optionally one CUDA graph for the
+// whole group step.
+struct wbrzf_group {
+  std::vector<wbrzf*> m;
+  std::vector<cudaStream_t> ms;
+  std::vector<cudaEvent_t> mev;
+  std::vector<int> engine;          // engine chosen by the autotuner (0: the member's own)
+  cudaStream_t user;
+  cudaEvent_t fork, t0, t1;
+  bool graph;
+  cudaStream_t gs;
+  cudaEvent_t gin, gout;
+  cudaGraphExec_t exec;
+  std::vector<const void*> key;     // H[], W[] of the captured step
+  int kmode;
+  std::vector<long long> glaunch;
+  std::vector<int> glast;
+};
 
 extern "C" {
 
@@ -350,6 +441,16 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   h->simt_ok = simt_ok;
   h->blocked_ok = blocked_ok;
   h->timing = false;
+  h->graph = false;
+  h->gstream = nullptr;
+  h->gev_in = h->gev_out = nullptr;
+  h->gexec = nullptr;
+  h->gH = h->gW = nullptr;
+  h->gactive = nullptr;
+  h->gmode = -1;
+  h->glaunches = 0;
+  h->glast_engine = 0;
+  h->in_group = false;
   {
     const size_t tc = tc_smem_bytes(K, r.dmax, r.rcap);
     h->smem_tc = (simt_ok && prec == WBRZF_C64 && K <= 32 && tc <= 227 * 1024) ? tc : 0;
@@ -392,16 +493,16 @@ wbrzf_status wbrzf_full_inverse_masked(wbrzf* h, const void* H_t, void* W_out,
   if (!h) return WBRZF_ERR_INVALID_ARG;
   h->t = 0;
   const int mode = (h->method == WBRZF_METHOD_FULL_INVERSE) ? MODE_FULL : MODE_INIT;
-  wbrzf_status s = run_step(h, H_t, W_out, mode, active);
+  wbrzf_status s = run_any(h, H_t, W_out, mode, active);
   if (s == WBRZF_OK) h->initialized = true;
   return s;
 }
 
 wbrzf_status wbrzf_update_masked(wbrzf* h, const void* H_t, void* W_out, const uint8_t* active) {
   if (!h) return WBRZF_ERR_INVALID_ARG;
-  if (h->method == WBRZF_METHOD_FULL_INVERSE) return run_step(h, H_t, W_out, MODE_FULL, active);
+  if (h->method == WBRZF_METHOD_FULL_INVERSE) return run_any(h, H_t, W_out, MODE_FULL, active);
   if (!h->initialized) return WBRZF_ERR_NOT_INITIALIZED;
-  return run_step(h, H_t, W_out, MODE_UPDATE, active);
+  return run_any(h, H_t, W_out, MODE_UPDATE, active);
 }
 
 wbrzf_status wbrzf_full_inverse(wbrzf* h, const void* H_t, void* W_out) {
@@ -466,6 +567,7 @@ wbrzf_status wbrzf_set_trace(wbrzf* h, void* trace, size_t bytes) {
   if (trace && (bytes < wbrzf_trace_bytes(h) || reinterpret_cast<uintptr_t>(trace) % 16))
     return WBRZF_ERR_INVALID_ARG;
   h->trace = static_cast<unsigned char*>(trace);
+  invalidate_graph(h);
   return WBRZF_OK;
 }
 
@@ -490,13 +592,14 @@ wbrzf_status wbrzf_set_engine(wbrzf* h, int engine) {
       return WBRZF_ERR_WORKSPACE;
   }
   h->engine = engine;
+  invalidate_graph(h);
   return WBRZF_OK;
 }
 
 int wbrzf_last_engine(const wbrzf* h) { return h ? h->last_engine : 0; }
 
 wbrzf_status wbrzf_set_stream(wbrzf* h, void* cuda_stream) {
-  if (!h) return WBRZF_ERR_INVALID_ARG;
+  if (!h || h->in_group) return WBRZF_ERR_INVALID_ARG;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   return WBRZF_OK;
 }
@@ -505,6 +608,7 @@ long long wbrzf_launch_count(const wbrzf* h) { return h ? h->launches : 0; }
 
 wbrzf_status wbrzf_set_stage_timing(wbrzf* h, int enable) {
   if (!h) return WBRZF_ERR_INVALID_ARG;
+  invalidate_graph(h);
   if (enable && !h->timing) {
     for (int i = 0; i < 6; ++i) {
       cudaError_t e = cudaEventCreate(&h->ev[i]);
@@ -536,10 +640,247 @@ wbrzf_status wbrzf_stage_times(wbrzf* h, float* ms_out) {
   return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
 }
 
+wbrzf_status wbrzf_set_graph(wbrzf* h, int enable) {
+  if (!h) return WBRZF_ERR_INVALID_ARG;
+  invalidate_graph(h);
+  if (enable && !h->graph) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->gev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->graph = true;
+  } else if (!enable && h->graph) {
+    cudaStreamSynchronize(h->gstream);
+    cudaEventDestroy(h->gev_in);
+    cudaEventDestroy(h->gev_out);
+    cudaStreamDestroy(h->gstream);
+    h->graph = false;
+  }
+  return WBRZF_OK;
+}
+
 void wbrzf_destroy(wbrzf* h) {
-  if (h && h->timing)
+  if (!h) return;
+  if (h->timing)
     for (int i = 0; i < 6; ++i) cudaEventDestroy(h->ev[i]);
+  wbrzf_set_graph(h, 0);
   delete h;
+}
+
+// ---------------------------------------------------------------- groups (uneven batches)
+wbrzf_status wbrzf_group_create(wbrzf* const* handles, int n, void* cuda_stream,
+                                wbrzf_group** out) {
+  if (!out || !handles || n < 1) return WBRZF_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!handles[i] || handles[i]->in_group) return WBRZF_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (handles[i] == handles[j]) return WBRZF_ERR_INVALID_ARG;
+  }
+  wbrzf_group* g = new (std::nothrow) wbrzf_group;
+  if (!g) return WBRZF_ERR_INVALID_ARG;
+  g->user = static_cast<cudaStream_t>(cuda_stream);
+  g->graph = false;
+  g->gs = nullptr;
+  g->fork = g->t0 = g->t1 = g->gin = g->gout = nullptr;
+  g->exec = nullptr;
+  g->kmode = -1;
+  cudaError_t e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&g->t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&g->t1);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->gs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->gin, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->gout, cudaEventDisableTiming);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) { cudaStreamDestroy(st); break; }
+    g->m.push_back(handles[i]);
+    g->ms.push_back(st);
+    g->mev.push_back(ev);
+    g->engine.push_back(0);
+    handles[i]->stream = st;        // the member runs on its group stream from now on
+    handles[i]->in_group = true;
+    invalidate_graph(handles[i]);
+  }
+  if (e != cudaSuccess) {
+    wbrzf_group_destroy(g);
+    return cuda_fail(e);
+  }
+  g->glaunch.assign(n, 0);
+  g->glast.assign(n, 0);
+  *out = g;
+  return WBRZF_OK;
+}
+
+namespace {
+
+int group_mode(const wbrzf* h, bool full) {
+  if (h->method == WBRZF_METHOD_FULL_INVERSE) return MODE_FULL;
+  return full ? MODE_INIT : MODE_UPDATE;
+}
+
+// Enqueue every member's step on its stream, forked from and joined to `base`.
+wbrzf_status group_enqueue(wbrzf_group* g, cudaStream_t base, const void* const* H,
+                           void* const* W, bool full) {
+  cudaError_t e = cudaEventRecord(g->fork, base);
+  if (e != cudaSuccess) return cuda_fail(e);
+  for (size_t i = 0; i < g->m.size(); ++i) {
+    wbrzf* h = g->m[i];
+    if ((e = cudaStreamWaitEvent(g->ms[i], g->fork, 0)) != cudaSuccess) return cuda_fail(e);
+    if (full) h->t = 0;
+    wbrzf_status st = run_step(h, H[i], W[i], group_mode(h, full), nullptr);
+    if (st != WBRZF_OK) return st;
+    if (full) h->initialized = true;
+    if ((e = cudaEventRecord(g->mev[i], g->ms[i])) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaStreamWaitEvent(base, g->mev[i], 0)) != cudaSuccess) return cuda_fail(e);
+  }
+  return WBRZF_OK;
+}
+
+wbrzf_status group_step(wbrzf_group* g, const void* const* H, void* const* W, bool full) {
+  if (!g || !H || !W) return WBRZF_ERR_INVALID_ARG;
+  const size_t n = g->m.size();
+  for (size_t i = 0; i < n; ++i) {
+    if (!H[i] || !W[i]) return WBRZF_ERR_INVALID_ARG;
+    if (!full && g->m[i]->method != WBRZF_METHOD_FULL_INVERSE && !g->m[i]->initialized)
+      return WBRZF_ERR_NOT_INITIALIZED;
+  }
+  if (!g->graph) return group_enqueue(g, g->user, H, W, full);
+  bool same = g->exec != nullptr && g->kmode == (full ? 1 : 0);
+  for (size_t i = 0; same && i < n; ++i) same = g->key[2 * i] == H[i] && g->key[2 * i + 1] == W[i];
+  cudaError_t e;
+  if (!same) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+    std::vector<long long> l0(n);
+    for (size_t i = 0; i < n; ++i) l0[i] = g->m[i]->launches;
+    if ((e = cudaStreamBeginCapture(g->gs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(e);
+    wbrzf_status st = group_enqueue(g, g->gs, H, W, full);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(g->gs, &graph);
+    if (st != WBRZF_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { g->exec = nullptr; return cuda_fail(e); }
+    g->key.assign(2 * n, nullptr);
+    for (size_t i = 0; i < n; ++i) {
+      g->key[2 * i] = H[i];
+      g->key[2 * i + 1] = W[i];
+      g->glaunch[i] = g->m[i]->launches - l0[i];
+      g->glast[i] = g->m[i]->last_engine;
+    }
+    g->kmode = full ? 1 : 0;
+  } else {
+    for (size_t i = 0; i < n; ++i) {
+      g->m[i]->launches += g->glaunch[i];
+      g->m[i]->last_engine = g->glast[i];
+      g->m[i]->t += 1;
+    }
+  }
+  e = cudaEventRecord(g->gin, g->user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g->gs, g->gin, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, g->gs);
+  if (e == cudaSuccess) e = cudaEventRecord(g->gout, g->gs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g->user, g->gout, 0);
+  return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
+}
+
+}  // namespace
+
+wbrzf_status wbrzf_group_full_inverse(wbrzf_group* g, const void* const* H, void* const* W) {
+  return group_step(g, H, W, true);
+}
+
+wbrzf_status wbrzf_group_update(wbrzf_group* g, const void* const* H, void* const* W) {
+  return group_step(g, H, W, false);
+}
+
+wbrzf_status wbrzf_group_set_graph(wbrzf_group* g, int enable) {
+  if (!g) return WBRZF_ERR_INVALID_ARG;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  g->exec = nullptr;
+  g->graph = enable != 0;
+  return WBRZF_OK;
+}
+
+wbrzf_status wbrzf_group_autotune(wbrzf_group* g, const void* const* H0, const void* const* H1,
+                                  void* const* W, unsigned engine_mask, int reps) {
+  if (!g || !H0 || !H1 || !W || reps < 1) return WBRZF_ERR_INVALID_ARG;
+  static const int cand[] = {WBRZF_ENGINE_TENSOR, WBRZF_ENGINE_SIMT, WBRZF_ENGINE_BLOCKED,
+                             WBRZF_ENGINE_BLOCKED_FMA};
+  wbrzf_group_set_graph(g, g->graph);          // drops the captured step
+  for (size_t i = 0; i < g->m.size(); ++i) {
+    wbrzf* h = g->m[i];
+    const int own = h->engine;
+    int best = -1;
+    float best_ms = 0.f;
+    for (int c : cand) {
+      if (!((engine_mask >> c) & 1u)) continue;
+      if (wbrzf_set_engine(h, c) != WBRZF_OK) continue;
+      h->t = 0;
+      wbrzf_status st = run_step(h, H0[i], W[i], group_mode(h, true), nullptr);
+      if (st != WBRZF_OK) continue;
+      h->initialized = true;
+      float tmin = -1.f;
+      for (int r = 0; r < reps && st == WBRZF_OK; ++r) {
+        cudaEventRecord(g->t0, h->stream);
+        st = run_step(h, H1[i], W[i], group_mode(h, false), nullptr);
+        cudaEventRecord(g->t1, h->stream);
+        if (cudaEventSynchronize(g->t1) != cudaSuccess) st = WBRZF_ERR_CUDA;
+        float ms = 0.f;
+        if (st == WBRZF_OK && cudaEventElapsedTime(&ms, g->t0, g->t1) == cudaSuccess &&
+            (tmin < 0.f || ms < tmin))
+          tmin = ms;
+      }
+      if (st == WBRZF_OK && tmin >= 0.f && (best < 0 || tmin < best_ms)) {
+        best = c;
+        best_ms = tmin;
+      }
+    }
+    wbrzf_set_engine(h, best >= 0 ? best : own);
+    if (best < 0) return WBRZF_ERR_UNSUPPORTED;
+    g->engine[i] = best;
+    h->t = 0;
+    wbrzf_status st = run_step(h, H0[i], W[i], group_mode(h, true), nullptr);
+    if (st != WBRZF_OK) return st;
+    h->initialized = true;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return WBRZF_OK;
+}
+
+int wbrzf_group_engine(const wbrzf_group* g, int i) {
+  if (!g || i < 0 || i >= (int)g->m.size()) return -1;
+  return g->engine[i] ? g->engine[i] : g->m[i]->engine;
+}
+
+void wbrzf_group_destroy(wbrzf_group* g) {
+  if (!g) return;
+  for (size_t i = 0; i < g->ms.size(); ++i) {
+    cudaStreamSynchronize(g->ms[i]);
+    g->m[i]->stream = g->user;      // members go back to the group's caller stream
+    g->m[i]->in_group = false;
+    cudaEventDestroy(g->mev[i]);
+    cudaStreamDestroy(g->ms[i]);
+  }
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->gs) { cudaStreamSynchronize(g->gs); cudaStreamDestroy(g->gs); }
+  if (g->fork) cudaEventDestroy(g->fork);
+  if (g->t0) cudaEventDestroy(g->t0);
+  if (g->t1) cudaEventDestroy(g->t1);
+  if (g->gin) cudaEventDestroy(g->gin);
+  if (g->gout) cudaEventDestroy(g->gout);
+  delete g;
 }
 
 const char* wbrzf_status_string(wbrzf_status s) {

@@ -61,3 +61,21 @@ def test_device_argument_and_subset():
     assert torch.equal(sub, full[[1, 3]])
     T = ch.trajectory(p, 3, t0=2)
     assert torch.equal(T[0], full)
+
+
+def test_uneven_population_is_seeded_and_spans_the_ranges():
+    a = ch.uneven_population(600, seed=4)
+    b = ch.uneven_population(600, seed=4)
+    assert sum(c.batch for c in a) == 600 and len(a) == 12
+    idx = torch.cat([c.index for c in a])
+    assert torch.equal(torch.sort(idx).values, torch.arange(600))
+    for ca, cb in zip(a, b):
+        assert torch.equal(ca.index, cb.index) and torch.equal(ca.radius, cb.radius)
+        assert torch.equal(ca.params.user_xy, cb.params.user_xy)
+        assert ca.scenario.N in (256, 512, 1024) and ca.scenario.K in (16, 32, 64, 128)
+        assert float(ca.radius.min()) >= 20e3 and float(ca.radius.max()) <= 200e3
+        assert float(ca.snr_db.min()) >= 0.0 and float(ca.snr_db.max()) <= 20.0
+        # users lie inside their instance's own disc
+        r = ca.params.user_xy.norm(dim=-1)
+        assert bool((r <= ca.radius[:, None] + 1e-6).all())
+        np.testing.assert_allclose(ca.alpha, [ca.scenario.K * s for s in ca.sigma2])

@@ -1,0 +1,122 @@
+"""CUDA-graph replay and groups of handles (uneven batches).
+
+A replayed step reads everything from device memory (H's contents, per-instance snapshot
+index, state), so replay must give the same bits as enqueueing; a group steps its members on
+streams of their own and must give each member the same bits as stepping it alone.
+"""
+import numpy as np
+import pytest
+import torch
+
+from gpu_harness import relerr, run_oracle
+from paper_2512_16543_gb300 import binding, channel
+from test_gpu_parity import tf32_w_bound
+
+pytestmark = pytest.mark.gpu
+
+
+def _handle(sc, B, prec, rule, engine, seed_ids=0):
+    wsf = "blocked" if engine.startswith("blocked") else "auto"
+    h = binding.WBRZF(B, sc.N, sc.K, sc.alpha, sc.sigma2, rule=rule, precision=prec,
+                      workspace_for=wsf)
+    if engine != "auto":
+        h.set_engine(engine)
+    return h
+
+
+@pytest.mark.parametrize("engine,prec", [("simt", "c128"), ("tensor", "c64"), ("blocked", "c64"),
+                                         ("blocked_fma", "c128")])
+def test_graph_replay_gives_the_enqueued_bits(engine, prec):
+    sc = channel.scenario_batched_256x32() if prec == "c64" else channel.scenario_single_small()
+    B, T = 3, 9
+    dt = torch.complex64 if prec == "c64" else torch.complex128
+    Hs = channel.trajectory(channel.draw_trajectories(sc, B, seed=9), T, dtype=dt).cuda()
+    rule = binding.RankRule(eta=0.9, k_init=2, p=4, r_max=min(16, sc.K), reinverse_period=4,
+                            seed=3)
+    a = _handle(sc, B, prec, rule, engine)
+    g = _handle(sc, B, prec, rule, engine)
+    g.set_graph(True)
+    Hbuf = torch.empty_like(Hs[0])          # the graph is keyed on fixed buffers
+    Wa = torch.empty(B, sc.N, sc.K, dtype=dt, device="cuda")
+    Wg = torch.empty_like(Wa)
+    for t in range(T):
+        Hbuf.copy_(Hs[t])
+        if t == 0:
+            a.full_inverse(Hbuf, Wa)
+            g.full_inverse(Hbuf, Wg)
+        else:
+            a.update(Hbuf, Wa)
+            g.update(Hbuf, Wg)
+        torch.cuda.synchronize()
+        assert torch.equal(Wa, Wg), t
+        assert torch.equal(a.state()[1], g.state()[1]), t
+        assert a.step_info() == g.step_info()
+    assert a.launches == g.launches and a.last_engine == g.last_engine
+    assert a.steps() == g.steps()
+    a.close()
+    g.close()
+
+
+def _classes():
+    return [(channel.LeoScenario(n_x=8, n_y=8, K=8), 3, "simt"),
+            (channel.scenario_batched_256x32(), 4, "tensor"),
+            (channel.LeoScenario(n_x=20, n_y=10, K=80, disc_radius=100e3), 2, "blocked")]
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_group_gives_each_member_its_own_bits(graph):
+    rule = binding.RankRule(eta=0.9, k_init=2, p=4, r_max=16, reinverse_period=5, seed=8)
+    T = 7
+    cls = _classes()
+    Hs = [channel.trajectory(channel.draw_trajectories(sc, B, seed=40 + i), T,
+                             dtype=torch.complex64).cuda() for i, (sc, B, _) in enumerate(cls)]
+    mk = lambda: [_handle(sc, B, "c64", rule, e) for sc, B, e in cls]   # noqa: E731
+    solo, members = mk(), mk()
+    grp = binding.WBRZFGroup(members)
+    grp.set_graph(graph)
+    Hb = [torch.empty_like(H[0]) for H in Hs]
+    Wg = [torch.empty(B, sc.N, sc.K, dtype=torch.complex64, device="cuda") for sc, B, _ in cls]
+    for t in range(T):
+        for i in range(len(cls)):
+            Hb[i].copy_(Hs[i][t])
+        (grp.full_inverse if t == 0 else grp.update)(Hb, Wg)
+        torch.cuda.synchronize()
+        for i, h in enumerate(solo):
+            W = h.full_inverse(Hs[i][t].contiguous()) if t == 0 else h.update(Hs[i][t].contiguous())
+            torch.cuda.synchronize()
+            assert torch.equal(W, Wg[i]), (t, i)
+            assert torch.equal(h.state()[1], members[i].state()[1]), (t, i)
+    assert [h.last_engine for h in members] == ["simt", "tensor", "blocked"]
+    grp.close()
+    for h in solo + members:
+        h.close()
+
+
+def test_group_autotune_chooses_an_accepted_engine_and_keeps_parity():
+    rule = binding.RankRule(eta=0.9, k_init=2, p=4, r_max=16, reinverse_period=20, seed=8)
+    cls = _classes()
+    Hs = [channel.trajectory(channel.draw_trajectories(sc, B, seed=70 + i), 4,
+                             dtype=torch.complex64).cuda() for i, (sc, B, _) in enumerate(cls)]
+    members = [_handle(sc, B, "c64", rule, "blocked") for sc, B, _ in cls]   # any engine fits
+    grp = binding.WBRZFGroup(members)
+    Ws = [torch.empty(B, sc.N, sc.K, dtype=torch.complex64, device="cuda") for sc, B, _ in cls]
+    chosen = grp.autotune([H[0] for H in Hs], [H[1] for H in Hs], Ws, reps=2)
+    assert chosen[0] in ("tensor", "simt", "blocked", "blocked_fma")
+    assert chosen[1] in ("tensor", "simt", "blocked", "blocked_fma")
+    assert chosen[2] in ("blocked", "blocked_fma")                  # K = 80: blocked only
+    outs = []
+    for t in range(1, 4):
+        grp.update([H[t] for H in Hs], Ws)
+        torch.cuda.synchronize()
+        outs.append([W.cpu().numpy() for W in Ws])
+    for i, (sc, B, _) in enumerate(cls):
+        tf32 = chosen[i] in ("tensor", "blocked")
+        for b in range(B):
+            Hb = Hs[i][:, b].cpu().numpy().astype(np.complex128)
+            ref = run_oracle(Hb, sc.alpha, sc.sigma2, sc.p_t, rule, instance=b)
+            for t in range(1, 4):
+                tol = max(2e-3, 2 * tf32_w_bound(Hb[t], ref[t].X)) if tf32 else 1e-4
+                assert relerr(outs[t - 1][i][b], ref[t].W) < tol, (i, b, t, chosen[i])
+    grp.close()
+    for h in members:
+        h.close()
