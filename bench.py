@@ -34,6 +34,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "precoder updates/s, WB-arSVD vs full-inverse RZF at fixed rate gap; p99 ms"
+UNEVEN = {"count": 4096, "desc": (
+    "uneven_4096: 4096 instances, N ~ U{256, 512, 1024} (16x16, 32x16, 32x32 UPA), "
+    "K ~ U{16, 32, 64, 128}, disc radius ~ U[20, 200] km, SNR ~ U[0, 20] dB, complex64/FP32 "
+    "(TF32 tensor-core products where the autotuned engine uses them), p=8, k_init=2, "
+    "r_max=min(K/2, 64), re-inverse every 20 snapshots; one handle per (N, K) class, classes "
+    "on their own streams, engine per class chosen by the autotuner, group step replayed "
+    "from a CUDA graph")}
 WORKLOADS = {
     # the default line: 1024 independent trajectories, one launch per snapshot
     "batched_256x32": {
@@ -220,7 +227,8 @@ def parse():
     ap.add_argument("--eta", type=float, default=None, help="energy fraction (default: grid)")
     ap.add_argument("--batch", type=int, default=None,
                     help="instances (default: the workload's)")
-    ap.add_argument("--workload", default="batched_256x32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="batched_256x32",
+                    choices=sorted(WORKLOADS) + ["uneven_4096"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=2512)
@@ -251,12 +259,18 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2512_16543_gb300 import channel
-    wl = WORKLOADS[args.workload]
-    sc = getattr(channel, wl["scenario"])()
-    B = args.batch or wl["batch"]
-    params = channel.draw_trajectories(sc, B, seed=args.seed)
-    rule_kw = dict(eta=args.eta or 0.65, k_init=2, p=8, r_max=wl["r_max"], reinverse_period=20,
-                   seed=77)
+    if args.workload == "uneven_4096":       # the oracle on the first (N, K) class
+        c = channel.uneven_population(args.batch or UNEVEN["count"], seed=args.seed)[0]
+        wl = {"desc": UNEVEN["desc"], "cpu_sample": (16, 6)}
+        sc, B, params = c.scenario, c.batch, c.params
+        rule_kw = uneven_rule_kw(sc.K, args.eta or 0.65)
+    else:
+        wl = WORKLOADS[args.workload]
+        sc = getattr(channel, wl["scenario"])()
+        B = args.batch or wl["batch"]
+        params = channel.draw_trajectories(sc, B, seed=args.seed)
+        rule_kw = dict(eta=args.eta or 0.65, k_init=2, p=8, r_max=wl["r_max"],
+                       reinverse_period=20, seed=77)
     n_inst = min(wl["cpu_sample"][0], B)
     n_steps = args.warmup + args.steps if B > 1 else wl["cpu_sample"][1]
     res = cpu_oracle_baseline(params, sc, rule_kw, n_inst, n_steps)
@@ -275,10 +289,183 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def uneven_rule_kw(K: int, eta: float) -> dict:
+    return dict(eta=eta, k_init=2, p=8, r_max=min(K // 2, 64), reinverse_period=20, seed=77)
+
+
+def main_uneven(args):
+    """Uneven batch: 4096 mixed (N, K) instances stepped as one group of per-class handles."""
+    import numpy as np
+    import torch
+
+    from paper_2512_16543_gb300 import binding, channel
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    W_, K_ = args.warmup, args.steps
+    assert W_ >= 3, "at least 3 warm-up steps"
+    count = args.batch or UNEVEN["count"]
+    pop = channel.uneven_population(count, seed=args.seed + 7919 * rank)
+    T = 1 + W_ + K_
+    Hs = [torch.stack([channel.channel_at(c.params, t, device=dev, dtype=torch.complex64)
+                       for t in range(T)]) for c in pop]          # per class [T, B_c, K, N]
+    Hb = [torch.empty_like(H[0]) for H in Hs]                     # graph-keyed input buffers
+    Ws = [torch.empty(c.batch, c.scenario.N, c.scenario.K, dtype=torch.complex64, device=dev)
+          for c in pop]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def make_group(method, eta):
+        hs = []
+        for c in pop:
+            rule = binding.RankRule(**uneven_rule_kw(c.scenario.K, eta))
+            h = binding.WBRZF(c.batch, c.scenario.N, c.scenario.K, c.alpha, c.sigma2,
+                              p_t=c.scenario.p_t, rule=rule, method=method, device=dev,
+                              workspace_for="blocked")
+            h.set_instance_ids([int(i) for i in c.index])
+            hs.append(h)
+        grp = binding.WBRZFGroup(hs)
+        engines = grp.autotune([H[0] for H in Hs], [H[1] for H in Hs], Ws, reps=2)
+        grp.set_graph(True)
+        return grp, hs, engines
+
+    def timed(grp, hs, collect=False):
+        for i, H in enumerate(Hs):
+            Hb[i].copy_(H[0])
+        grp.full_inverse(Hb, Ws)
+        for t in range(1, 1 + W_):
+            for i, H in enumerate(Hs):
+                Hb[i].copy_(H[t])
+            grp.update(Hb, Ws)
+        torch.cuda.synchronize()
+        ms, rates = [], []
+        l0 = sum(h.launches for h in hs)
+        for k in range(K_):
+            for i, H in enumerate(Hs):
+                Hb[i].copy_(H[1 + W_ + k])                     # outside the events
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            grp.update(Hb, Ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            if collect:
+                rates.append(torch.cat([h.sum_rate()[1] for h in hs]).clone())
+        return ms, sum(h.launches for h in hs) - l0, rates
+
+    full, fhs, fengines = make_group("full", 0.9)
+    ms_full, _, rates_full = timed(full, fhs, collect=True)
+    full.close()
+    for h in fhs:
+        h.close()
+    grid = [args.eta] if args.eta else list(ETA_GRID)
+    chosen, gaps, runs = None, {}, {}
+    clock = ClockSampler(local)
+    clock.start()
+    for eta in grid:
+        grp, hs, engines = make_group("wb", eta)
+        ms, launches, rates = timed(grp, hs, collect=True)
+        gap = float(torch.stack([(a - b).abs() for a, b in zip(rates, rates_full)]).mean())
+        gaps[eta] = gap
+        runs[eta] = (ms, launches, engines, grp, hs)
+        if gap <= RATE_GAP_BOUND:
+            chosen = eta
+            break
+        grp.close()
+        for h in hs:
+            h.close()
+    clk = clock.stop()
+    if chosen is None:
+        chosen = grid[-1]
+    ms_wb, launches, engines, grp, hs = runs[chosen]
+
+    # ---- parity against the FP64 oracle on sampled instances (two per class)
+    from oracle import method as om
+    worst_w, worst_rate = 0.0, 0.0
+    for ci, c in enumerate(pop):
+        K = c.scenario.K
+        rule = om.RankRule(**uneven_rule_kw(K, chosen))
+        for j in range(min(2, c.batch)):
+            Hn = Hs[ci][:4, j].cpu().numpy().astype(np.complex128)
+            ref = om.run_trajectory(list(Hn), c.alpha[j], c.scenario.p_t, c.sigma2[j],
+                                    method="wb", rule=rule, instance=int(c.index[j]))
+            h = binding.WBRZF(1, c.scenario.N, K, [c.alpha[j]], [c.sigma2[j]],
+                              p_t=c.scenario.p_t, rule=binding.RankRule(**uneven_rule_kw(K, chosen)),
+                              device=dev, workspace_for="blocked")
+            h.set_engine(engines[ci])
+            h.set_instance_ids([int(c.index[j])])
+            for t in range(4):
+                Hd = Hs[ci][t, j:j + 1].contiguous()
+                W = h.full_inverse(Hd) if t == 0 else h.update(Hd)
+                _, r = h.sum_rate()
+                Wn = W[0].cpu().numpy()
+                worst_w = max(worst_w, float(np.linalg.norm(Wn - ref[t].W) /
+                                             np.linalg.norm(ref[t].W)))
+                worst_rate = max(worst_rate, abs(float(r[0]) - ref[t].sum_rate))
+            h.close()
+
+    tot_wb = barrier_max(sum(ms_wb) / 1e3, world)
+    tot_full = barrier_max(sum(ms_full) / 1e3, world)
+    value = world * count * K_ / tot_wb
+    value_full = world * count * K_ / tot_full
+    peaks = measured_peaks()
+    abytes = sum(c.batch * algorithmic_bytes_per_update(c.scenario.N, c.scenario.K, "wb")
+                 for c in pop)
+    achieved = abytes / (statistics.mean(ms_wb) / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peaks["source"], "kernel": "group step (all classes)",
+                "algorithmic_bytes_per_launch": abytes}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        c = pop[0]
+        res = cpu_oracle_baseline(c.params, c.scenario, uneven_rule_kw(c.scenario.K, chosen),
+                                  min(16, c.batch), 6)
+        cpu = {"value": res["value"], "unit": "updates/s", "cores": res["cores"],
+               "kind": "oracle", "sample": f"{min(16, c.batch)} instances of the (N={c.scenario.N}, "
+               f"K={c.scenario.K}) class x 6 snapshots, FP64 numpy oracle"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+            "steps": K_, "warmup": W_, "ms_per_step": statistics.mean(ms_wb),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": UNEVEN["desc"], "global_batch": world * count, "eta": chosen,
+                       "eta_grid_gaps_bits": gaps, "rate_gap_bound_bits": RATE_GAP_BOUND,
+                       "classes": [{"N": c.scenario.N, "K": c.scenario.K, "batch": c.batch,
+                                    "engine": e} for c, e in zip(pop, engines)],
+                       "l2": "flushed (512 MB write) between timed snapshots",
+                       "parallelism": f"instances sharded over {world} GPU(s)"},
+            "p50_ms": float(np.percentile(ms_wb, 50)), "p99_ms": float(np.percentile(ms_wb, 99)),
+            "full_inverse_rzf": {"value": value_full, "unit": "updates/s",
+                                 "p50_ms": float(np.percentile(ms_full, 50)),
+                                 "p99_ms": float(np.percentile(ms_full, 99)),
+                                 "engines": fengines},
+            "wb_over_full": value / value_full,
+            "error_vs_fp64": {"max_W_relerr": worst_w, "max_sum_rate_gap_bits": worst_rate,
+                              "sample": "2 instances per class x 4 snapshots"},
+            "precision_modes": {"tf32": "measured", "bf16_refine": "not built"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": None,
+            "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    grp.close()
+    for h in hs:
+        h.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "uneven_4096":
+        main_uneven(args)
         return
     import numpy as np
     import torch

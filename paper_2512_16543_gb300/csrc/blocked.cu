@@ -89,7 +89,17 @@ struct GemmArgs {
   T beta;
   const int* ctl; int gidx; int gmask;
   const T* dshift;           // op(A) - dshift[b] I (may be null; square A only)
+  // live extents: rows >= m_live, columns >= n_live of C are zero and terms >= k_live of the
+  // reduction vanish (the callers' operands are zero there); each limit is the host value or,
+  // when its ctl index is >= 0, the smaller of that and the instance's control word
+  int m_live, n_live, k_live, lm, ln, lk;
 };
+
+// Live extents of the batched GEMM from the instance's control words.
+struct Live {
+  int m, n, k;
+};
+__host__ __device__ inline Live live_none() { return Live{1 << 30, 1 << 30, 1 << 30}; }
 
 template <class T>
 __global__ void __launch_bounds__(256) cgemm_kernel(const GemmArgs<T> g) {
@@ -101,18 +111,24 @@ __global__ void __launch_bounds__(256) cgemm_kernel(const GemmArgs<T> g) {
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const cx<T>* A = g.A + (size_t)b * g.sA;
   const cx<T>* B = g.B + (size_t)b * g.sB;
+  int mlive = g.m_live, nlive = g.n_live, klive = g.k_live;
+  if (g.lm >= 0) mlive = min(mlive, g.ctl[8 * b + g.lm]);
+  if (g.ln >= 0) nlive = min(nlive, g.ctl[8 * b + g.ln]);
+  if (g.lk >= 0) klive = min(klive, g.ctl[8 * b + g.lk]);
+  // a tile wholly outside the live rows / columns is zero: skip its reduction
+  const int kend = (m0 >= mlive || n0 >= nlive) ? 0 : min(g.k, klive);
   cx<T> acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = cmk<T>(0, 0);
-  for (int k0 = 0; k0 < g.k; k0 += 16) {
+  for (int k0 = 0; k0 < kend; k0 += 16) {
     for (int e = tid; e < 16 * 64; e += 256) {
       int r, kk;
       if (g.opA == 0) { r = e >> 4; kk = e & 15; } else { kk = e >> 6; r = e & 63; }
       const int gi = m0 + r, gk = k0 + kk;
       cx<T> v = cmk<T>(0, 0);
-      if (gi < g.m && gk < g.k) {
+      if (gi < g.m && gk < kend) {
         v = (g.opA == 0) ? A[(size_t)gi * g.lda + gk] : cconj(A[(size_t)gk * g.lda + gi]);
         if (g.dshift != nullptr && gi == gk) v.re -= g.dshift[b];
       }
@@ -123,7 +139,7 @@ __global__ void __launch_bounds__(256) cgemm_kernel(const GemmArgs<T> g) {
       if (g.opB == 0) { kk = e >> 6; c = e & 63; } else { c = e >> 4; kk = e & 15; }
       const int gj = n0 + c, gk = k0 + kk;
       cx<T> v = cmk<T>(0, 0);
-      if (gj < g.n && gk < g.k)
+      if (gj < g.n && gk < kend)
         v = (g.opB == 0) ? B[(size_t)gk * g.ldb + gj] : cconj(B[(size_t)gj * g.ldb + gk]);
       Bs[kk][c] = v;
     }
@@ -163,10 +179,11 @@ template <class T>
 cudaError_t gemm(cudaStream_t s, int batch, int m, int n, int k, const cx<T>* A, int lda,
                  size_t sA, int opA, const cx<T>* B, int ldb, size_t sB, int opB, cx<T>* C,
                  int ldc, size_t sC, T alpha, const T* scale, T beta, const int* ctl, int gidx,
-                 int gmask, const T* dshift = nullptr) {
+                 int gmask, const T* dshift = nullptr, Live live = live_none(), int lm = -1,
+                 int ln = -1, int lk = -1) {
   if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
   GemmArgs<T> g{m, n, k, A, lda, sA, opA, B, ldb, sB, opB, C, ldc, sC, alpha, scale, beta,
-                ctl, gidx, gmask, dshift};
+                ctl, gidx, gmask, dshift, live.m, live.n, live.k, lm, ln, lk};
   dim3 grid((n + 63) / 64, (m + 63) / 64, batch);
   cgemm_kernel<T><<<grid, 256, 0, s>>>(g);
   return cudaGetLastError();
@@ -859,8 +876,9 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
       WB_TRY(cudaGetLastError());
       // Y = (2^-e dG) Omega: the power-of-two scale is exact, so applying it to the product
       // gives the same values as scaling dG first
+      // (Omega's columns >= d are zero: those tiles of Y are zero without a reduction)
       WB_TRY(gemm<T>(s, B, K, dmax, K, w.D, K, L.sD, 0, w.Om, dmax, L.sOm, 0, w.Q, dmax, L.sOm,
-                     one, w.dsc, zero, w.ctl, C_ACTIVE, 2));
+                     one, w.dsc, zero, w.ctl, C_ACTIVE, 2, nullptr, Live{1 << 30, d, 1 << 30}));
       for (int pass = 0; pass < 2; ++pass) {
         WB_TRY(gemm<T>(s, B, d, d, K, w.Q, dmax, L.sOm, 1, w.Q, dmax, L.sOm, 0, w.Gy, dmax,
                        L.sGy, one, nullptr, zero, w.ctl, C_ACTIVE, 2));
@@ -870,7 +888,7 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
         WB_TRY(cudaGetLastError());
       }
       WB_TRY(gemm<T>(s, B, dmax, K, K, w.Q, dmax, L.sOm, 1, w.D, K, L.sD, 0, w.Bm, K, L.sBm,
-                     one, w.dsc, zero, w.ctl, C_ACTIVE, 2));
+                     one, w.dsc, zero, w.ctl, C_ACTIVE, 2, nullptr, Live{d, 1 << 30, 1 << 30}));
       WB_TRY(gemm<T>(s, B, d, d, K, w.Bm, K, L.sBm, 0, w.Bm, K, L.sBm, 1, w.E, dmax, L.sGy,
                      one, nullptr, zero, w.ctl, C_ACTIVE, 2));
       if (d > 32) jacobi_kernel<1024, T><<<B, 1024, js, s>>>(w, d);
@@ -883,26 +901,28 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
     if ((e = mark(2)) != cudaSuccess) return e;
     const int g = 1 << WBRZF_BRANCH_WOODBURY;
     // L = Q U_r, R^H = nu U_r^H B (nu undoes the scaling of dG), T = X L, Z = R^H X, C = Z L
+    // (U_r vanishes beyond rank r and sketch width d: live extents from the control words)
+    const Live all = live_none();
     WB_TRY(gemm<T>(s, B, K, rcap, dmax, w.Q, dmax, L.sOm, 0, w.Ur, rcap, L.sUr, 0, w.Lm, rcap,
-                   L.sL, one, nullptr, zero, w.ctl, C_BRANCH, g));
+                   L.sL, one, nullptr, zero, w.ctl, C_BRANCH, g, nullptr, all, -1, C_R, C_D));
     WB_TRY(gemm<T>(s, B, rcap, K, dmax, w.Ur, rcap, L.sUr, 1, w.Bm, K, L.sBm, 0, w.Rh, K,
-                   L.sRh, one, w.nu, zero, w.ctl, C_BRANCH, g));
+                   L.sRh, one, w.nu, zero, w.ctl, C_BRANCH, g, nullptr, all, C_R, -1, C_D));
     if (a.trace != nullptr) {
       trace_lr_kernel<T><<<dim3((unsigned)((K * (size_t)rcap + 255) / 256), B), 256, 0, s>>>(a, w);
       WB_TRY(cudaGetLastError());
     }
     WB_TRY(gemm<T>(s, B, K, rcap, K, a.Xs, K, KK, 0, w.Lm, rcap, L.sL, 0, w.Tm, rcap, L.sL,
-                   one, nullptr, zero, w.ctl, C_BRANCH, g));
+                   one, nullptr, zero, w.ctl, C_BRANCH, g, nullptr, all, -1, C_R, -1));
     WB_TRY(gemm<T>(s, B, rcap, K, K, w.Rh, K, L.sRh, 0, a.Xs, K, KK, 0, w.Z, K, L.sRh, one,
-                   nullptr, zero, w.ctl, C_BRANCH, g));
+                   nullptr, zero, w.ctl, C_BRANCH, g, nullptr, all, C_R, -1, -1));
     WB_TRY(gemm<T>(s, B, rcap, rcap, K, w.Z, K, L.sRh, 0, w.Lm, rcap, L.sL, 0, w.Cm, rcap,
-                   L.sCm, one, nullptr, zero, w.ctl, C_BRANCH, g));
+                   L.sCm, one, nullptr, zero, w.ctl, C_BRANCH, g, nullptr, all, C_R, C_R, -1));
     capinv_kernel<T><<<B, 256, ps, s>>>(w);
     WB_TRY(cudaGetLastError());
     WB_TRY(gemm<T>(s, B, rcap, K, rcap, w.Cm, rcap, L.sCm, 0, w.Z, K, L.sRh, 0, w.CZ, K, L.sRh,
-                   one, nullptr, zero, w.ctl, C_BRANCH, g));
+                   one, nullptr, zero, w.ctl, C_BRANCH, g, nullptr, all, C_R, -1, C_R));
     WB_TRY(gemm<T>(s, B, K, K, rcap, w.Tm, rcap, L.sL, 0, w.CZ, K, L.sRh, 0, a.Xs, K, KK,
-                   T(-1), nullptr, one, w.ctl, C_BRANCH, g));
+                   T(-1), nullptr, one, w.ctl, C_BRANCH, g, nullptr, all, -1, -1, C_R));
   }
   if (a.mode != MODE_UPDATE && (e = mark(2)) != cudaSuccess) return e;
   if ((e = mark(3)) != cudaSuccess) return e;
