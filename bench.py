@@ -41,6 +41,12 @@ UNEVEN = {"count": 4096, "desc": (
     "r_max=min(K/2, 64), re-inverse every 20 snapshots; one handle per (N, K) class, classes "
     "on their own streams, engine per class chosen by the autotuner, group step replayed "
     "from a CUDA graph")}
+SERVING = {"states": 2000, "rate": 50000.0, "classes": ((256, 32), (512, 64), (1024, 128)),
+           "desc": ("serving_2000: 2000 resident beam states, (N, K) ~ U{(256, 32), (512, 64), "
+                    "(1024, 128)}, complex64, 50 km discs, SNR 10 dB, p=8, k_init=2, "
+                    "r_max=min(K/2, 64), Poisson requests at 50k/s aggregate, continuous "
+                    "batching per class (masked steps, 2 launches in flight per class), "
+                    "admission by HBM footprint")}
 WORKLOADS = {
     # the default line: 1024 independent trajectories, one launch per snapshot
     "batched_256x32": {
@@ -228,7 +234,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=None,
                     help="instances (default: the workload's)")
     ap.add_argument("--workload", default="batched_256x32",
-                    choices=sorted(WORKLOADS) + ["uneven_4096"])
+                    choices=sorted(WORKLOADS) + ["uneven_4096", "serving_2000"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=2512)
@@ -459,6 +465,111 @@ def main_uneven(args):
         torch.distributed.destroy_process_group()
 
 
+def main_serving(args):
+    """Open-loop Poisson requests against the continuous-batching server; one timed run of
+    args.steps x 10 ms of arrivals after a warm-up that gives every state its full inverse."""
+    import numpy as np
+    import torch
+
+    from paper_2512_16543_gb300 import binding, channel, serving
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n_states, rate = SERVING["states"], SERVING["rate"]
+    duration = args.steps * 0.01
+    sched = serving.poisson_schedule(rate, duration, n_states, seed=args.seed + rank)
+    g = torch.Generator().manual_seed(args.seed)
+    cls_of = torch.randint(len(SERVING["classes"]), (n_states,), generator=g).tolist()
+    counts = [cls_of.count(c) for c in range(len(SERVING["classes"]))]
+    need = collections_counter(st for _, st in sched)
+    T = 2 + max(need.values(), default=0)
+    store, local_idx = [], {}
+    for c, (N, K) in enumerate(SERVING["classes"]):
+        members = [s_ for s_ in range(n_states) if cls_of[s_] == c]
+        for j, s_ in enumerate(members):
+            local_idx[s_] = j
+        nx, ny = channel.UNEVEN_ARRAYS[N]
+        sc = channel.LeoScenario(n_x=nx, n_y=ny, K=K)
+        p = channel.draw_trajectories(sc, len(members), seed=args.seed * 10 + c)
+        store.append((sc, torch.stack([channel.channel_at(p, t, device=dev,
+                                                          dtype=torch.complex64)
+                                       for t in range(T)], dim=1)))   # [B_c, T, K, N]
+    rules = [binding.RankRule(eta=args.eta or 0.65, k_init=2, p=8, r_max=min(K // 2, 64),
+                              reinverse_period=20, seed=77) for _, K in SERVING["classes"]]
+    srv = serving.BeamServer([(N, K, counts[c], rules[c])
+                              for c, (N, K) in enumerate(SERVING["classes"])],
+                             device=dev, budget_bytes=int(200e9))
+    for s_ in range(n_states):
+        sc = store[cls_of[s_]][0]
+        assert srv.admit(s_, cls_of[s_], sc.alpha, sc.sigma2)
+    nxt = [0] * n_states
+
+    def request(s_):
+        r = serving.Request(s_, store[cls_of[s_]][1][local_idx[s_], nxt[s_]])
+        nxt[s_] += 1
+        return r
+
+    for s_ in range(n_states):                          # warm-up: every state's full inverse
+        srv.submit(request(s_))
+    srv.drain()
+    for s_ in range(n_states):                          # and one update each
+        srv.submit(request(s_))
+    srv.drain()
+    srv.completed.clear()
+    launches0 = sum(c.handle.launches for c in srv.classes)
+    clock = ClockSampler(local)
+    clock.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(sched) or any(c.pending or c.inflight for c in srv.classes):
+        now = time.perf_counter() - t0
+        while i < len(sched) and sched[i][0] <= now:
+            r = request(sched[i][1])
+            r.arrival = t0 + sched[i][0]
+            srv.submit(r)
+            i += 1
+        srv.pump()
+    t_end = time.perf_counter()
+    clk = clock.stop()
+    done = srv.completed
+    p50, p99 = srv.latency_ms()
+    value = len(done) / (t_end - t0)
+    launches = sum(c.handle.launches for c in srv.classes) - launches0
+    peaks = measured_peaks()
+    abytes = sum(algorithmic_bytes_per_update(srv.classes[cls_of[r.state]].N,
+                                              srv.classes[cls_of[r.state]].K, "wb")
+                 for r in done)
+    achieved = abytes / (t_end - t0) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": 2, "ms_per_step": 1e3 * (t_end - t0) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": SERVING["desc"], "states": n_states, "eta": args.eta or 0.65,
+                       "offered_req_per_s": rate, "duration_s": duration,
+                       "requests": len(sched), "classes": [
+                           {"N": c.N, "K": c.K, "states": c.capacity, "launches": c.launches,
+                            "engine": c.handle.last_engine} for c in srv.classes],
+                       "hbm_admitted_bytes": srv.used_bytes,
+                       "l2": "not flushed (open-loop serving run)"},
+            "p50_ms": p50, "p99_ms": p99,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "peak_source": peaks["source"], "kernel": "all serving launches"},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    srv.close()
+
+
+def collections_counter(it):
+    import collections
+    return collections.Counter(it)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -466,6 +577,9 @@ def main():
         return
     if args.workload == "uneven_4096":
         main_uneven(args)
+        return
+    if args.workload == "serving_2000":
+        main_serving(args)
         return
     import numpy as np
     import torch

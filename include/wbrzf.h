@@ -224,6 +224,13 @@ wbrzf_status wbrzf_set_trace(wbrzf* h, void* trace, size_t bytes);
  * not depend on its position in a batch.  Default: ids[b] = b.  Synchronises the stream. */
 wbrzf_status wbrzf_set_instance_ids(wbrzf* h, const uint32_t* ids, int count);
 
+/* Replace alpha, sigma^2 and / or the identity of instances first .. first+count-1 (host
+ * arrays of `count` entries; a NULL array leaves that parameter unchanged; same ranges as
+ * wbrzf_create and wbrzf_set_instance_ids).  For reusing an instance slot for another beam
+ * state; follow with a full inverse of that instance.  Synchronises the stream. */
+wbrzf_status wbrzf_set_instance_params(wbrzf* h, int first, int count, const double* alpha,
+                                       const double* sigma2, const uint32_t* ids);
+
 /* Choose the kernel (WBRZF_ENGINE_*).  An engine whose conditions the handle does not meet
  * returns WBRZF_ERR_UNSUPPORTED; WBRZF_ENGINE_BLOCKED on a handle created with less workspace
  * than wbrzf_workspace_bytes_engine(..., WBRZF_ENGINE_BLOCKED) (either blocked variant)

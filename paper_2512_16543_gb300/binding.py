@@ -94,6 +94,9 @@ def lib() -> ctypes.CDLL:
         f = getattr(L, name)
         f.restype = i32
         f.argtypes = [vp, vp, vp, vp]
+    L.wbrzf_set_instance_params.restype = i32
+    L.wbrzf_set_instance_params.argtypes = [vp, i32, i32, ctypes.POINTER(dbl),
+                                            ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_uint32)]
     L.wbrzf_set_graph.restype = i32
     L.wbrzf_set_graph.argtypes = [vp, i32]
     L.wbrzf_group_create.restype = i32
@@ -253,6 +256,30 @@ class WBRZF:
         buf = (ctypes.c_int * self.batch)()
         _check(lib().wbrzf_get_steps(self._h, buf, self.batch), "wbrzf_get_steps")
         return list(buf)
+
+    def set_instance_params(self, first: int, alpha=None, sigma2=None, instance_id=None):
+        """Set alpha / sigma^2 / identity of instance `first` (scalars) or of instances
+        first.. (sequences); None leaves a parameter unchanged."""
+        def arr(x, ct):
+            if x is None:
+                return None, 0
+            xs = list(x) if hasattr(x, "__len__") else [x]
+            return (ct * len(xs))(*xs), len(xs)
+        a, na = arr(alpha, ctypes.c_double)
+        sg, ns = arr(sigma2, ctypes.c_double)
+        ids, ni = arr(instance_id, ctypes.c_uint32)
+        n = max(na, ns, ni)
+        if any(k not in (0, n) for k in (na, ns, ni)):
+            raise ValueError("alpha, sigma2 and instance_id need the same length")
+        _check(lib().wbrzf_set_instance_params(self._h, int(first), n, a, sg, ids),
+               "wbrzf_set_instance_params")
+
+    def sum_rate_into(self, rate: torch.Tensor, sinr: torch.Tensor | None = None) -> None:
+        """Write the last step's per-instance sum-rate (and SINR) into given device tensors."""
+        if rate.dtype != torch.float32 or rate.numel() != self.batch or not rate.is_contiguous():
+            raise ValueError("rate must be a contiguous float32 tensor of batch entries")
+        _check(lib().wbrzf_sum_rate(self._h, None if sinr is None else _ptr(sinr), _ptr(rate)),
+               "wbrzf_sum_rate")
 
     def sum_rate(self) -> tuple[torch.Tensor, torch.Tensor]:
         sinr = torch.empty(self.batch, self.K, dtype=torch.float32, device=self.device)

@@ -581,6 +581,42 @@ wbrzf_status wbrzf_set_instance_ids(wbrzf* h, const uint32_t* ids, int count) {
   return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
 }
 
+wbrzf_status wbrzf_set_instance_params(wbrzf* h, int first, int count, const double* alpha,
+                                       const double* sigma2, const uint32_t* ids) {
+  if (!h || first < 0 || count < 0 || first + count > h->batch) return WBRZF_ERR_INVALID_ARG;
+  if (count == 0) return WBRZF_OK;
+  for (int i = 0; i < count; ++i) {
+    if (alpha && (!(alpha[i] >= 0.0) || !isfinite(alpha[i]))) return WBRZF_ERR_INVALID_ARG;
+    if (sigma2 && (!(sigma2[i] > 0.0) || !isfinite(sigma2[i]))) return WBRZF_ERR_INVALID_ARG;
+    if (ids && ids[i] >= (1u << 28)) return WBRZF_ERR_INVALID_ARG;
+  }
+  const size_t rb = re_bytes(h->prec);
+  unsigned char* host = static_cast<unsigned char*>(malloc(2 * (size_t)count * rb));
+  if (!host) return WBRZF_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (h->prec == WBRZF_C128) {
+      if (alpha) reinterpret_cast<double*>(host)[i] = alpha[i];
+      if (sigma2) reinterpret_cast<double*>(host)[count + i] = sigma2[i];
+    } else {
+      if (alpha) reinterpret_cast<float*>(host)[i] = (float)alpha[i];
+      if (sigma2) reinterpret_cast<float*>(host)[count + i] = (float)sigma2[i];
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (alpha)
+    e = cudaMemcpyAsync(h->ws + h->wl.oAlpha + (size_t)first * rb, host, (size_t)count * rb,
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && sigma2)
+    e = cudaMemcpyAsync(h->ws + h->wl.oSigma2 + (size_t)first * rb, host + (size_t)count * rb,
+                        (size_t)count * rb, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && ids)
+    e = cudaMemcpyAsync(h->ws + h->wl.oIds + (size_t)first * sizeof(uint32_t), ids,
+                        (size_t)count * sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  free(host);
+  return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
+}
+
 wbrzf_status wbrzf_set_engine(wbrzf* h, int engine) {
   if (!h || engine < WBRZF_ENGINE_AUTO || engine > WBRZF_ENGINE_BLOCKED_FMA)
     return WBRZF_ERR_INVALID_ARG;

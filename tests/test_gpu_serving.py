@@ -1,0 +1,95 @@
+"""Continuous-batching server: results alone and in the mix, admission by HBM footprint."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_harness import relerr, run_oracle
+from paper_2512_16543_gb300 import binding, channel, serving
+from test_gpu_parity import tf32_w_bound
+
+pytestmark = pytest.mark.gpu
+
+CLASSES = [(256, 32), (512, 64)]                 # (N, K): 16x16 and 32x16 UPA
+ARR = {256: (16, 16), 512: (32, 16)}
+
+
+def _states(n_per_class, T, seed):
+    """Per state: class, scenario, snapshots [T, K, N] (complex64, device)."""
+    out = []
+    for ci, (N, K) in enumerate(CLASSES):
+        sc = channel.LeoScenario(n_x=ARR[N][0], n_y=ARR[N][1], K=K)
+        p = channel.draw_trajectories(sc, n_per_class, seed=seed + ci)
+        Hs = channel.trajectory(p, T, dtype=torch.complex64).cuda()
+        for j in range(n_per_class):
+            out.append((ci, sc, Hs[:, j].contiguous()))
+    return out
+
+
+def _serve(states, order, rule, bursts):
+    """Submit the requests of `order` (state ids) in bursts of the given sizes, pumping
+    between bursts, so that requests join launches already in flight."""
+    srv = serving.BeamServer([(N, K, 8) for N, K in CLASSES], rule, keep_results=True)
+    for sid in sorted(set(order)):
+        ci, sc, _ = states[sid]
+        assert srv.admit(sid, ci, sc.alpha, sc.sigma2)
+    nxt = {sid: 0 for sid in set(order)}
+    reqs, i = [], 0
+    for b in bursts:
+        for sid in order[i:i + b]:
+            r = serving.Request(sid, states[sid][2][nxt[sid]])
+            nxt[sid] += 1
+            srv.submit(r)
+            reqs.append(r)
+        i += b
+        srv.pump()
+    srv.drain()
+    srv.close()
+    return reqs, srv
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix():
+    rule = binding.RankRule(eta=0.9, k_init=2, p=4, r_max=16, reinverse_period=5, seed=13)
+    states = _states(4, 9, seed=300)
+    g = torch.Generator().manual_seed(5)
+    order = []
+    for _ in range(6):                       # every state 6 requests, interleaved at random
+        order += torch.randperm(len(states), generator=g).tolist()
+    bursts = [3, 1, 5, 2, 7, 4, 6, 3, 5, 2, 4, 6]
+    mix, srv = _serve(states, order, rule, bursts)
+    assert all(r.done is not None for r in mix)
+    assert srv.classes[0].launches > 2 and srv.classes[1].launches > 2
+    for sid in (0, 3, 5, 7):
+        alone, _ = _serve(states, [sid] * 6, rule, [1] * 6)
+        mine = [r for r in mix if r.state == sid]
+        assert len(mine) == len(alone) == 6
+        for a, m in zip(alone, mine):
+            assert torch.equal(a.W, m.W), sid
+            assert a.sum_rate == m.sum_rate
+    # and one state against the FP64 oracle (its first request is the full inverse)
+    ci, sc, Hs = states[1]
+    mine = [r for r in mix if r.state == 1]
+    Hn = Hs[:6].cpu().numpy().astype(np.complex128)
+    ref = run_oracle(Hn, sc.alpha, sc.sigma2, sc.p_t, rule, instance=1)
+    for t, r in enumerate(mine):
+        tol = max(2e-3, 2 * tf32_w_bound(Hn[t], ref[t].X))
+        assert relerr(r.W.cpu().numpy(), ref[t].W) < tol
+        assert abs(r.sum_rate - ref[t].sum_rate) < 1e-3
+
+
+def test_admission_respects_the_hbm_budget():
+    rule = binding.RankRule(eta=0.9, k_init=2, p=4, r_max=16, seed=1)
+    probe = serving.BeamServer([(256, 32, 8)], rule)
+    per = probe.classes[0].per_state_bytes
+    probe.close()
+    srv = serving.BeamServer([(256, 32, 8)], rule, budget_bytes=3 * per + per // 2)
+    sc = channel.scenario_batched_256x32()
+    ok = [srv.admit(s, 0, sc.alpha, sc.sigma2) for s in range(5)]
+    assert ok == [True, True, True, False, False]
+    H = channel.channel_at(channel.draw_trajectories(sc, 1, seed=2), 0,
+                           dtype=torch.complex64, device="cuda")[0]
+    assert not srv.submit(serving.Request(4, H))
+    assert srv.rejected == 1
+    srv.retire(1)
+    assert srv.admit(4, 0, sc.alpha, sc.sigma2)
+    assert srv.used_bytes <= 3 * per + per // 2
+    srv.close()
