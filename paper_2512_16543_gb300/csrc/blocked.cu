@@ -392,14 +392,8 @@ __device__ T block_sum_n(T v, T* red) {
 }
 
 // Cyclic Jacobi eigendecomposition of E (d x d Hermitian, ld dmax): eigenvalues to lam,
-// eigenvectors (columns) to Uh.  Each round rotates the disjoint pairs of the round-robin
-// ordering at once, E <- J^H E J with J the product of the pairs' plane rotations.  Because
-// the pairs are disjoint, every 2 x 2 block (rows of pair k, columns of pair l) of J^H E J
-// depends only on the same block of E and the two rotations, so one phase updates all blocks
-// (and U <- U J) after one phase that computes the rotations: two barriers per round.  The
-// rotation of a pair zeroes its off-diagonal entry: with E_pq = |E_pq| e^{i phi},
-// tan(2 theta) = 2 |E_pq| / (E_qq - E_pp), t = tan(theta) the smaller root, c = 1/sqrt(1+t^2),
-// s = t c, and columns p, q of J are (c, -s e^{-i phi}) and (s, c e^{-i phi}).
+// eigenvectors (columns) to Uh, one CTA of NT threads per instance; each round is
+// jacobi_round (all pairs' rotations, then every 2 x 2 block of J^H E J and U J: two barriers).
 template <int NT, class T>
 __global__ void __launch_bounds__(NT) jacobi_kernel(const Bufs<T> w, int d) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -420,7 +414,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const Bufs<T> w, int d) {
     U[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
   }
   __syncthreads();
-  const int dd = d + (d & 1), npairs = dd >> 1, dm1 = dd - 1;
+  const int dm1 = d + (d & 1) - 1;
   const T eps = (sizeof(T) == 4) ? T(1e-10) : T(1e-26);
   for (int sweep = 0; sweep < ((sizeof(T) == 4) ? 12 : 20); ++sweep) {
     T off = 0, tot = 0;
@@ -433,93 +427,8 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const Bufs<T> w, int d) {
     off = block_sum_n<NT>(off, red);
     tot = block_sum_n<NT>(tot, red);
     if (!(off > eps * tot)) break;
-    for (int rnd = 0; rnd < dm1; ++rnd) {
-      // phase 1: the rotation of every pair (circle method: x_i = 1 + ((i + rnd) mod (dd-1));
-      // pairs (0, x_0), (x_k, x_{dd-1-k}))
-      for (int k = tid; k < npairs; k += NT) {
-        int p0, q0;
-        if (k == 0) { p0 = 0; q0 = 1 + rnd; }
-        else {
-          int a1 = k + rnd, a2 = dm1 - k + rnd;
-          if (a1 >= dm1) a1 -= dm1;
-          if (a2 >= dm1) a2 -= dm1;
-          p0 = 1 + a1;
-          q0 = 1 + a2;
-        }
-        const int p1 = min(p0, q0), q1 = max(p0, q0);
-        bool act = false;
-        T c = 1, sn = 0;
-        cx<T> f = cmk<T>(1, 0);
-        if (q1 < d) {
-          const cx<T> bpq = E[p1 * dmax + q1];
-          const T ab = hypot(bpq.re, bpq.im);
-          if (ab > T(0)) {
-            const T inv = T(1) / ab;
-            f = cmk(bpq.re * inv, -bpq.im * inv);
-            const T tau = (E[q1 * dmax + q1].re - E[p1 * dmax + p1].re) * (T(0.5) * inv);
-            const T t = copysign(T(1), tau) / (fabs(tau) + sqrt(T(1) + tau * tau));
-            c = T(1) / sqrt(T(1) + t * t);
-            sn = t * c;
-            act = true;
-          }
-        }
-        pp[k] = act ? p1 : -1 - p1;       // inactive: -1 - p (p still needed as a row/column)
-        pq[k] = q1;
-        rc[k] = c;
-        rs[k] = sn;
-        ph[k] = f;
-      }
-      __syncthreads();
-      // phase 2a: E's 2 x 2 blocks (rows of pair k, columns of pair l) <- J_k^H block J_l
-      for (int e = tid; e < npairs * npairs; e += NT) {
-        const int k = e / npairs, l = e - k * npairs;
-        const int pk = pp[k], pl = pp[l];
-        if (pk < 0 && pl < 0) continue;                 // both identity: block unchanged
-        const int rp = pk < 0 ? -1 - pk : pk, rq = pq[k];
-        const int cp = pl < 0 ? -1 - pl : pl, cq = pq[l];
-        const bool rq_ok = rq < d, cq_ok = cq < d;
-        cx<T> a00 = E[rp * dmax + cp];
-        cx<T> a01 = cq_ok ? E[rp * dmax + cq] : cmk<T>(0, 0);
-        cx<T> a10 = rq_ok ? E[rq * dmax + cp] : cmk<T>(0, 0);
-        cx<T> a11 = (rq_ok && cq_ok) ? E[rq * dmax + cq] : cmk<T>(0, 0);
-        if (pl >= 0) {          // columns: col_p <- c col_p - s f col_q; col_q <- s col_p + c f col_q
-          const T c = rc[l], sn = rs[l];
-          const cx<T> f = ph[l];
-          const cx<T> q0 = cmul(f, a01), q1v = cmul(f, a11);
-          const cx<T> n00 = csub(cscale(a00, c), cscale(q0, sn));
-          const cx<T> n01 = cadd(cscale(a00, sn), cscale(q0, c));
-          const cx<T> n10 = csub(cscale(a10, c), cscale(q1v, sn));
-          const cx<T> n11 = cadd(cscale(a10, sn), cscale(q1v, c));
-          a00 = n00; a01 = n01; a10 = n10; a11 = n11;
-        }
-        if (pk >= 0) {          // rows: row_p <- c row_p - s conj(f) row_q; row_q <- s row_p + c conj(f) row_q
-          const T c = rc[k], sn = rs[k];
-          const cx<T> fc = cconj(ph[k]);
-          const cx<T> q0 = cmul(fc, a10), q1v = cmul(fc, a11);
-          const cx<T> n00 = csub(cscale(a00, c), cscale(q0, sn));
-          const cx<T> n10 = cadd(cscale(a00, sn), cscale(q0, c));
-          const cx<T> n01 = csub(cscale(a01, c), cscale(q1v, sn));
-          const cx<T> n11 = cadd(cscale(a01, sn), cscale(q1v, c));
-          a00 = n00; a01 = n01; a10 = n10; a11 = n11;
-        }
-        E[rp * dmax + cp] = a00;
-        if (cq_ok) E[rp * dmax + cq] = a01;
-        if (rq_ok) E[rq * dmax + cp] = a10;
-        if (rq_ok && cq_ok) E[rq * dmax + cq] = a11;
-      }
-      // phase 2b: U <- U J (columns of the active pairs)
-      for (int e = tid; e < npairs * d; e += NT) {
-        const int l = e / d, i = e - l * d;
-        const int pl = pp[l];
-        if (pl < 0) continue;
-        const int ql = pq[l];
-        const T c = rc[l], sn = rs[l];
-        const cx<T> up = U[i * dmax + pl], uq = cmul(ph[l], U[i * dmax + ql]);
-        U[i * dmax + pl] = csub(cscale(up, c), cscale(uq, sn));
-        U[i * dmax + ql] = cadd(cscale(up, sn), cscale(uq, c));
-      }
-      __syncthreads();
-    }
+    for (int rnd = 0; rnd < dm1; ++rnd)
+      jacobi_round<T, NT>(E, U, dmax, d, rnd, pp, pq, rc, rs, ph);
   }
   cx<T>* Ug = w.Uh + (size_t)b * w.L.sGy;
   for (int e = tid; e < d * d; e += NT) {

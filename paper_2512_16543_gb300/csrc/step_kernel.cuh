@@ -221,6 +221,128 @@ __device__ __forceinline__ void prefetch_state(const StepArgs<T>& a, int b, cx<T
   cp_async_commit();
 }
 
+// ------------------------------------------------------------------ Jacobi rounds
+// Plane rotation that zeroes E_pq of a Hermitian E: with E_pq = |E_pq| e^{i phi},
+// tan(2 theta) = 2 |E_pq| / (E_qq - E_pp), t = tan(theta) the smaller root, c = 1/sqrt(1+t^2),
+// s = t c; columns p, q of J are (c, -s f) and (s, c f) with f = e^{-i phi}.  Returns false
+// (identity) when E_pq is zero.  Single precision uses the hardware reciprocal square root:
+// dG is scaled to unit norm, so |E_pq|^2 below 1e-30 is negligible and dropped instead of
+// being squared into the denormal range.
+template <class T>
+__device__ __forceinline__ bool jacobi_rotation(cx<T> bpq, T epp, T eqq, T& c, T& s,
+                                                cx<T>& f);
+template <>
+__device__ __forceinline__ bool jacobi_rotation<float>(cx<float> bpq, float epp, float eqq,
+                                                       float& c, float& s, cx<float>& f) {
+  const float a2 = fmaf(bpq.re, bpq.re, bpq.im * bpq.im);
+  if (!(a2 > 1e-30f)) return false;
+  const float inv = rsqrtf(a2);
+  f = cmk(bpq.re * inv, -bpq.im * inv);
+  const float tau = (eqq - epp) * (0.5f * inv);
+  const float t = __fdividef(copysignf(1.f, tau), fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+  c = rsqrtf(fmaf(t, t, 1.f));
+  s = t * c;
+  return true;
+}
+template <>
+__device__ __forceinline__ bool jacobi_rotation<double>(cx<double> bpq, double epp, double eqq,
+                                                        double& c, double& s, cx<double>& f) {
+  const double ab = hypot(bpq.re, bpq.im);       // no squaring: unit-modulus phase
+  if (!(ab > 0.0)) return false;
+  const double inv = 1.0 / ab;
+  f = cmk(bpq.re * inv, -bpq.im * inv);
+  const double tau = (eqq - epp) * (0.5 * inv);
+  const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
+  return true;
+}
+
+// One round of the parallel cyclic Jacobi method on E (d x d, ld dmax) with eigenvector
+// accumulation U <- U J, by the NT threads of a CTA.  The round rotates the disjoint pairs of
+// the round-robin ordering (x_i = 1 + ((i + rnd) mod (dd - 1)); pairs (0, x_0) and
+// (x_k, x_{dd-1-k}), dd = d rounded up to even) at once: phase 1 computes the rotations; as
+// the pairs are disjoint, every 2 x 2 block (rows of pair k, columns of pair l) of J^H E J
+// depends only on the same block of E and the two rotations, so phase 2 updates all blocks
+// and U's columns.  pp, pq, rc, rs, ph: npairs-entry scratch.  Ends with a barrier.
+template <class T, int NT>
+__device__ void jacobi_round(cx<T>* E, cx<T>* U, int dmax, int d, int rnd, int* pp, int* pq,
+                             T* rc, T* rs, cx<T>* ph) {
+  const int tid = threadIdx.x;
+  const int dd = d + (d & 1), npairs = dd >> 1, dm1 = dd - 1;
+  for (int k = tid; k < npairs; k += NT) {
+    int p0, q0;
+    if (k == 0) { p0 = 0; q0 = 1 + rnd; }
+    else {
+      int a1 = k + rnd, a2 = dm1 - k + rnd;
+      if (a1 >= dm1) a1 -= dm1;
+      if (a2 >= dm1) a2 -= dm1;
+      p0 = 1 + a1;
+      q0 = 1 + a2;
+    }
+    const int p1 = min(p0, q0), q1 = max(p0, q0);
+    T c = 1, sn = 0;
+    cx<T> f = cmk<T>(1, 0);
+    const bool act = q1 < d && jacobi_rotation<T>(E[p1 * dmax + q1], E[p1 * dmax + p1].re,
+                                                   E[q1 * dmax + q1].re, c, sn, f);
+    pp[k] = act ? p1 : -1 - p1;        // inactive: -1 - p (p is still a row / column)
+    pq[k] = q1;
+    rc[k] = c;
+    rs[k] = sn;
+    ph[k] = f;
+  }
+  __syncthreads();
+  const int nb = npairs * npairs;
+  for (int e = tid; e < nb + npairs * d; e += NT) {
+    if (e < nb) {
+      const int k = e / npairs, l = e - k * npairs;
+      const int pk = pp[k], pl = pp[l];
+      if (pk < 0 && pl < 0) continue;                 // both identity: block unchanged
+      const int rp = pk < 0 ? -1 - pk : pk, rq = pq[k];
+      const int cp = pl < 0 ? -1 - pl : pl, cq = pq[l];
+      const bool rq_ok = rq < d, cq_ok = cq < d;
+      cx<T> a00 = E[rp * dmax + cp];
+      cx<T> a01 = cq_ok ? E[rp * dmax + cq] : cmk<T>(0, 0);
+      cx<T> a10 = rq_ok ? E[rq * dmax + cp] : cmk<T>(0, 0);
+      cx<T> a11 = (rq_ok && cq_ok) ? E[rq * dmax + cq] : cmk<T>(0, 0);
+      if (pl >= 0) {        // columns: col_p <- c col_p - s f col_q; col_q <- s col_p + c f col_q
+        const T c = rc[l], sn = rs[l];
+        const cx<T> f = ph[l];
+        const cx<T> q0 = cmul(f, a01), q1v = cmul(f, a11);
+        const cx<T> n00 = csub(cscale(a00, c), cscale(q0, sn));
+        const cx<T> n01 = cadd(cscale(a00, sn), cscale(q0, c));
+        const cx<T> n10 = csub(cscale(a10, c), cscale(q1v, sn));
+        const cx<T> n11 = cadd(cscale(a10, sn), cscale(q1v, c));
+        a00 = n00; a01 = n01; a10 = n10; a11 = n11;
+      }
+      if (pk >= 0) {        // rows: row_p <- c row_p - s conj(f) row_q; row_q <- s row_p + c conj(f) row_q
+        const T c = rc[k], sn = rs[k];
+        const cx<T> fc = cconj(ph[k]);
+        const cx<T> q0 = cmul(fc, a10), q1v = cmul(fc, a11);
+        const cx<T> n00 = csub(cscale(a00, c), cscale(q0, sn));
+        const cx<T> n10 = cadd(cscale(a00, sn), cscale(q0, c));
+        const cx<T> n01 = csub(cscale(a01, c), cscale(q1v, sn));
+        const cx<T> n11 = cadd(cscale(a01, sn), cscale(q1v, c));
+        a00 = n00; a01 = n01; a10 = n10; a11 = n11;
+      }
+      E[rp * dmax + cp] = a00;
+      if (cq_ok) E[rp * dmax + cq] = a01;
+      if (rq_ok) E[rq * dmax + cp] = a10;
+      if (rq_ok && cq_ok) E[rq * dmax + cq] = a11;
+    } else {              // U <- U J on the columns of an active pair
+      const int e2 = e - nb, l = e2 / d, i = e2 - l * d;
+      const int pl = pp[l];
+      if (pl < 0) continue;
+      const int ql = pq[l];
+      const T c = rc[l], sn = rs[l];
+      const cx<T> up = U[i * dmax + pl], uq = cmul(ph[l], U[i * dmax + ql]);
+      U[i * dmax + pl] = csub(cscale(up, c), cscale(uq, sn));
+      U[i * dmax + ql] = cadd(cscale(up, sn), cscale(uq, c));
+    }
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------------ phases 2-6
 // Given G_t in w.G (Hermitian, alpha on the diagonal), run the perturbation, the low-rank
 // step, the Woodbury update or direct inverse, the state write-back, the power scale and the
@@ -392,137 +514,27 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
         Uh[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
       }
       __syncthreads();
-      if (tid < 32) {   // one warp: rounds synchronise with __syncwarp only
-        const int lane = tid;
-        const int dd = d + (d & 1);
-        const int npairs = dd >> 1, dm1 = dd - 1;
-        const int nit = npairs * d;                  // work items (pair k, row or column)
-        const uint32_t magic = (1u << 20) / (uint32_t)d + 1u;   // e / d for e < 1024
-        const int max_sweeps = (sizeof(T) == 4) ? 12 : 20;
+      {
         // converged when the off-diagonal energy is below eps of the total: 1e-10 keeps FP32
         // rotations above the rounding floor of a d x d sweep (about (d u)^2)
+        const int dm1 = d + (d & 1) - 1;
+        const int max_sweeps = (sizeof(T) == 4) ? 12 : 20;
         const T eps = (sizeof(T) == 4) ? T(1e-10) : T(1e-26);
         for (int sweep = 0; sweep < max_sweeps; ++sweep) {
           T off = 0, tot = 0;
-          if (lane < d) {
-            for (int i = 0; i < d; ++i) {
-              const T v = cabs2(Gy[i * dmax + lane]);
-              tot += v;
-              if (i != lane) off += v;
-            }
+          for (int e = tid; e < d * d; e += kThreads) {
+            const int i = e / d, j = e - i * d;
+            const T v = cabs2(Gy[i * dmax + j]);
+            tot += v;
+            if (i != j) off += v;
           }
-          off = warp_sum(off);
-          tot = warp_sum(tot);
+          off = block_sum(off, red);
+          tot = block_sum(tot, red);
           if (!(off > eps * tot)) break;
-          for (int rnd = 0; rnd < dm1; ++rnd) {
-            // rotation of pair `lane` (circle method: x_i = 1 + ((i + rnd) mod (dd - 1));
-            // pairs (0, x_0), (x_k, x_{dd-1-k}))
-            int p1 = 0, q1 = 0;
-            T c = 1, s = 0;
-            cx<T> ph = cmk<T>(1, 0);
-            bool act = false;
-            if (lane < npairs) {
-              int a1 = lane + rnd, a2 = dm1 - lane + rnd;
-              if (a1 >= dm1) a1 -= dm1;
-              if (a2 >= dm1) a2 -= dm1;
-              const int p0 = lane == 0 ? 0 : 1 + a1;
-              const int q0 = lane == 0 ? 1 + (rnd < dm1 ? rnd : rnd - dm1) : 1 + a2;
-              p1 = min(p0, q0);
-              q1 = max(p0, q0);
-              if (q1 < d) {
-                const cx<T> bpq = Gy[p1 * dmax + q1];
-                const T ab = hypot(bpq.re, bpq.im);     // no squaring: unit-modulus phase
-                if (ab > T(0)) {
-                  const T inv = T(1) / ab;
-                  ph = cmk(bpq.re * inv, -bpq.im * inv);             // e^{-i phi}
-                  // tan(2 theta) = 2|E_pq| / (E_qq - E_pp); smaller root t = tan(theta)
-                  const T tau = (Gy[q1 * dmax + q1].re - Gy[p1 * dmax + p1].re) * (T(0.5) * inv);
-                  const T t = copysign(T(1), tau) / (fabs(tau) + sqrt(T(1) + tau * tau));
-                  c = T(1) / sqrt(T(1) + t * t);
-                  s = t * c;
-                  act = true;
-                }
-              }
-            }
-            // columns (E and U_hat): col_p <- c col_p - s ph col_q ; col_q <- s col_p + c ph col_q
-            for (int base = 0; base < nit; base += 64) {
-              int kk[2], ii[2];
-              T cc[2], ss[2];
-              cx<T> pp2[2], ep[2], eq[2], up[2], uq[2];
-              bool ok[2];
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                const int e = base + lane + 32 * u;
-                const int k = (int)(((uint32_t)e * magic) >> 20);
-                const int src = k < 32 ? k : 0;
-                const int pk = __shfl_sync(0xffffffffu, p1, src);
-                const int qk = __shfl_sync(0xffffffffu, q1, src);
-                const bool ak = __shfl_sync(0xffffffffu, act ? 1 : 0, src) != 0;
-                cc[u] = __shfl_sync(0xffffffffu, c, src);
-                ss[u] = __shfl_sync(0xffffffffu, s, src);
-                pp2[u] = cmk<T>(__shfl_sync(0xffffffffu, ph.re, src), __shfl_sync(0xffffffffu, ph.im, src));
-                ok[u] = e < nit && ak;
-                kk[u] = pk;
-                ii[u] = qk;
-                if (ok[u]) {
-                  const int i = e - k * d;
-                  ep[u] = Gy[i * dmax + pk]; eq[u] = Gy[i * dmax + qk];
-                  up[u] = Uh[i * dmax + pk]; uq[u] = Uh[i * dmax + qk];
-                }
-              }
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                if (!ok[u]) continue;
-                const int e = base + lane + 32 * u;
-                const int k = (int)(((uint32_t)e * magic) >> 20), i = e - k * d;
-                const cx<T> q1v = cmul(pp2[u], eq[u]), q2v = cmul(pp2[u], uq[u]);
-                Gy[i * dmax + kk[u]] = csub(cscale(ep[u], cc[u]), cscale(q1v, ss[u]));
-                Gy[i * dmax + ii[u]] = cadd(cscale(ep[u], ss[u]), cscale(q1v, cc[u]));
-                Uh[i * dmax + kk[u]] = csub(cscale(up[u], cc[u]), cscale(q2v, ss[u]));
-                Uh[i * dmax + ii[u]] = cadd(cscale(up[u], ss[u]), cscale(q2v, cc[u]));
-              }
-            }
-            __syncwarp();
-            // rows: row_p <- c row_p - s conj(ph) row_q ; row_q <- s row_p + c conj(ph) row_q
-            for (int base = 0; base < nit; base += 64) {
-              int kk[2], ii[2];
-              T cc[2], ss[2];
-              cx<T> pp2[2], ep[2], eq[2];
-              bool ok[2];
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                const int e = base + lane + 32 * u;
-                const int k = (int)(((uint32_t)e * magic) >> 20);
-                const int src = k < 32 ? k : 0;
-                const int pk = __shfl_sync(0xffffffffu, p1, src);
-                const int qk = __shfl_sync(0xffffffffu, q1, src);
-                const bool ak = __shfl_sync(0xffffffffu, act ? 1 : 0, src) != 0;
-                cc[u] = __shfl_sync(0xffffffffu, c, src);
-                ss[u] = __shfl_sync(0xffffffffu, s, src);
-                pp2[u] = cmk<T>(__shfl_sync(0xffffffffu, ph.re, src), -__shfl_sync(0xffffffffu, ph.im, src));
-                ok[u] = e < nit && ak;
-                kk[u] = pk;
-                ii[u] = qk;
-                if (ok[u]) {
-                  const int j2 = e - k * d;
-                  ep[u] = Gy[pk * dmax + j2]; eq[u] = Gy[qk * dmax + j2];
-                }
-              }
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                if (!ok[u]) continue;
-                const int e = base + lane + 32 * u;
-                const int k = (int)(((uint32_t)e * magic) >> 20), j2 = e - k * d;
-                const cx<T> q1v = cmul(pp2[u], eq[u]);
-                Gy[kk[u] * dmax + j2] = csub(cscale(ep[u], cc[u]), cscale(q1v, ss[u]));
-                Gy[ii[u] * dmax + j2] = cadd(cscale(ep[u], ss[u]), cscale(q1v, cc[u]));
-              }
-            }
-            __syncwarp();
-          }
+          for (int rnd = 0; rnd < dm1; ++rnd)
+            jacobi_round<T, kThreads>(Gy, Uh, dmax, d, rnd, pp, pq, rc, rs, rph);
         }
       }
-      __syncthreads();
       // 3f. sigma_hat^2 (eigenvalues, clamped at 0) sorted descending
       if (tid < d) lam[tid] = fmax(Gy[tid * dmax + tid].re, T(0));
       __syncthreads();
