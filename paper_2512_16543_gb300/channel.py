@@ -153,6 +153,59 @@ def channel_at(params: TrajectoryParams, t: int, *, device="cpu",
     return H.to(dtype).contiguous()
 
 
+def steering_at(params: TrajectoryParams, t: int, *, device="cpu") -> torch.Tensor:
+    """The array-manifold vectors a(theta_n(t), phi_n(t)) of eq. 3 (no gain, no NLOS part):
+    [B, K, N] complex128.  This is the geometric channel the satellite knows from positions
+    (Section II), the input of the digital precoder in the hybrid case."""
+    sc = params.scenario
+    user_xy = params.user_xy.to(device)
+    elem_xy = params.elem_xy.to(device)
+    x_sat = sc.v * sc.dt * float(t)
+    dx = user_xy[..., 0] - x_sat
+    dy = user_xy[..., 1]
+    dist = torch.sqrt(dx * dx + dy * dy + sc.h_alt * sc.h_alt)
+    k0 = 2.0 * math.pi / sc.wavelength
+    phase = k0 * ((dx / dist)[..., None] * elem_xy[:, 0] + (dy / dist)[..., None] * elem_xy[:, 1])
+    return torch.polar(torch.full_like(phase, 1.0 / math.sqrt(sc.N)), phase)
+
+
+def dft_codebook(scenario: LeoScenario, *, device="cpu") -> torch.Tensor:
+    """Orthonormal 2-D DFT codebook of the UPA (Section II eq. 4): column (p, q) steers to the
+    direction cosines (-1 + 2p / n_x, -1 + 2q / n_y) on the lambda/2 grid; [N, N] complex128,
+    column index p * n_y + q."""
+    nx, ny = scenario.n_x, scenario.n_y
+    mx = torch.arange(nx, dtype=torch.float64, device=device) - (nx - 1) / 2.0
+    my = torch.arange(ny, dtype=torch.float64, device=device) - (ny - 1) / 2.0
+    gy, gx = torch.meshgrid(my, mx, indexing="ij")          # element m = m_y * n_x + m_x
+    ux = -1.0 + 2.0 * torch.arange(nx, dtype=torch.float64, device=device) / nx
+    uy = -1.0 + 2.0 * torch.arange(ny, dtype=torch.float64, device=device) / ny
+    bx, by = torch.meshgrid(ux, uy, indexing="ij")           # beam (p, q)
+    phase = math.pi * (gx.reshape(-1, 1) * bx.reshape(1, -1) +
+                       gy.reshape(-1, 1) * by.reshape(1, -1))
+    return torch.polar(torch.full_like(phase, 1.0 / math.sqrt(nx * ny)), phase)
+
+
+def best_power_beams(steer: torch.Tensor, codebook: torch.Tensor) -> torch.Tensor:
+    """Per user the codebook column with the largest |a_n^H f|^2 (best-power selection of
+    Section II): steer [B, K, N], codebook [N, M] -> beam indices [B, K]."""
+    return torch.argmax((steer.conj() @ codebook).abs(), dim=-1)
+
+
+def hybrid_channels(params: TrajectoryParams, t: int, codebook: torch.Tensor, *, device="cpu",
+                    dtype: torch.dtype = torch.complex128):
+    """Hybrid beamforming at snapshot t with N_RF = K (one beam per user, best power):
+    returns (H_eff, H_true_eff, F_RF).  H_eff = A F_RF [B, K, K] is the geometric effective
+    channel the digital precoder is computed from (eq. 4, A = the steering vectors), in `dtype`;
+    H_true_eff = H F_RF [B, K, K] (complex128) is the Rician channel of eqs. 1-3 seen through the
+    same beams (for the sum-rate of eq. 15); F_RF [B, N, K] complex128."""
+    cb = codebook.to(device)
+    A = steering_at(params, t, device=device)
+    beams = best_power_beams(A.to(torch.complex64), cb.to(torch.complex64))
+    F = cb[:, beams].permute(1, 0, 2)                        # [B, N, K]
+    H = channel_at(params, t, device=device, dtype=torch.complex128)
+    return (A @ F).to(dtype).contiguous(), (H @ F).contiguous(), F
+
+
 def trajectory(params: TrajectoryParams, steps: int, *, t0: int = 0, device="cpu",
                dtype: torch.dtype = torch.complex128) -> torch.Tensor:
     """Stack H(t0), ..., H(t0+steps-1): tensor [steps, B, K, N]."""
@@ -230,3 +283,38 @@ def uneven_population(count: int, seed: int, *, n_choices=(256, 512, 1024),
                                        radius=rad[idx])
             out.append(UnevenClass(sc, idx, rad[idx], snr[idx], params))
     return out
+
+
+def scenario_paper_hybrid(K: int = 16, snr_db: float = 10.0) -> LeoScenario:
+    """Section VI / Table III: 18 GHz, 600 km, 16x16 UPA at lambda/2, N_RF = K <= 16 beams,
+    K_R = 10 dB, updates every 50 ms (users: draw_beam_users, one per beam cell).  The paper
+    gives no noise bandwidth, so P_t / sigma^2 is a parameter: 10 dB as in the other workloads;
+    about 30 dB is the order of Table III's link budget (P_t = 20 dBW, UT gain 39.7 dBi,
+    173 dB free-space loss, a few hundred MHz of noise) with the array gain inside
+    |a^H f|^2 <= 1."""
+    return LeoScenario(n_x=16, n_y=16, K=K, f_c=18e9, dt=50e-3, disc_radius=250e3,
+                       snr_db=snr_db)
+
+
+def draw_beam_users(scenario: LeoScenario, batch: int, seed: int,
+                    beams: tuple = (6, 7, 8, 9)) -> TrajectoryParams:
+    """Users for the hybrid case, one per DFT beam (Table III: one active user per beam): user
+    k of each trajectory is uniform inside the cell of beam (p_k, q_k), p, q over `beams` (the
+    cells of direction cosines (-1 + 2p / n_x +- 1 / n_x, ...) seen from the satellite at
+    t = 0), mapped to the ground; K must equal len(beams)^2.  LOS phases and NLOS fields are
+    drawn as in draw_trajectories."""
+    K, nx, ny = scenario.K, scenario.n_x, scenario.n_y
+    cells = [(p, q) for p in beams for q in beams]
+    if len(cells) != K:
+        raise ValueError("K must equal the number of beam cells")
+    base = draw_trajectories(scenario, batch, seed)
+    g = torch.Generator(device="cpu")
+    g.manual_seed(int(seed) + 7)
+    jit = torch.rand(batch, K, 2, generator=g, dtype=torch.float64) * 2.0 - 1.0
+    cu = torch.tensor([[-1.0 + 2.0 * p / nx, -1.0 + 2.0 * q / ny] for p, q in cells],
+                      dtype=torch.float64)
+    half = torch.tensor([1.0 / nx, 1.0 / ny], dtype=torch.float64)
+    u = cu + jit * half                                       # direction cosines [B, K, 2]
+    uz = torch.sqrt(1.0 - (u * u).sum(-1, keepdim=True))
+    user_xy = scenario.h_alt * u / uz                         # ground point seen at (ux, uy)
+    return TrajectoryParams(scenario, user_xy, base.psi, base.g_nlos)

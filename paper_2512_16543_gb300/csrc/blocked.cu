@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const Bufs<T> w, int d) {
   }
   __syncthreads();
   const int dm1 = d + (d & 1) - 1;
-  const T eps = (sizeof(T) == 4) ? T(1e-10) : T(1e-26);
+  const T eps = (sizeof(T) == 4) ? T(1e-8) : T(1e-26);
   for (int sweep = 0; sweep < ((sizeof(T) == 4) ? 12 : 20); ++sweep) {
     T off = 0, tot = 0;
     for (int e = tid; e < d * d; e += NT) {

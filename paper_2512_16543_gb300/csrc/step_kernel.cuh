@@ -515,11 +515,14 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       }
       __syncthreads();
       {
-        // converged when the off-diagonal energy is below eps of the total: 1e-10 keeps FP32
-        // rotations above the rounding floor of a d x d sweep (about (d u)^2)
+        // converged when the off-diagonal energy is below eps of the total.  FP32: 1e-8, an
+        // off-diagonal norm of 1e-4 of E's, which leaves the eigenvalues (the energy rule's
+        // input) exact to second order, about 1e-8, and turns the eigenvectors by about 1e-4
+        // -- a change of that relative size in the low-rank part of dG, far below the FP32
+        // rounding of X once scaled by ||dG|| / ||G|| ~ 1e-5.  FP64: 1e-26.
         const int dm1 = d + (d & 1) - 1;
         const int max_sweeps = (sizeof(T) == 4) ? 12 : 20;
-        const T eps = (sizeof(T) == 4) ? T(1e-10) : T(1e-26);
+        const T eps = (sizeof(T) == 4) ? T(1e-8) : T(1e-26);
         for (int sweep = 0; sweep < max_sweeps; ++sweep) {
           T off = 0, tot = 0;
           for (int e = tid; e < d * d; e += kThreads) {

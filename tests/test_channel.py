@@ -79,3 +79,18 @@ def test_uneven_population_is_seeded_and_spans_the_ranges():
         r = ca.params.user_xy.norm(dim=-1)
         assert bool((r <= ca.radius[:, None] + 1e-6).all())
         np.testing.assert_allclose(ca.alpha, [ca.scenario.K * s for s in ca.sigma2])
+
+
+def test_dft_codebook_and_beam_users():
+    sc = ch.scenario_paper_hybrid()
+    cb = ch.dft_codebook(sc)
+    np.testing.assert_allclose((cb.conj().T @ cb).numpy(), np.eye(sc.N), atol=1e-12)
+    p = ch.draw_beam_users(sc, 3, seed=8)
+    beams = ch.best_power_beams(ch.steering_at(p, 0), cb)
+    for b in range(3):                     # one user per beam cell at mid-pass
+        assert len(set(beams[b].tolist())) == sc.K
+    He, Ht, F = ch.hybrid_channels(p, 5, cb)
+    assert He.shape == (3, sc.K, sc.K) and Ht.dtype == torch.complex128
+    # H_eff is the steering part seen through the selected beams
+    A = ch.steering_at(p, 5)
+    np.testing.assert_allclose(He.numpy(), (A @ F).numpy(), atol=1e-12)
