@@ -264,6 +264,21 @@ long long wbrzf_launch_count(const wbrzf* h);
 void wbrzf_destroy(wbrzf* h);
 
 /*
+ * Precision modes of the blocked engine (WBRZF_ENGINE_BLOCKED / _BLOCKED_FMA only; a step on
+ * another engine with a mode set returns WBRZF_ERR_UNSUPPORTED).
+ *   bf16_products != 0 (complex64, WBRZF_ENGINE_BLOCKED): the precoder product H^H X takes
+ *     BF16 operands on the tensor cores (tcgen05 kind::f16, FP32 accumulation; unit roundoff
+ *     2^-9 per operand) instead of TF32.  The Gram matrix keeps its FP32-faithful split:
+ *     dG is 1e-5 .. 5e-5 of G, far below BF16 resolution.
+ *   refine_steps = 1: after the inverse update of every snapshot, one Newton step
+ *     X <- X (2 I - G_t X) with the FP32-faithful G_t (FP32 / FP64 FMA): it squares the
+ *     residual I - G_t X left by low-precision products and by the rank-r truncation (which
+ *     also moves X from the Woodbury iterate towards G_t^-1: not part of the paper's
+ *     method).  Costs two K^3 products per instance.
+ */
+wbrzf_status wbrzf_set_precision_mode(wbrzf* h, int bf16_products, int refine_steps);
+
+/*
  * CUDA-graph replay (not part of the paper's method).  With enable != 0 the next step is
  * captured into a CUDA graph on a stream the handle owns and replayed, fork/joined with the
  * handle's stream by events, for every later step with the same kind (full inverse or

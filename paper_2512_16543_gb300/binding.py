@@ -97,6 +97,8 @@ def lib() -> ctypes.CDLL:
     L.wbrzf_set_instance_params.restype = i32
     L.wbrzf_set_instance_params.argtypes = [vp, i32, i32, ctypes.POINTER(dbl),
                                             ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_uint32)]
+    L.wbrzf_set_precision_mode.restype = i32
+    L.wbrzf_set_precision_mode.argtypes = [vp, i32, i32]
     L.wbrzf_set_graph.restype = i32
     L.wbrzf_set_graph.argtypes = [vp, i32]
     L.wbrzf_group_create.restype = i32
@@ -246,6 +248,11 @@ class WBRZF:
         _check(lib().wbrzf_update_masked(self._h, _ptr(self._in(H)), _ptr(W),
                                          self._mask(active)), "wbrzf_update")
         return W
+
+    def set_precision_mode(self, bf16_products: bool = False, refine: int = 0) -> None:
+        """Blocked engine: BF16 precoder product and / or one Newton refinement of X."""
+        _check(lib().wbrzf_set_precision_mode(self._h, int(bf16_products), int(refine)),
+               "wbrzf_set_precision_mode")
 
     def set_graph(self, enable: bool = True) -> None:
         """Replay steps from a CUDA graph while H, W and the mask stay the same tensors."""
@@ -451,6 +458,11 @@ class WBRZFGroup:
     def update(self, Hs, Ws) -> None:
         Ha, Wa = self._arrays(Hs, Ws)
         _check(lib().wbrzf_group_update(self._g, Ha, Wa), "wbrzf_group_update")
+
+    def set_precision_mode(self, bf16_products: bool = False, refine: int = 0) -> None:
+        """Blocked engine: BF16 precoder product and / or one Newton refinement of X."""
+        _check(lib().wbrzf_set_precision_mode(self._h, int(bf16_products), int(refine)),
+               "wbrzf_set_precision_mode")
 
     def set_graph(self, enable: bool = True) -> None:
         _check(lib().wbrzf_group_set_graph(self._g, int(enable)), "wbrzf_group_set_graph")

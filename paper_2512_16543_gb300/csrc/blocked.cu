@@ -37,6 +37,7 @@ constexpr int kLiveMask = ~(1 << kInactive);
 template <class T>
 struct Bufs {
   cx<T>*D, *Om, *Q, *Gy, *Bm, *E, *Uh, *Ur, *Lm, *Tm, *Rh, *Z, *Cm, *CZ, *PC, *PR, *PU, *PV, *Pb;
+  cx<T>* S;
   T *lam, *rinv, *ws, *nu, *rows, *dsc;
   double *et, *nrm, *gpart;
   int *ctl, *perm, *drop;
@@ -53,6 +54,7 @@ Bufs<T> make_bufs(unsigned char* base, int batch, int N, int K, int dmax, int rc
   b.E = C(b.L.oE); b.Uh = C(b.L.oUh); b.Ur = C(b.L.oUr); b.Lm = C(b.L.oL); b.Tm = C(b.L.oT);
   b.Rh = C(b.L.oRh); b.Z = C(b.L.oZ); b.Cm = C(b.L.oCm); b.CZ = C(b.L.oCZ);
   b.PC = C(b.L.oPC); b.PR = C(b.L.oPR); b.PU = C(b.L.oPU); b.PV = C(b.L.oPV); b.Pb = C(b.L.oPb);
+  b.S = C(b.L.oS);
   b.lam = reinterpret_cast<T*>(base + b.L.oLam);
   b.rinv = reinterpret_cast<T*>(base + b.L.oRinv);
   b.ws = reinterpret_cast<T*>(base + b.L.oWs);
@@ -662,6 +664,23 @@ __global__ void fixup_kernel(const StepArgs<T> a, const Bufs<T> w, int p, int bs
   if (!inP) X[(size_t)(P0 + c) * K + i] = cscale(w.PV[(size_t)b * w.L.sPR + (size_t)c * K + i], T(-1));
 }
 
+// Refinement step X <- X (2 I - G X) (one Newton iteration for G^-1): D = -G X on entry, this
+// kernel adds 2 I; S = X D follows, then S is copied back into the resident X.
+template <class T>
+__global__ void add_two_diag_kernel(const StepArgs<T> a, const Bufs<T> w) {
+  const int b = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.K || !instance_active(a, b)) return;
+  w.D[(size_t)b * w.L.sD + (size_t)i * a.K + i].re += T(2);
+}
+
+template <class T>
+__global__ void copy_refined_kernel(const StepArgs<T> a, const Bufs<T> w) {
+  const int b = blockIdx.y;
+  if (!instance_active(a, b)) return;
+  const size_t KK = (size_t)a.K * a.K, idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < KK) a.Xs[(size_t)b * KK + idx] = w.S[(size_t)b * KK + idx];
+}
+
 // Row sums of M = (G - alpha I) X = H H^H X (in D), one warp per user n: Re sum_i conj(X_ni)
 // M_ni (its sum over n is ||H^H X||_F^2), the interference sum_{i != n} |M_ni|^2 and the
 // signal |M_nn|^2 (Section VI eq. 15; user n's gain on beam i is (H W)_{n i} = s M_{n i}).
@@ -855,6 +874,18 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
     WB_TRY(cudaGetLastError());
   }
   if ((e = mark(4)) != cudaSuccess) return e;
+  if (a.refine) {
+    // one Newton step for G^-1 with the FP32-faithful G: X <- X (2 I - G X); it squares the
+    // residual I - G X that low-precision products and the rank-r truncation leave in X
+    WB_TRY(gemm<T>(s, B, K, K, K, a.Gs, K, KK, 0, a.Xs, K, KK, 0, w.D, K, L.sD, T(-1), nullptr,
+                   zero, w.ctl, C_BRANCH, kLiveMask));
+    add_two_diag_kernel<T><<<dim3((K + 127) / 128, B), 128, 0, s>>>(a, w);
+    WB_TRY(cudaGetLastError());
+    WB_TRY(gemm<T>(s, B, K, K, K, a.Xs, K, KK, 0, w.D, K, L.sD, 0, w.S, K, KK, one, nullptr,
+                   zero, w.ctl, C_BRANCH, kLiveMask));
+    copy_refined_kernel<T><<<dim3((unsigned)((KK + 255) / 256), B), 256, 0, s>>>(a, w);
+    WB_TRY(cudaGetLastError());
+  }
   // SINR and scale, then W = s H^H X.  M = (G - alpha I) X: the shift is applied to G before
   // the product, since G X - alpha X cancels to about I - I when alpha dominates H H^H.
   WB_TRY(gemm<T>(s, B, K, K, K, a.Gs, K, KK, 0, a.Xs, K, KK, 0, w.D, K, L.sD, one, nullptr,
@@ -867,7 +898,7 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
     if (a.tc_products) {
       e = tc_wprod_f32(a.H, reinterpret_cast<float*>(base + L.oP), a.Xs, w.ws,
                        reinterpret_cast<float*>(base + L.oXB), a.W, B, N, K, L.Kp,
-                       reinterpret_cast<int*>(a.info) + 7, 8, a.active, s, &nl);
+                       reinterpret_cast<int*>(a.info) + 7, 8, a.active, a.gemm_bf16, s, &nl);
       if (e != cudaSuccess) return e;
     }
   }

@@ -115,6 +115,8 @@ wbrzf_status run_noalloc(int batch, int N, int K, const void* H, double alpha, d
   a.tvec = nullptr;        // no step counters: every instance takes the step as snapshot 0
   a.active = nullptr;
   a.tc_products = 0;
+  a.gemm_bf16 = 0;
+  a.refine = 0;
   a.eta = 1.0;
   a.k_init = 1;
   a.p = 0;

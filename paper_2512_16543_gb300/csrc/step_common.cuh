@@ -49,6 +49,8 @@ struct StepArgs {
   int dmax, rcap;          // largest sketch width, largest Woodbury rank
   size_t trace_stride;     // bytes per instance trace record
   int tc_products;         // blocked engine, complex64: Gram and precoder on tensor cores
+  int gemm_bf16;           // blocked engine, complex64: the precoder product in BF16
+  int refine;              // blocked engine: one Newton step X <- X (2 I - G X) per snapshot
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -161,6 +163,7 @@ struct BlockedLayout {
   // multi-CTA reductions: Gram tiles' partial sums of |dG|^2 and |G|^2 (double, kGramTile
   // entries per tile), the per-user SINR row sums (3 reals per user), the dG down-scale 2^-e
   size_t oGpart, oRows, oDsc;
+  size_t oS;                       // K x K scratch of the refinement step
   int gtiles;
   // complex64 only, operands of the tensor-core products (floats):
   //   P  [batch][4][K][Np]   Re_hi, Im_hi, Re_lo, Im_lo planes of H (TF32), Np = N rounded to 4
@@ -207,6 +210,7 @@ __host__ __device__ inline BlockedLayout blocked_layout(int batch, int N, int K,
   L.oGpart = take(2 * (size_t)L.gtiles, 8);
   L.oRows = take(3 * (size_t)K, tb);
   L.oDsc = take(1, tb);
+  L.oS = take((size_t)K * K, cxb);
   L.Np = (N + 3) / 4 * 4;
   L.Kp = (K + 1) / 2 * 2;
   L.sP = 4 * (size_t)K * L.Np;
@@ -263,10 +267,11 @@ cudaError_t run_blocked_f64(const StepArgs<double>& a, unsigned char* base, cuda
 cudaError_t tc_gram_f32(const cx<float>* H, float* P, cx<float>* D, size_t sD, int batch, int N,
                         int K, int Np, int* stat, int stat_stride, const unsigned char* active,
                         cudaStream_t s, int* launches);
+// bf16 != 0: the precoder product takes BF16 operands (kind::f16) instead of TF32.
 cudaError_t tc_wprod_f32(const cx<float>* H, float* T, const cx<float>* X, const float* ws,
                          float* XB, cx<float>* W, int batch, int N, int K, int Kp, int* stat,
-                         int stat_stride, const unsigned char* active, cudaStream_t s,
-                         int* launches);
+                         int stat_stride, const unsigned char* active, int bf16,
+                         cudaStream_t s, int* launches);
 // Tensor-core kernel (complex64, K <= 32, even N); hmap: H as a 2-D FP32 tensor map
 // {2N, batch K}, box {64, K} (step_tc.cu).  `hmap` points to a CUtensorMap.
 cudaError_t launch_step_tc(const StepArgs<float>& a, const void* hmap, size_t smem,

@@ -23,6 +23,7 @@
 // Every mbarrier wait is bounded by a %globaltimer deadline; a CTA whose wait expires records
 // WBRZF_STATUS_TIMEOUT for its instance, waits (again bounded) for its own loads and MMAs in
 // flight and frees its tensor memory before it exits.
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include "step_kernel.cuh"
@@ -50,6 +51,7 @@ struct TcArgs {
   int* stat;              // instance b's status word at stat[stat_stride * b]
   int stat_stride;
   const unsigned char* active;   // NULL or per-instance mask: inactive instances are skipped
+  int bf16;               // operands are BF16 (kind::f16), else TF32 (kind::tf32)
 };
 
 __device__ __forceinline__ bool mbar_wait_drain(uint32_t a, uint32_t parity) {
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(
         const uint32_t sa = smem_u32(sm + (size_t)s * kStageBytes), sb = sa + kStageA;
         const uint32_t full = bar_full + 8 * s;
         mbar_expect_tx(full, kStageBytes);
-        const int x = 32 * c;
+        const int x = (g.bf16 ? 64 : 32) * c;    // 128 bytes of the reduction per stage
         if (g.mode == TC_GRAM) {
           for (int p = 0; p < 4; ++p) {
             tma_load_2d(sa + 4096 * p, &mapA, x, (4 * b + p) * K + 32 * tm, full);
@@ -136,16 +138,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t id = idesc_tf32(128, 256);
+      const uint32_t id = g.bf16 ? idesc_bf16(128, 256) : idesc_tf32(128, 256);
       for (int c = 0; c < g.ksteps; ++c) {
         const int s = c % kTcStages;
         if (!mbar_wait(bar_full + 8 * s, (uint32_t)((c / kTcStages) & 1), abort_flag)) break;
         tc_fence_after();
         const uint32_t sa = smem_u32(sm + (size_t)s * kStageBytes), sb = sa + kStageA;
+        // 4 MMAs per 128-byte row: K = 8 TF32 or K = 16 BF16 elements (32 bytes) each
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_tf32(tmem, desc_sw128(sa + 32 * kk), desc_sw128(sb + 32 * kk), id,
-                   (c > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < 4; ++kk) {
+          if (g.bf16)
+            mma_bf16(tmem, desc_sw128(sa + 32 * kk), desc_sw128(sb + 32 * kk), id,
+                     (c > 0 || kk > 0) ? 1u : 0u);
+          else
+            mma_tf32(tmem, desc_sw128(sa + 32 * kk), desc_sw128(sb + 32 * kk), id,
+                     (c > 0 || kk > 0) ? 1u : 0u);
+        }
         mma_commit(bar_empty + 8 * s);
         *consumed = c + 1;
       }
@@ -300,6 +308,70 @@ __global__ void expand_x_kernel(const cx<float>* __restrict__ X, const float* __
   }
 }
 
+// BF16 variants of the precoder operands (round to nearest even), row stride 2 Kp4 elements
+__global__ void transpose_h_bf16_kernel(const cx<float>* __restrict__ H,
+                                        __nv_bfloat16* __restrict__ T, int N, int K, int Kp4) {
+  __shared__ cx<float> tl[32][33];
+  const int b = blockIdx.z, n0 = 32 * blockIdx.x, k0 = 32 * blockIdx.y;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const cx<float>* Hb = H + (size_t)b * K * N;
+  for (int r = ty; r < 32; r += 8) {
+    const int k = k0 + r, n = n0 + tx;
+    tl[r][tx] = (k < K && n < N) ? Hb[(size_t)k * N + n] : cmk(0.f, 0.f);
+  }
+  __syncthreads();
+  __nv_bfloat16* Tb = T + (size_t)b * N * 2 * Kp4;
+  for (int r = ty; r < 32; r += 8) {
+    const int n = n0 + r, k = k0 + tx;
+    if (n < N && k < K) {
+      const cx<float> v = tl[tx][r];
+      *reinterpret_cast<__nv_bfloat162*>(Tb + (size_t)n * 2 * Kp4 + 2 * k) =
+          __floats2bfloat162_rn(v.re, v.im);
+    }
+  }
+}
+
+__global__ void expand_x_bf16_kernel(const cx<float>* __restrict__ X, const float* __restrict__ ws,
+                                     __nv_bfloat16* __restrict__ XB, int K, int Kp4) {
+  __shared__ cx<float> tl[32][33];
+  const int b = blockIdx.z, j0 = 32 * blockIdx.x, k0 = 32 * blockIdx.y;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const cx<float>* Xb = X + (size_t)b * K * K;
+  const float s = ws[b];
+  for (int r = ty; r < 32; r += 8) {
+    const int k = k0 + r, j = j0 + tx;
+    tl[r][tx] = (k < K && j < K) ? Xb[(size_t)k * K + j] : cmk(0.f, 0.f);
+  }
+  __syncthreads();
+  __nv_bfloat16* XBb = XB + (size_t)b * 2 * K * 2 * Kp4;
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r, k = k0 + tx;
+    if (j < K && k < K) {
+      const cx<float> x = tl[tx][r];
+      *reinterpret_cast<__nv_bfloat162*>(XBb + (size_t)(2 * j) * 2 * Kp4 + 2 * k) =
+          __floats2bfloat162_rn(s * x.re, s * x.im);
+      *reinterpret_cast<__nv_bfloat162*>(XBb + (size_t)(2 * j + 1) * 2 * Kp4 + 2 * k) =
+          __floats2bfloat162_rn(s * x.im, -s * x.re);
+    }
+  }
+}
+
+// 2-D BF16 tensor map: `rows` rows of `width` elements (stride `stride` elements), box 64
+// elements (128 bytes) x box_rows, 128-byte swizzle.
+bool encode_map_bf16(CUtensorMap* map, const __nv_bfloat16* base, int width, size_t rows,
+                     size_t stride, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)stride * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims,
+             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 // 2-D FP32 tensor map over `rows` rows of `width` floats (row stride `stride` floats), box
 // 32 floats (128 bytes) x box_rows, 128-byte swizzle.
 bool encode_map(CUtensorMap* map, const float* base, int width, size_t rows, size_t stride,
@@ -344,6 +416,7 @@ cudaError_t tc_gram_f32(const cx<float>* H, float* P, cx<float>* D, size_t sD, i
     return cudaErrorInvalidValue;
   TcArgs g;
   g.mode = TC_GRAM;
+  g.bf16 = 0;
   g.batch = batch;
   g.N = N;
   g.K = K;
@@ -363,26 +436,41 @@ cudaError_t tc_gram_f32(const cx<float>* H, float* P, cx<float>* D, size_t sD, i
 
 cudaError_t tc_wprod_f32(const cx<float>* H, float* T, const cx<float>* X, const float* ws,
                          float* XB, cx<float>* W, int batch, int N, int K, int Kp, int* stat,
-                         int stat_stride, const unsigned char* active, cudaStream_t s,
+                         int stat_stride, const unsigned char* active, int bf16, cudaStream_t s,
                          int* launches) {
   cudaError_t e = set_tc_smem();
   if (e != cudaSuccess) return e;
-  transpose_h_kernel<<<dim3((N + 31) / 32, (K + 31) / 32, batch), dim3(32, 8), 0, s>>>(H, T, N,
-                                                                                      K, Kp);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  expand_x_kernel<<<dim3((K + 31) / 32, (K + 31) / 32, batch), dim3(32, 8), 0, s>>>(X, ws, XB,
-                                                                                    K, Kp);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   alignas(64) CUtensorMap ma, mb;
-  if (!encode_map(&ma, T, 2 * K, (size_t)batch * N, 2 * (size_t)Kp, 128) ||
-      !encode_map(&mb, XB, 2 * K, (size_t)batch * 2 * K, 2 * (size_t)Kp, 256))
-    return cudaErrorInvalidValue;
+  const dim3 tg((N + 31) / 32, (K + 31) / 32, batch), xg((K + 31) / 32, (K + 31) / 32, batch);
+  if (bf16) {
+    // BF16 operands in the same buffers (they need half the bytes); rows of 2 Kp4 elements
+    // keep every row 16-byte aligned
+    const int Kp4 = (K + 3) / 4 * 4;
+    __nv_bfloat16* T16 = reinterpret_cast<__nv_bfloat16*>(T);
+    __nv_bfloat16* X16 = reinterpret_cast<__nv_bfloat16*>(XB);
+    transpose_h_bf16_kernel<<<tg, dim3(32, 8), 0, s>>>(H, T16, N, K, Kp4);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    expand_x_bf16_kernel<<<xg, dim3(32, 8), 0, s>>>(X, ws, X16, K, Kp4);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!encode_map_bf16(&ma, T16, 2 * K, (size_t)batch * N, 2 * (size_t)Kp4, 128) ||
+        !encode_map_bf16(&mb, X16, 2 * K, (size_t)batch * 2 * K, 2 * (size_t)Kp4, 256))
+      return cudaErrorInvalidValue;
+  } else {
+    transpose_h_kernel<<<tg, dim3(32, 8), 0, s>>>(H, T, N, K, Kp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    expand_x_kernel<<<xg, dim3(32, 8), 0, s>>>(X, ws, XB, K, Kp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!encode_map(&ma, T, 2 * K, (size_t)batch * N, 2 * (size_t)Kp, 128) ||
+        !encode_map(&mb, XB, 2 * K, (size_t)batch * 2 * K, 2 * (size_t)Kp, 256))
+      return cudaErrorInvalidValue;
+  }
   TcArgs g;
   g.mode = TC_WPROD;
+  g.bf16 = bf16;
   g.batch = batch;
   g.N = N;
   g.K = K;
-  g.ksteps = (2 * K + 31) / 32;
+  g.ksteps = bf16 ? (2 * K + 63) / 64 : (2 * K + 31) / 32;
   g.tiles_n = (K + 127) / 128;
   g.out = W;
   g.sOut = (size_t)N * K;

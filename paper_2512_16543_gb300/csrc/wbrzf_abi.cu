@@ -173,6 +173,8 @@ struct wbrzf {
   long long glaunches;
   int glast_engine;
   bool in_group;         // stepped by a wbrzf_group (its stream belongs to the group)
+  int gemm_bf16;         // wbrzf_set_precision_mode: BF16 precoder product
+  int refine;            // wbrzf_set_precision_mode: Newton refinement steps (0 or 1)
 };
 
 namespace {
@@ -212,6 +214,8 @@ StepArgs<T> make_args(const wbrzf* h, const void* H, void* W, int mode,
   a.rcap = h->rule.rcap;
   a.trace_stride = h->trace_stride;
   a.tc_products = (h->prec == WBRZF_C64 && h->engine != WBRZF_ENGINE_BLOCKED_FMA) ? 1 : 0;
+  a.gemm_bf16 = (a.tc_products && h->gemm_bf16) ? 1 : 0;
+  a.refine = h->refine;
   return a;
 }
 
@@ -239,11 +243,17 @@ bool use_blocked(const wbrzf* h) {
          (h->engine == WBRZF_ENGINE_AUTO && !h->simt_ok);
 }
 
+// The precision modes run on the blocked engine only.
+bool precision_mode_ok(const wbrzf* h) {
+  return (h->gemm_bf16 == 0 && h->refine == 0) || use_blocked(h);
+}
+
 wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode,
                       const unsigned char* active) {
   if (!h || !H || !W) return WBRZF_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(H) | reinterpret_cast<uintptr_t>(W)) % cx_bytes(h->prec))
     return WBRZF_ERR_INVALID_ARG;
+  if (!precision_mode_ok(h)) return WBRZF_ERR_UNSUPPORTED;
   cudaError_t e;
   if (use_blocked(h)) {
     unsigned char* base = h->ws + blocked_offset(h->batch, h->K, h->prec);
@@ -451,6 +461,8 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   h->glaunches = 0;
   h->glast_engine = 0;
   h->in_group = false;
+  h->gemm_bf16 = 0;
+  h->refine = 0;
   {
     const size_t tc = tc_smem_bytes(K, r.dmax, r.rcap);
     h->smem_tc = (simt_ok && prec == WBRZF_C64 && K <= 32 && tc <= 227 * 1024) ? tc : 0;
@@ -674,6 +686,15 @@ wbrzf_status wbrzf_stage_times(wbrzf* h, float* ms_out) {
   }
   e = cudaEventElapsedTime(&ms_out[5], h->ev[0], h->ev[5]);
   return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
+}
+
+wbrzf_status wbrzf_set_precision_mode(wbrzf* h, int bf16_products, int refine_steps) {
+  if (!h || refine_steps < 0 || refine_steps > 1) return WBRZF_ERR_INVALID_ARG;
+  if (bf16_products && h->prec != WBRZF_C64) return WBRZF_ERR_UNSUPPORTED;
+  h->gemm_bf16 = bf16_products ? 1 : 0;
+  h->refine = refine_steps;
+  invalidate_graph(h);
+  return WBRZF_OK;
 }
 
 wbrzf_status wbrzf_set_graph(wbrzf* h, int enable) {
