@@ -40,7 +40,8 @@ UNEVEN = {"count": 4096, "desc": (
     "(TF32 tensor-core products where the autotuned engine uses them), p=8, k_init=2, "
     "r_max=min(K/2, 64), re-inverse every 20 snapshots; one handle per (N, K) class, classes "
     "on their own streams, engine per class chosen by the autotuner, group step replayed "
-    "from a CUDA graph")}
+    "from a CUDA graph; second run: blocked engine with BF16 precoder products and one "
+    "Newton refinement of X per snapshot")}
 SERVING = {"states": 2000, "rate": 50000.0, "classes": ((256, 32), (512, 64), (1024, 128)),
            "desc": ("serving_2000: 2000 resident beam states, (N, K) ~ U{(256, 32), (512, 64), "
                     "(1024, 128)}, complex64, 50 km discs, SNR 10 dB, p=8, k_init=2, "
@@ -417,6 +418,56 @@ def main_uneven(args):
             for h in hs_:
                 h.close()
 
+    grp.close()
+    for h in hs:
+        h.close()
+
+    # ---- second run: BF16 precoder products plus one Newton refinement of X per snapshot
+    # (blocked engine for every class), error against FP64 as above
+    hs = []
+    for c in pop:
+        h = binding.WBRZF(c.batch, c.scenario.N, c.scenario.K, c.alpha, c.sigma2,
+                          p_t=c.scenario.p_t, rule=binding.RankRule(**uneven_rule_kw(
+                              c.scenario.K, chosen)), device=dev, workspace_for="blocked")
+        h.set_instance_ids([int(i) for i in c.index])
+        h.set_engine("blocked")
+        h.set_precision_mode(True, 1)
+        hs.append(h)
+    grp = binding.WBRZFGroup(hs)
+    grp.set_graph(True)
+    ms_bf, _, _ = timed(grp, hs)
+    bf_w, bf_rate = 0.0, 0.0
+    for ci, c in enumerate(pop):
+        K = c.scenario.K
+        rk = uneven_rule_kw(K, chosen)
+        for j in range(min(2, c.batch)):
+            pair = []
+            for prec in ("c64", "c128"):
+                h = binding.WBRZF(1, c.scenario.N, K, [c.alpha[j]], [c.sigma2[j]],
+                                  p_t=c.scenario.p_t, rule=binding.RankRule(**rk),
+                                  precision=prec, device=dev, workspace_for="blocked")
+                h.set_instance_ids([int(c.index[j])])
+                if prec == "c64":
+                    h.set_engine("blocked")
+                    h.set_precision_mode(True, 1)
+                pair.append(h)
+            for t in range(4):
+                Hd = Hs[ci][t, j:j + 1].contiguous()
+                outs = []
+                for h, dt in zip(pair, (torch.complex64, torch.complex128)):
+                    Hx = Hd.to(dt)
+                    W = h.full_inverse(Hx) if t == 0 else h.update(Hx)
+                    outs.append((W[0].to(torch.complex128), float(h.sum_rate()[1][0])))
+                (W32, r32), (W64, r64) = outs
+                bf_w = max(bf_w, float((W32 - W64).norm() / W64.norm()))
+                bf_rate = max(bf_rate, abs(r32 - r64))
+            for h in pair:
+                h.close()
+    bf16_refine = {"value": world * count * K_ / barrier_max(sum(ms_bf) / 1e3, world),
+                   "unit": "updates/s", "ms_per_step": statistics.mean(ms_bf),
+                   "engine": "blocked (all classes)",
+                   "error_vs_fp64": {"max_W_relerr": bf_w, "max_sum_rate_gap_bits": bf_rate}}
+
     tot_wb = barrier_max(sum(ms_wb) / 1e3, world)
     tot_full = barrier_max(sum(ms_full) / 1e3, world)
     value = world * count * K_ / tot_wb
@@ -458,7 +509,7 @@ def main_uneven(args):
             "error_vs_fp64": {"max_W_relerr": worst_w, "max_sum_rate_gap_bits": worst_rate,
                               "sample": "2 instances per class x 4 snapshots, against the "
                                         "library's complex128 path on the same inputs"},
-            "precision_modes": {"tf32": "measured", "bf16_refine": "not built"},
+            "precision_modes": {"tf32": "the headline run above", "bf16_refine": bf16_refine},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": None,
             "gpu_launches": launches, "clocks": clk,
         }
