@@ -12,8 +12,9 @@
 //         accurate to FP32 rounding (the hi/lo split keeps 22 of FP32's 24 mantissa bits and
 //         the tensor cores accumulate in FP32) -- the precision dG = G_t - G_{t-1} needs.
 //   W = s H^H X.  Per 128-antenna M-tile the CTA writes H^T (antennas x interleaved users,
-//         TF32) and B = s [[Xr, Xi], [Xi, -Xr]] (interleaved, TF32), and one M = 128, N = 64
-//         MMA per 8-element step yields W's interleaved rows directly (TF32 inputs, FP32
+//         TF32; H read from global memory, where the Gram phase left it in L2) and
+//         B = s [[Xr, Xi], [Xi, -Xr]] (interleaved, TF32), and one M = 128, N = 64 MMA per
+//         8-element step yields W's interleaved rows directly (TF32 inputs, FP32
 //         accumulation).
 //
 // The phases in between (dG, arSVD, Woodbury / direct inverse, scale, SINR) are the shared
@@ -75,9 +76,8 @@ __global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
   const int row0 = b * K;
   prefetch_state<float>(a, b, Dm, X);
 
-  auto issue_block = [&](int g) {      // g: running block index (Gram blocks, then W blocks)
-    const int s = g % kStages;
-    const int c = g < nblk ? g : g - nblk;
+  auto issue_block = [&](int c) {      // block c of 32 antennas of the Gram phase
+    const int s = c % kStages;
     mbar_expect_tx(bar_full + 8 * s, tx_bytes);
     tma_load_2d(smem_u32(ring + s * 8192), &hmap, 64 * c, row0, bar_full + 8 * s);
   };
@@ -128,10 +128,6 @@ __global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
       }
       mma_commit(bar_mma + 8 * buf);
     }
-  }
-  // W-phase prefetch: the staging ring is free once the last split has been read
-  if (tid == 0) {
-    for (int g = nblk; g < nblk + kStages && g < 2 * nblk; ++g) issue_block(g);
   }
   mbar_wait(bar_mma + 8 * ((nblk - 1) & 1), (uint32_t)(((nblk - 1) >> 1) & 1), abort_flag);
   tc_fence_after();
@@ -216,28 +212,28 @@ __global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
     const int nmt = (N + 127) / 128;
     cx<float>* const Wb = a.W + (size_t)b * N * K;
     for (int mt = 0; mt < nmt; ++mt) {
-      for (int qd = 0; qd < 4; ++qd) {
-        const int c = 4 * mt + qd;
-        if (c < nblk) {
-          const int g = nblk + c, sl = g % kStages;
-          mbar_wait(bar_full + 8 * sl, (uint32_t)((g / kStages) & 1), abort_flag);
-          const float* rawf = reinterpret_cast<const float*>(ring + sl * 8192);
-          // warp -> users k = warp + 8 i, lane -> antenna n of this block
+      {
+        // H^T of this M-tile straight from global memory (H was read once in the Gram phase
+        // and sits in L2): a thread's 16 loads are all in flight before the first is used.
+        // warp -> users k = warp + 8 i, lane -> antenna 128 mt + 32 qd + lane
+        const float2* Hg = reinterpret_cast<const float2*>(a.H) + (size_t)row0 * N;
+        float2 hv[4][4];
+#pragma unroll
+        for (int qd = 0; qd < 4; ++qd) {
+          const int n = 128 * mt + 32 * qd + lane;
+#pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int k = warp + 8 * i;
-            float2 hv = make_float2(0.f, 0.f);
-            if (k < K) hv = *reinterpret_cast<const float2*>(rawf + k * 64 + 2 * lane);
-            const int row = 32 * qd + lane, kf = 2 * k;
-            *reinterpret_cast<float2*>(At + (kf >> 5) * 16384 + sw128(row, kf & 31)) =
-                make_float2(tf32_rna(hv.x), tf32_rna(hv.y));
+            hv[qd][i] = (k < K && n < N) ? __ldg(Hg + (size_t)k * N + n) : make_float2(0.f, 0.f);
           }
-          __syncthreads();
-          if (tid == 0 && g + kStages < 2 * nblk) issue_block(g + kStages);
-        } else {
+        }
+#pragma unroll
+        for (int qd = 0; qd < 4; ++qd) {
+#pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int k = warp + 8 * i, row = 32 * qd + lane, kf = 2 * k;
             *reinterpret_cast<float2*>(At + (kf >> 5) * 16384 + sw128(row, kf & 31)) =
-                make_float2(0.f, 0.f);
+                make_float2(tf32_rna(hv[qd][i].x), tf32_rna(hv[qd][i].y));
           }
         }
       }
