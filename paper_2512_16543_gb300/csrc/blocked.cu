@@ -103,14 +103,19 @@ struct Live {
 };
 __host__ __device__ inline Live live_none() { return Live{1 << 30, 1 << 30, 1 << 30}; }
 
-template <class T>
-__global__ void __launch_bounds__(256) cgemm_kernel(const GemmArgs<T> g) {
+// BM x BN output tile per CTA of (BM/4) x (BN/4) threads, 4 x 4 outputs each (rows
+// ty + BM/4 i, columns tx + BN/4 j), reduction in chunks of 16 through shared memory.  The
+// host takes 32-wide tiles where the (live) output is that narrow: the small matrices of
+// Algorithm 1 and of the Woodbury update would fill a 64 x 64 tile only a few percent.
+template <class T, int BM, int BN>
+__global__ void __launch_bounds__((BM / 4) * (BN / 4)) cgemm_kernel(const GemmArgs<T> g) {
+  constexpr int NT = (BM / 4) * (BN / 4), TX = BN / 4;
   const int b = blockIdx.z;
   if (!gate_ok(g.ctl, b, g.gidx, g.gmask)) return;
-  __shared__ cx<T> As[16][64 + 1];
-  __shared__ cx<T> Bs[16][64 + 1];
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  __shared__ cx<T> As[16][BM + 1];
+  __shared__ cx<T> Bs[16][BN + 1];
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX;
   const cx<T>* A = g.A + (size_t)b * g.sA;
   const cx<T>* B = g.B + (size_t)b * g.sB;
   int mlive = g.m_live, nlive = g.n_live, klive = g.k_live;
@@ -125,9 +130,9 @@ __global__ void __launch_bounds__(256) cgemm_kernel(const GemmArgs<T> g) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = cmk<T>(0, 0);
   for (int k0 = 0; k0 < kend; k0 += 16) {
-    for (int e = tid; e < 16 * 64; e += 256) {
+    for (int e = tid; e < 16 * BM; e += NT) {
       int r, kk;
-      if (g.opA == 0) { r = e >> 4; kk = e & 15; } else { kk = e >> 6; r = e & 63; }
+      if (g.opA == 0) { r = e >> 4; kk = e & 15; } else { kk = e / BM; r = e % BM; }
       const int gi = m0 + r, gk = k0 + kk;
       cx<T> v = cmk<T>(0, 0);
       if (gi < g.m && gk < kend) {
@@ -136,9 +141,9 @@ __global__ void __launch_bounds__(256) cgemm_kernel(const GemmArgs<T> g) {
       }
       As[kk][r] = v;
     }
-    for (int e = tid; e < 16 * 64; e += 256) {
+    for (int e = tid; e < 16 * BN; e += NT) {
       int c, kk;
-      if (g.opB == 0) { kk = e >> 6; c = e & 63; } else { c = e >> 4; kk = e & 15; }
+      if (g.opB == 0) { kk = e / BN; c = e % BN; } else { c = e >> 4; kk = e & 15; }
       const int gj = n0 + c, gk = k0 + kk;
       cx<T> v = cmk<T>(0, 0);
       if (gj < g.n && gk < kend)
@@ -150,9 +155,9 @@ __global__ void __launch_bounds__(256) cgemm_kernel(const GemmArgs<T> g) {
     for (int kk = 0; kk < 16; ++kk) {
       cx<T> av[4], bv[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + (BM / 4) * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + (BN / 4) * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -164,17 +169,24 @@ __global__ void __launch_bounds__(256) cgemm_kernel(const GemmArgs<T> g) {
   cx<T>* C = g.C + (size_t)b * g.sC;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int gi = m0 + ty + 16 * i;
+    const int gi = m0 + ty + (BM / 4) * i;
     if (gi >= g.m) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int gj = n0 + tx + 16 * j;
+      const int gj = n0 + tx + (BN / 4) * j;
       if (gj >= g.n) continue;
       cx<T> v = cscale(acc[i][j], al);
       if (g.beta != T(0)) v = cadd(v, cscale(C[(size_t)gi * g.ldc + gj], g.beta));
       C[(size_t)gi * g.ldc + gj] = v;
     }
   }
+}
+
+template <class T, int BM, int BN>
+cudaError_t launch_cgemm(const GemmArgs<T>& g, int batch, cudaStream_t s) {
+  dim3 grid((g.n + BN - 1) / BN, (g.m + BM - 1) / BM, batch);
+  cgemm_kernel<T, BM, BN><<<grid, (BM / 4) * (BN / 4), 0, s>>>(g);
+  return cudaGetLastError();
 }
 
 template <class T>
@@ -186,9 +198,13 @@ cudaError_t gemm(cudaStream_t s, int batch, int m, int n, int k, const cx<T>* A,
   if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
   GemmArgs<T> g{m, n, k, A, lda, sA, opA, B, ldb, sB, opB, C, ldc, sC, alpha, scale, beta,
                 ctl, gidx, gmask, dshift, live.m, live.n, live.k, lm, ln, lk};
-  dim3 grid((n + 63) / 64, (m + 63) / 64, batch);
-  cgemm_kernel<T><<<grid, 256, 0, s>>>(g);
-  return cudaGetLastError();
+  // tile widths from the extents known on the host (the control-word limits can only shrink
+  // them further)
+  const bool nm = (m < live.m ? m : live.m) <= 32, nn = (n < live.n ? n : live.n) <= 32;
+  if (nm && nn) return launch_cgemm<T, 32, 32>(g, batch, s);
+  if (nm) return launch_cgemm<T, 32, 64>(g, batch, s);
+  if (nn) return launch_cgemm<T, 64, 32>(g, batch, s);
+  return launch_cgemm<T, 64, 64>(g, batch, s);
 }
 
 

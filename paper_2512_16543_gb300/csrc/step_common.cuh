@@ -108,17 +108,17 @@ __host__ __device__ inline size_t simt_smem_bytes(int K, int dmax, int rcap, siz
 }
 
 // ---------------------------------------------------------------- tensor-core kernel plan
-constexpr int kStages = 2;                    // TMA staging ring depth (blocks of 32 antennas)
 constexpr uint32_t kTmemCols = 128;           // Gram D: 128 x 128; W D: 128 x 64
 
-// Shared memory of the tensor-core kernel (offsets from a 1024-byte aligned base):
+// Shared memory of the tensor-core kernel (offsets from a 1024-byte aligned base), sized so
+// that four CTAs fit on an SM (54 KiB at K = 32):
 //   GXD   G (K x K) at 0, dG right after it, X at the end of the region; after the SINR phase
-//         the first 16 KiB hold the B tile of the precoder product (G and dG are dead, X is
+//         the first 16 KiB hold the B operand of the precoder product (G and dG are dead, X is
 //         read while B is written, so the region is at least 16 KiB + K^2 complex)
-//   ring  kStages TMA slots of 32 users x 32 antennas (8 KiB each)
-//   union Gram tiles (2 x 16 KiB) / Gram epilogue slices / SIMT workspace / H^T tile (32 KiB)
+//   union the Gram split tile (16 KiB) / Gram epilogue slices / SIMT workspace / one 16-user
+//         half of the precoder's A operand (16 KiB)
 struct TcLayout {
-  size_t oGXD, gxd_bytes, oX, oRing, oUnion, oBar, bytes_unpadded, union_bytes;
+  size_t oGXD, gxd_bytes, oX, oUnion, oBar, bytes_unpadded, union_bytes;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int K, int dmax, int rcap) {
@@ -130,14 +130,13 @@ __host__ __device__ inline TcLayout tc_layout(int K, int dmax, int rcap) {
   L.oGXD = 0;
   L.oX = L.gxd_bytes - kk8;
   size_t o = L.gxd_bytes;
-  L.oRing = o;  o = align_up(o + (size_t)kStages * 32 * 256, 1024);
   L.oUnion = o;
-  size_t u = 2 * 16384;                                   // Gram: two 128 x 128 B tiles
+  size_t u = 16384;                                       // split tile / A-operand half
   const size_t wk = work_bytes(K, dmax, rcap, false, 8, 4);
   if (wk > u) u = wk;
   const size_t sl = 2 * (size_t)K * (K + 1) * 8;          // Gram epilogue: two padded slices
   if (sl > u) u = sl;
-  L.union_bytes = align_up(u, 1024);                      // (>= the 32 KiB H^T tile)
+  L.union_bytes = align_up(u, 1024);
   o += L.union_bytes;
   L.oBar = o;   o += 256;
   L.bytes_unpadded = o;
@@ -272,9 +271,7 @@ cudaError_t tc_wprod_f32(const cx<float>* H, float* T, const cx<float>* X, const
                          float* XB, cx<float>* W, int batch, int N, int K, int Kp, int* stat,
                          int stat_stride, const unsigned char* active, int bf16,
                          cudaStream_t s, int* launches);
-// Tensor-core kernel (complex64, K <= 32, even N); hmap: H as a 2-D FP32 tensor map
-// {2N, batch K}, box {64, K} (step_tc.cu).  `hmap` points to a CUtensorMap.
-cudaError_t launch_step_tc(const StepArgs<float>& a, const void* hmap, size_t smem,
-                           cudaStream_t s);
+// Tensor-core kernel (complex64, K <= 32, even N, H 16-byte aligned) (step_tc.cu).
+cudaError_t launch_step_tc(const StepArgs<float>& a, size_t smem, cudaStream_t s);
 
 }  // namespace wbk

@@ -2,8 +2,8 @@
 //
 // Same steps and results as the SIMT kernel; the two dense contractions run on tcgen05:
 //
-//   Gram  G_t = H H^H.  For each block of 32 antennas a TMA load brings H[:, block] into a
-//         4-slot staging ring; the CTA splits it into four 32-row TF32 parts
+//   Gram  G_t = H H^H.  Each block of 32 antennas is read from global memory (the next block
+//         is in flight while the current one is used) and split into four 32-row TF32 parts
 //         P = [Re_hi; Im_hi; Re_lo; Im_lo] (hi = round-to-nearest TF32 of the FP32 value,
 //         lo = TF32 of the remainder), stored K-major with the 128-byte swizzle, and one
 //         M = N = 128 MMA per 8-antenna step accumulates D = P P^T in tensor memory.  With
@@ -11,16 +11,17 @@
 //         Im G = Im Re^T - Re Im^T are sums of the 32 x 32 blocks of D, so the Gram matrix is
 //         accurate to FP32 rounding (the hi/lo split keeps 22 of FP32's 24 mantissa bits and
 //         the tensor cores accumulate in FP32) -- the precision dG = G_t - G_{t-1} needs.
-//   W = s H^H X.  Per 128-antenna M-tile the CTA writes H^T (antennas x interleaved users,
-//         TF32; H read from global memory, where the Gram phase left it in L2) and
-//         B = s [[Xr, Xi], [Xi, -Xr]] (interleaved, TF32), and one M = 128, N = 64 MMA per
-//         8-element step yields W's interleaved rows directly (TF32 inputs, FP32
-//         accumulation).
+//   W = s H^H X.  Per 128-antenna M-tile and 16-user half the CTA writes H^T (antennas x
+//         interleaved users, TF32; H read from global memory, where the Gram phase left it in
+//         L2) beside B = s [[Xr, Xi], [Xi, -Xr]] (interleaved, TF32), and M = 128, N = 64
+//         MMAs per 8-element step accumulate W's interleaved rows in tensor memory (TF32
+//         inputs, FP32 accumulation).
 //
-// The phases in between (dG, arSVD, Woodbury / direct inverse, scale, SINR) are the shared
-// SIMT code (core_phases).  Every wait on an mbarrier is bounded by a %globaltimer deadline;
-// a CTA whose wait expires records WBRZF_STATUS_TIMEOUT, stops waiting and still frees its
-// tensor memory before it exits.
+// Shared memory is one split tile / workspace union beside G, dG and X (54 KiB at K = 32), so
+// four CTAs share an SM.  The phases in between (dG, arSVD, Woodbury / direct inverse, scale,
+// SINR) are the shared SIMT code (core_phases).  Every wait on an mbarrier is bounded by a
+// %globaltimer deadline; a CTA whose wait expires records WBRZF_STATUS_TIMEOUT, stops waiting
+// and still frees its tensor memory before it exits.
 #pragma once
 #include <cuda.h>
 
@@ -30,8 +31,7 @@
 namespace wbk {
 
 // ---------------------------------------------------------------- the kernel
-__global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
-    const StepArgs<float> a, const __grid_constant__ CUtensorMap hmap) {
+__global__ void __launch_bounds__(kThreads, 4) wbrzf_step_tc_kernel(const StepArgs<float> a) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw_u = smem_u32(smem_raw);
   unsigned char* const sm = smem_raw + ((1024 - (raw_u & 1023)) & 1023);
@@ -44,21 +44,16 @@ __global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
   cx<float>* const G = reinterpret_cast<cx<float>*>(sm + Ly.oGXD);
   cx<float>* const Dm = G + KK;
   cx<float>* const X = reinterpret_cast<cx<float>*>(sm + Ly.oX);
-  unsigned char* const ring = sm + Ly.oRing;              // kStages x (32 rows x 256 B)
   unsigned char* const uni = sm + Ly.oUnion;
   uint64_t* const bars = reinterpret_cast<uint64_t*>(sm + Ly.oBar);
-  // bars[0..kStages): staging full; [kStages, kStages+2): Gram MMA done; [kStages+2]: W done
-  const uint32_t bar_full = smem_u32(bars), bar_mma = smem_u32(bars + kStages),
-                 bar_w = smem_u32(bars + kStages + 2);
-  volatile int* const abort_flag = reinterpret_cast<volatile int*>(bars + kStages + 3);
-  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bars + kStages + 4);
+  // bars[0]: Gram MMA done; bars[1]: precoder MMA done
+  const uint32_t bar_mma = smem_u32(bars), bar_w = smem_u32(bars + 1);
+  volatile int* const abort_flag = reinterpret_cast<volatile int*>(bars + 2);
+  uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
   const int nblk = (N + 31) / 32;
-  const uint32_t tx_bytes = (uint32_t)K * 256u;
 
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(bar_full + 8 * s, 1);
     mbar_init(bar_mma, 1);
-    mbar_init(bar_mma + 8, 1);
     mbar_init(bar_w, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -76,31 +71,33 @@ __global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
   const int row0 = b * K;
   prefetch_state<float>(a, b, Dm, X);
 
-  auto issue_block = [&](int c) {      // block c of 32 antennas of the Gram phase
-    const int s = c % kStages;
-    mbar_expect_tx(bar_full + 8 * s, tx_bytes);
-    tma_load_2d(smem_u32(ring + s * 8192), &hmap, 64 * c, row0, bar_full + 8 * s);
-  };
-
   // ------------------------------------------------------------ 1. Gram on tensor cores
-  if (tid == 0) {
-    for (int g = 0; g < kStages && g < nblk; ++g) issue_block(g);
-  }
+  // Thread -> user gk = tid / 8 and antennas 4 gq .. 4 gq + 3 (gq = tid % 8) of every block
+  // of 32 antennas, read from global memory as two 16-byte words (N is even, so antenna pairs
+  // never straddle the end of a row); the next block is loaded while the current one is split
+  // and multiplied.
+  const int gk = tid >> 3, gq = tid & 7;
+  const float4* const Hrow =
+      reinterpret_cast<const float4*>(a.H + (size_t)(row0 + (gk < K ? gk : 0)) * N);
+  auto load_block = [&](int c, float4& v0, float4& v1) {
+    const int n0 = 32 * c + 4 * gq;
+    v0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    v1 = v0;
+    if (gk < K) {
+      if (n0 < N) v0 = __ldg(Hrow + (n0 >> 1));
+      if (n0 + 2 < N) v1 = __ldg(Hrow + (n0 >> 1) + 1);
+    }
+  };
+  float4 c0, c1, n0v, n1v;
+  load_block(0, c0, c1);
+  if (nblk > 1) load_block(1, n0v, n1v);
+  unsigned char* const tile = uni;                        // 128 rows x 128 B, one block
   for (int c = 0; c < nblk; ++c) {
-    const int s = c % kStages, buf = c & 1;
-    mbar_wait(bar_full + 8 * s, (uint32_t)((c / kStages) & 1), abort_flag);
-    if (c >= 2) mbar_wait(bar_mma + 8 * buf, (uint32_t)(((c - 2) >> 1) & 1), abort_flag);
+    // the tile is free once the MMAs of the previous block have completed
+    if (c >= 1) mbar_wait(bar_mma, (uint32_t)((c - 1) & 1), abort_flag);
     {
-      // split: thread -> (user k, 4 antennas q); parts Re_hi, Im_hi, Re_lo, Im_lo
-      const float* rawf = reinterpret_cast<const float*>(ring + s * 8192);
-      unsigned char* tile = uni + buf * 16384;
-      const int k = tid >> 3, q = tid & 7;
-      float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-      if (k < K) {
-        v0 = *reinterpret_cast<const float4*>(rawf + k * 64 + 8 * q);
-        v1 = *reinterpret_cast<const float4*>(rawf + k * 64 + 8 * q + 4);
-      }
-      const float re[4] = {v0.x, v0.z, v1.x, v1.z}, im[4] = {v0.y, v0.w, v1.y, v1.w};
+      // split into parts Re_hi, Im_hi, Re_lo, Im_lo (rows 0-31, 32-63, 64-95, 96-127)
+      const float re[4] = {c0.x, c0.z, c1.x, c1.z}, im[4] = {c0.y, c0.w, c1.y, c1.w};
       float rh[4], ih[4], rl[4], il[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -109,27 +106,30 @@ __global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
         rl[i] = tf32_rna(re[i] - rh[i]);
         il[i] = tf32_rna(im[i] - ih[i]);
       }
-      *reinterpret_cast<float4*>(tile + sw128(k, 4 * q)) = make_float4(rh[0], rh[1], rh[2], rh[3]);
-      *reinterpret_cast<float4*>(tile + sw128(32 + k, 4 * q)) = make_float4(ih[0], ih[1], ih[2], ih[3]);
-      *reinterpret_cast<float4*>(tile + sw128(64 + k, 4 * q)) = make_float4(rl[0], rl[1], rl[2], rl[3]);
-      *reinterpret_cast<float4*>(tile + sw128(96 + k, 4 * q)) = make_float4(il[0], il[1], il[2], il[3]);
+      *reinterpret_cast<float4*>(tile + sw128(gk, 4 * gq)) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+      *reinterpret_cast<float4*>(tile + sw128(32 + gk, 4 * gq)) = make_float4(ih[0], ih[1], ih[2], ih[3]);
+      *reinterpret_cast<float4*>(tile + sw128(64 + gk, 4 * gq)) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+      *reinterpret_cast<float4*>(tile + sw128(96 + gk, 4 * gq)) = make_float4(il[0], il[1], il[2], il[3]);
     }
     fence_async_smem();
+    tc_fence_before();
     __syncthreads();
     if (tid == 0) {
-      if (c + kStages < nblk) issue_block(c + kStages);
       tc_fence_after();
       const uint32_t id = idesc_tf32(128, 128);
-      const uint32_t tile = smem_u32(uni + buf * 16384);
+      const uint32_t ta = smem_u32(tile);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
-        const uint64_t dsc = desc_sw128(tile + 32 * kk);
+        const uint64_t dsc = desc_sw128(ta + 32 * kk);
         mma_tf32(tmem, dsc, dsc, id, (c > 0 || kk > 0) ? 1u : 0u);
       }
-      mma_commit(bar_mma + 8 * buf);
+      mma_commit(bar_mma);
     }
+    c0 = n0v;
+    c1 = n1v;
+    if (c + 2 < nblk) load_block(c + 2, n0v, n1v);
   }
-  mbar_wait(bar_mma + 8 * ((nblk - 1) & 1), (uint32_t)(((nblk - 1) >> 1) & 1), abort_flag);
+  mbar_wait(bar_mma, (uint32_t)((nblk - 1) & 1), abort_flag);
   tc_fence_after();
   {
     // Gram epilogue.  Warp (quadrant qa = part a of the rows, half h) reads D rows 32a + k,
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
 
   // ------------------------------------------------------------ 7. W = s H^H X on tensor cores
   {
-    unsigned char* const At = uni;              // 2 K-blocks x 128 rows x 128 B
+    unsigned char* const At = uni;              // one 16-user half: 128 rows x 128 B
     unsigned char* const Bt = sm + Ly.oGXD;     // 2 K-blocks x 64 rows x 128 B (G, dG dead)
     // B[(j, c')][(k, c)]: rows 2j (Re W), 2j + 1 (Im W); columns 2k (Re H), 2k + 1 (Im H)
     for (int e = tid; e < 64 * 16; e += kThreads) {
@@ -210,49 +210,53 @@ __global__ void __launch_bounds__(kThreads, 3) wbrzf_step_tc_kernel(
       *reinterpret_cast<float4*>(Bt + kb * 8192 + sw128(row, kin)) = make_float4(v[0], v[1], v[2], v[3]);
     }
     const int nmt = (N + 127) / 128;
+    const int nh = K > 16 ? 2 : 1;              // 16-user halves of the reduction
+    int wph = 0;                                // precoder MMA commits so far
     cx<float>* const Wb = a.W + (size_t)b * N * K;
     for (int mt = 0; mt < nmt; ++mt) {
-      {
-        // H^T of this M-tile straight from global memory (H was read once in the Gram phase
-        // and sits in L2): a thread's 16 loads are all in flight before the first is used.
-        // warp -> users k = warp + 8 i, lane -> antenna 128 mt + 32 qd + lane
-        const float2* Hg = reinterpret_cast<const float2*>(a.H) + (size_t)row0 * N;
-        float2 hv[4][4];
+      // H^T of this M-tile straight from global memory (H was read once in the Gram phase
+      // and sits in L2): a thread's 16 loads are all in flight before the first is used.
+      // warp -> users k = warp + 8 i, lane -> antenna 128 mt + 32 qd + lane
+      const float2* Hg = reinterpret_cast<const float2*>(a.H) + (size_t)row0 * N;
+      float2 hv[4][4];
 #pragma unroll
-        for (int qd = 0; qd < 4; ++qd) {
-          const int n = 128 * mt + 32 * qd + lane;
+      for (int qd = 0; qd < 4; ++qd) {
+        const int n = 128 * mt + 32 * qd + lane;
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int k = warp + 8 * i;
-            hv[qd][i] = (k < K && n < N) ? __ldg(Hg + (size_t)k * N + n) : make_float2(0.f, 0.f);
-          }
-        }
-#pragma unroll
-        for (int qd = 0; qd < 4; ++qd) {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int k = warp + 8 * i, row = 32 * qd + lane, kf = 2 * k;
-            *reinterpret_cast<float2*>(At + (kf >> 5) * 16384 + sw128(row, kf & 31)) =
-                make_float2(tf32_rna(hv[qd][i].x), tf32_rna(hv[qd][i].y));
-          }
+        for (int i = 0; i < 4; ++i) {
+          const int k = warp + 8 * i;
+          hv[qd][i] = (k < K && n < N) ? __ldg(Hg + (size_t)k * N + n) : make_float2(0.f, 0.f);
         }
       }
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t id = idesc_tf32(128, 64);
-        const uint32_t at = smem_u32(At), bt = smem_u32(Bt);
+      for (int h = 0; h < nh; ++h) {
+        // the A half is free once the previous MMAs have completed
+        if (wph > 0) mbar_wait(bar_w, (uint32_t)((wph - 1) & 1), abort_flag);
 #pragma unroll
-        for (int ks = 0; ks < 8; ++ks) {
-          const uint64_t ad = desc_sw128(at + (ks >> 2) * 16384 + 32 * (ks & 3));
-          const uint64_t bd = desc_sw128(bt + (ks >> 2) * 8192 + 32 * (ks & 3));
-          mma_tf32(tmem, ad, bd, id, ks > 0 ? 1u : 0u);
+        for (int qd = 0; qd < 4; ++qd) {
+#pragma unroll
+          for (int ii = 0; ii < 2; ++ii) {
+            const int i = 2 * h + ii, k = warp + 8 * i, row = 32 * qd + lane;
+            const float2 v = h == 0 ? hv[qd][ii] : hv[qd][2 + ii];
+            *reinterpret_cast<float2*>(At + sw128(row, 2 * k - 32 * h)) =
+                make_float2(tf32_rna(v.x), tf32_rna(v.y));
+          }
         }
-        mma_commit(bar_w);
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+          tc_fence_after();
+          const uint32_t id = idesc_tf32(128, 64);
+          const uint32_t at = smem_u32(At), bt = smem_u32(Bt) + h * 8192;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma_tf32(tmem, desc_sw128(at + 32 * kk), desc_sw128(bt + 32 * kk), id,
+                     (h > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(bar_w);
+        }
+        ++wph;
       }
-      mbar_wait(bar_w, (uint32_t)(mt & 1), abort_flag);
+      mbar_wait(bar_w, (uint32_t)((wph - 1) & 1), abort_flag);
       tc_fence_after();
       {
         const int qa = warp & 3, h = warp >> 2;

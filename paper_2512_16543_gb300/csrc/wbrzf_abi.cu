@@ -224,20 +224,6 @@ bool tc_eligible(const wbrzf* h) {
   return h->prec == WBRZF_C64 && h->K <= 32 && (h->N % 2) == 0 && h->smem_tc > 0;
 }
 
-// H as a 2-D FP32 tensor {2N, batch K}, box {64, K} (32 antennas of every user).
-bool encode_hmap(const wbrzf* h, const void* H, CUtensorMap* map) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)2 * h->N, (cuuint64_t)h->batch * h->K};
-  const cuuint64_t strides[1] = {(cuuint64_t)8 * h->N};
-  const cuuint32_t box[2] = {64, (cuuint32_t)h->K};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(H), dims, strides, box,
-             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
-}
-
 bool use_blocked(const wbrzf* h) {
   return h->engine == WBRZF_ENGINE_BLOCKED || h->engine == WBRZF_ENGINE_BLOCKED_FMA ||
          (h->engine == WBRZF_ENGINE_AUTO && !h->simt_ok);
@@ -270,14 +256,12 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode,
     h->t += 1;
     return WBRZF_OK;
   }
-  bool use_tc = h->engine != WBRZF_ENGINE_SIMT && tc_eligible(h) &&
-                (reinterpret_cast<uintptr_t>(H) % 16) == 0;
-  alignas(64) CUtensorMap map;
-  if (use_tc && !encode_hmap(h, H, &map)) use_tc = false;
+  const bool use_tc = h->engine != WBRZF_ENGINE_SIMT && tc_eligible(h) &&
+                      (reinterpret_cast<uintptr_t>(H) % 16) == 0;
   if (h->engine == WBRZF_ENGINE_TENSOR && !use_tc) return WBRZF_ERR_UNSUPPORTED;
   if (h->timing && (e = cudaEventRecord(h->ev[0], h->stream)) != cudaSuccess) return cuda_fail(e);
   if (use_tc) {
-    e = launch_step_tc(make_args<float>(h, H, W, mode, active), &map, h->smem_tc, h->stream);
+    e = launch_step_tc(make_args<float>(h, H, W, mode, active), h->smem_tc, h->stream);
   } else if (h->prec == WBRZF_C128) {
     e = launch_step_f64(make_args<double>(h, H, W, mode, active), h->smem, h->stream);
   } else {
