@@ -247,7 +247,8 @@ int wbrzf_last_engine(const wbrzf* h);
  * waits for the last snapshot's events and writes six durations in milliseconds to the host
  * array ms_out: [0] Gram matrix and dG, [1] Algorithm 1, [2] Woodbury update, [3] direct
  * inverse, [4] SINR, sum-rate and precoder, [5] the whole snapshot.  On the single-CTA
- * engines every stage runs inside one kernel: [0]-[4] are -1 and only [5] is measured.
+ * engines every stage runs inside one kernel, and a snapshot replayed from a CUDA graph
+ * (wbrzf_set_graph) is timed as a whole: there [0]-[4] are -1 and only [5] is measured.
  * wbrzf_stage_times returns WBRZF_ERR_INVALID_ARG when timing is off or nothing has run.
  */
 wbrzf_status wbrzf_set_stage_timing(wbrzf* h, int enable);

@@ -159,6 +159,7 @@ struct wbrzf {
   bool simt_ok;          // the single-CTA kernel fits (K <= kMaxK and its shared memory)
   bool blocked_ok;       // the blocked engine's limits hold (workspace checked separately)
   bool timing;           // stage events recorded (wbrzf_set_stage_timing)
+  bool stages_recorded;  // the last step recorded all six events (not a graph replay)
   cudaEvent_t ev[6];
   // CUDA-graph replay of steps (wbrzf_set_graph): the step is captured on gstream once per
   // (mode, H, W, mask) and replayed while those stay the same
@@ -252,6 +253,7 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode,
     if (e != cudaSuccess) return cuda_fail(e);
     h->last_engine =
         h->engine == WBRZF_ENGINE_BLOCKED_FMA ? WBRZF_ENGINE_BLOCKED_FMA : WBRZF_ENGINE_BLOCKED;
+    h->stages_recorded = h->timing;
     h->launches += nl;
     h->t += 1;
     return WBRZF_OK;
@@ -270,6 +272,7 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode,
   if (e != cudaSuccess) return cuda_fail(e);
   if (h->timing && (e = cudaEventRecord(h->ev[5], h->stream)) != cudaSuccess) return cuda_fail(e);
   h->last_engine = use_tc ? WBRZF_ENGINE_TENSOR : WBRZF_ENGINE_SIMT;
+  h->stages_recorded = false;
   h->launches += 1;
   h->t += 1;
   return WBRZF_OK;
@@ -310,7 +313,10 @@ wbrzf_status run_any(wbrzf* h, const void* H, void* W, int mode, const unsigned 
     invalidate_graph(h);
     const long long l0 = h->launches;
     cudaGraphExec_t ex = nullptr;
+    const bool timing = h->timing;
+    h->timing = false;                 // timing events stay outside the graph
     wbrzf_status st = capture_step(h, h->gstream, H, W, mode, active, &ex);
+    h->timing = timing;
     if (st != WBRZF_OK) return st;
     h->gexec = ex;
     h->gH = H;
@@ -324,9 +330,12 @@ wbrzf_status run_any(wbrzf* h, const void* H, void* W, int mode, const unsigned 
     h->last_engine = h->glast_engine;
     h->t += 1;
   }
+  h->stages_recorded = false;
   cudaError_t e = cudaEventRecord(h->gev_in, h->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->gstream, h->gev_in, 0);
+  if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[0], h->gstream);
   if (e == cudaSuccess) e = cudaGraphLaunch(h->gexec, h->gstream);
+  if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[5], h->gstream);
   if (e == cudaSuccess) e = cudaEventRecord(h->gev_out, h->gstream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->gev_out, 0);
   return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
@@ -435,6 +444,7 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   h->simt_ok = simt_ok;
   h->blocked_ok = blocked_ok;
   h->timing = false;
+  h->stages_recorded = false;
   h->graph = false;
   h->gstream = nullptr;
   h->gev_in = h->gev_out = nullptr;
@@ -662,7 +672,7 @@ wbrzf_status wbrzf_stage_times(wbrzf* h, float* ms_out) {
   cudaError_t e = cudaEventSynchronize(h->ev[5]);
   if (e != cudaSuccess) return cuda_fail(e);
   for (int i = 0; i < 5; ++i) ms_out[i] = -1.0f;
-  if (h->last_engine == WBRZF_ENGINE_BLOCKED) {
+  if (h->stages_recorded) {
     for (int i = 0; i < 5; ++i) {
       e = cudaEventElapsedTime(&ms_out[i], h->ev[i], h->ev[i + 1]);
       if (e != cudaSuccess) return cuda_fail(e);
