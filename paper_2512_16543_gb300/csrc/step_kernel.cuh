@@ -343,6 +343,84 @@ __device__ void jacobi_round(cx<T>* E, cx<T>* U, int dmax, int d, int rnd, int* 
   __syncthreads();
 }
 
+// One-sided (Hestenes) cyclic Jacobi on the rows of B (d x K, ld K) by the kThreads threads of
+// a CTA.  Each round rotates the disjoint pairs of the round-robin ordering, one pair per
+// half-warp at a time: the half-warp forms the pair's block of E = B B^H, [[|b_p|^2, b_p b_q^H],
+// [., |b_q|^2]], by 16-lane shuffle sums over the K columns, takes that block's rotation
+// (jacobi_rotation) and applies it to rows p, q of B (B <- J^H B) and to columns p, q of U
+// (U <- U J); one barrier per round.  A pair with |b_p b_q^H|^2 <= tol2 tr(E)^2 is left alone
+// (tr(E) = ||B||_F^2 does not change under the rotations); the sweeps stop when a whole sweep
+// rotated nothing, so the off-diagonal energy of E ends below d^2 / 2 tol2 tr(E)^2.  At the end the rows of B are orthogonal, B = U^H B_in, and the squared row
+// norms are the eigenvalues of B_in B_in^H with eigenvectors the columns of U (U starts as I).
+// flags: two ints of shared scratch; red: the block_sum scratch.
+template <class T>
+__device__ void hestenes_jacobi(cx<T>* Bm, int K, cx<T>* U, int dmax, int d, T tol2,
+                                int max_sweeps, int* flags, T* red) {
+  const int tid = threadIdx.x, hw = tid >> 4, hl = tid & 15;
+  const unsigned hmask = 0xFFFFu << (tid & 16);
+  const int dd = d + (d & 1), npairs = dd >> 1, dm1 = dd - 1;
+  T part = 0;
+  for (int e = tid; e < d * K; e += kThreads) part += cabs2(Bm[e]);
+  const T tr = block_sum(part, red);
+  const T thr = tol2 * tr * tr;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int* const flag = flags + (sweep & 1);
+    if (tid == 0) *flag = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < dm1; ++rnd) {
+      for (int pk = hw; pk < npairs; pk += kThreads / 16) {   // pairs beyond 16 in turn
+        int p0, q0;
+        if (pk == 0) { p0 = 0; q0 = 1 + rnd; }
+        else {
+          int a1 = pk + rnd, a2 = dm1 - pk + rnd;
+          if (a1 >= dm1) a1 -= dm1;
+          if (a2 >= dm1) a2 -= dm1;
+          p0 = 1 + a1;
+          q0 = 1 + a2;
+        }
+        const int p = min(p0, q0), q = max(p0, q0);
+        if (q < d) {
+          cx<T>* const bp = Bm + (size_t)p * K;
+          cx<T>* const bq = Bm + (size_t)q * K;
+          T al = 0, be = 0;
+          cx<T> ga = cmk<T>(0, 0);
+          for (int k = hl; k < K; k += 16) {
+            const cx<T> x = bp[k], y = bq[k];
+            al += cabs2(x);
+            be += cabs2(y);
+            cfma_cj(ga, x, y);                        // b_p b_q^H
+          }
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(hmask, al, o);
+            be += __shfl_xor_sync(hmask, be, o);
+            ga.re += __shfl_xor_sync(hmask, ga.re, o);
+            ga.im += __shfl_xor_sync(hmask, ga.im, o);
+          }
+          T c, sn;
+          cx<T> f;
+          if (cabs2(ga) > thr && jacobi_rotation<T>(ga, al, be, c, sn, f)) {
+            const cx<T> fc = cconj(f);
+            for (int k = hl; k < K; k += 16) {    // rows: b_p <- c b_p - s conj(f) b_q, ...
+              const cx<T> x = bp[k], y = cmul(fc, bq[k]);
+              bp[k] = csub(cscale(x, c), cscale(y, sn));
+              bq[k] = cadd(cscale(x, sn), cscale(y, c));
+            }
+            for (int i = hl; i < d; i += 16) {    // U columns: u_p <- c u_p - s f u_q, ...
+              const cx<T> x = U[i * dmax + p], y = cmul(f, U[i * dmax + q]);
+              U[i * dmax + p] = csub(cscale(x, c), cscale(y, sn));
+              U[i * dmax + q] = cadd(cscale(x, sn), cscale(y, c));
+            }
+            if (hl == 0) *flag = 1;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (*flag == 0) break;           // (the flag of the next sweep is the other int)
+  }
+}
+
 // ------------------------------------------------------------------ phases 2-6
 // Given G_t in w.G (Hermitian, alpha on the diagonal), run the perturbation, the low-rank
 // step, the Woodbury update or direct inverse, the state write-back, the power scale and the
@@ -507,39 +585,28 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       // 3d. projection B = Q^H dG  (d x K)
       mm<T, true, false, MM_SET>(d, K, K, Q, dmax, D, K, Bm, K);
       __syncthreads();
-      // 3e. E = B B^H (d x d, Hermitian), eigen-decomposition by parallel cyclic Jacobi
-      mm<T, false, true, MM_SET>(d, d, K, Bm, K, Bm, K, Gy, dmax);
+      // 3e. svd(B): one-sided Jacobi on B's rows.  B becomes U^H B with orthogonal rows, its
+      // squared row norms are sigma_hat^2 and U's columns the left singular vectors.
+      // Converged when no pair has |b_p b_q^H|^2 above tol2 tr(B B^H)^2: FP32 1e-10 (the
+      // off-diagonal of E = B B^H then at most about 1e-4 of its trace for d <= 32, which
+      // leaves the eigenvalues -- the energy rule's input -- exact to second order, about
+      // 1e-8, and turns the singular vectors by about 1e-4, a change far below the FP32
+      // rounding of X once scaled by ||dG|| / ||G|| ~ 1e-5); FP64 1e-28.
       for (int e = tid; e < d * d; e += kThreads) {
         const int i = e / d, j = e - i * d;
         Uh[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
       }
       __syncthreads();
-      {
-        // converged when the off-diagonal energy is below eps of the total.  FP32: 1e-8, an
-        // off-diagonal norm of 1e-4 of E's, which leaves the eigenvalues (the energy rule's
-        // input) exact to second order, about 1e-8, and turns the eigenvectors by about 1e-4
-        // -- a change of that relative size in the low-rank part of dG, far below the FP32
-        // rounding of X once scaled by ||dG|| / ||G|| ~ 1e-5.  FP64: 1e-26.
-        const int dm1 = d + (d & 1) - 1;
-        const int max_sweeps = (sizeof(T) == 4) ? 12 : 20;
-        const T eps = (sizeof(T) == 4) ? T(1e-8) : T(1e-26);
-        for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-          T off = 0, tot = 0;
-          for (int e = tid; e < d * d; e += kThreads) {
-            const int i = e / d, j = e - i * d;
-            const T v = cabs2(Gy[i * dmax + j]);
-            tot += v;
-            if (i != j) off += v;
-          }
-          off = block_sum(off, red);
-          tot = block_sum(tot, red);
-          if (!(off > eps * tot)) break;
-          for (int rnd = 0; rnd < dm1; ++rnd)
-            jacobi_round<T, kThreads>(Gy, Uh, dmax, d, rnd, pp, pq, rc, rs, rph);
-        }
+      hestenes_jacobi<T>(Bm, K, Uh, dmax, d, (sizeof(T) == 4) ? T(1e-10) : T(1e-28),
+                         (sizeof(T) == 4) ? 12 : 20, misc + 4, red);
+      // 3f. sigma_hat^2 (squared row norms of the rotated B) sorted descending
+      for (int j = tid >> 4; j < d; j += kThreads / 16) {
+        T v = 0;
+        for (int k = tid & 15; k < K; k += 16) v += cabs2(Bm[j * K + k]);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFu << (tid & 16), v, o);
+        if ((tid & 15) == 0) lam[j] = v;
       }
-      // 3f. sigma_hat^2 (eigenvalues, clamped at 0) sorted descending
-      if (tid < d) lam[tid] = fmax(Gy[tid * dmax + tid].re, T(0));
       __syncthreads();
       if (tid < d) {
         const T v = lam[tid];
@@ -585,12 +652,10 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       Lm[i * rcap + c] = acc;
     }
     const T up = (T)ldexp(1.0, dg_exp);      // undo the scaling of dG: dG = L (up R^H)
+    // R^H = U_r^H B: the leading rows of the rotated B (which holds U^H B)
     for (int idx = tid; idx < r * K; idx += kThreads) {
       const int c = idx / K, j = idx - c * K;
-      const int pc = perm[c];
-      cx<T> acc = cmk<T>(0, 0);
-      for (int k = 0; k < d; ++k) cfma_jc(acc, Uh[k * dmax + pc], Bm[k * K + j]);
-      Rh[c * K + j] = cscale(acc, up);
+      Rh[c * K + j] = cscale(Bm[perm[c] * K + j], up);
     }
     __syncthreads();
     if (a.trace != nullptr) {
