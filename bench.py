@@ -70,7 +70,7 @@ RATE_GAP_BOUND = 0.05        # bit/s/Hz, mean |R_WB - R_full|
 # tensor-core step kernel on this workload, from the ncu capture summarised in
 # profiles/step_tc_kernel_batched_256x32.md; reported only while the kernel source is the one
 # the counters were taken on (sha256 of its four source files, first 16 hex digits).
-NCU_TRAFFIC = {"source_sha": "e5e09aa1ebc32f45", "bytes_per_launch": 119160064}
+NCU_TRAFFIC = {"source_sha": "8ad7760b568c8def", "bytes_per_launch": 116629504}
 KERNEL_SOURCES = ("step_common.cuh", "step_kernel.cuh", "step_tc.cuh", "tc_ptx.cuh")
 
 
@@ -794,38 +794,63 @@ def main():
                     "full": {k: statistics.mean(v) for k, v in stages_full.items()}}
         roofline = blocked_roofline(stage_ms["wb"], B, sc.N, sc.K)
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers: snapshot i + 1's H goes up on one
+    # copy stream and snapshot i - 1's W and sum-rates come down on another while snapshot i
+    # computes (two device buffers each; events order reuse)
     e2e = None
     if not args.no_e2e:
         Hh = Hs[1 + W_:1 + W_ + K_].cpu().pin_memory()
-        Wh = torch.empty(B, sc.N, sc.K, dtype=torch.complex64).pin_memory()
-        Rh = torch.empty(B, dtype=torch.float32).pin_memory()
+        Wh = torch.empty(2, B, sc.N, sc.K, dtype=torch.complex64).pin_memory()
+        Rh = torch.empty(2, B, dtype=torch.float32).pin_memory()
         h = make("wb", chosen)
-        Hd = torch.empty_like(Hs[0])
-        Wd = torch.empty(B, sc.N, sc.K, dtype=torch.complex64, device=dev)
-        Rd = torch.empty(B, dtype=torch.float32, device=dev)
-        h.full_inverse(Hs[0], Wd)
+        Hd = [torch.empty_like(Hs[0]) for _ in range(2)]
+        Wd = [torch.empty(B, sc.N, sc.K, dtype=torch.complex64, device=dev) for _ in range(2)]
+        Rd = [torch.empty(B, dtype=torch.float32, device=dev) for _ in range(2)]
+        h.full_inverse(Hs[0], Wd[0])
         for t in range(1, 1 + W_):
-            h.update(Hs[t], Wd)
+            h.update(Hs[t], Wd[0])
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        done_c, done_o = [], []
         e0.record(stream)
+        s_in.wait_event(e0)
+        s_out.wait_event(e0)
         for i in range(K_):
-            Hd.copy_(Hh[i], non_blocking=True)
-            h.update(Hd, Wd)
-            binding._check(binding.lib().wbrzf_sum_rate(h._h, None, Rd.data_ptr()), "sum_rate")
-            Wh.copy_(Wd, non_blocking=True)
-            Rh.copy_(Rd, non_blocking=True)
+            j = i % 2
+            if i >= 2:
+                s_in.wait_event(done_c[i - 2])          # H buffer j no longer read
+            with torch.cuda.stream(s_in):
+                Hd[j].copy_(Hh[i], non_blocking=True)
+            ev_in = torch.cuda.Event()
+            ev_in.record(s_in)
+            stream.wait_event(ev_in)
+            if i >= 2:
+                stream.wait_event(done_o[i - 2])        # W, R buffers j copied out
+            h.update(Hd[j], Wd[j])
+            binding._check(binding.lib().wbrzf_sum_rate(h._h, None, Rd[j].data_ptr()),
+                           "sum_rate")
+            done_c.append(torch.cuda.Event())
+            done_c[-1].record(stream)
+            s_out.wait_event(done_c[-1])
+            with torch.cuda.stream(s_out):
+                Wh[j].copy_(Wd[j], non_blocking=True)
+                Rh[j].copy_(Rd[j], non_blocking=True)
+            done_o.append(torch.cuda.Event())
+            done_o[-1].record(s_out)
+        stream.wait_stream(s_in)
+        stream.wait_stream(s_out)
         e1.record(stream)
         torch.cuda.synchronize()
         h.close()
         t_e2e = barrier_max(e0.elapsed_time(e1) / 1e3, world)
         e2e = {"value": world * B * K_ / t_e2e, "unit": "updates/s",
                "h2d_bytes_per_step": Hh[0].numel() * 8,
-               "d2h_bytes_per_step": Wh.numel() * 8 + Rh.numel() * 4}
+               "d2h_bytes_per_step": Wh[0].numel() * 8 + Rh[0].numel() * 4,
+               "overlap": "H2D, compute and D2H on three streams, double-buffered"}
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N = 1 only
     cpu = None
