@@ -85,6 +85,12 @@ __device__ __forceinline__ cx<double> box_muller(uint32_t xa, uint32_t xb, doubl
   return cmk(rad * cs, rad * sn);
 }
 
+// 2^e, and the exponent e of x = m 2^e with m in [0.5, 1) (0 for x = 0), in the type of the path
+__device__ __forceinline__ float pow2(int e, float) { return ldexpf(1.f, e); }
+__device__ __forceinline__ double pow2(int e, double) { return ldexp(1.0, e); }
+__device__ __forceinline__ int exponent_of(float x) { int e; frexpf(x, &e); return e; }
+__device__ __forceinline__ int exponent_of(double x) { int e; frexp(x, &e); return e; }
+
 // ------------------------------------------------------------------ cp.async
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
@@ -465,7 +471,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
   cx<T>* const Gsb = a.Gs + (size_t)b * KK;
   cx<T>* const Xsb = a.Xs + (size_t)b * KK;
   int branch;
-  double dg2 = 0.0;
+  T dgs = 0;           // ||dG||_F^2
   if (a.mode == MODE_UPDATE) {
     T s_dg = 0, s_g = 0;
     for (int idx = tid; idx < KK; idx += kThreads) {
@@ -476,11 +482,10 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       s_dg += cabs2(d);
       s_g += cabs2(g);
     }
-    const T dgs = block_sum(s_dg, red);
+    dgs = block_sum(s_dg, red);
     const T gs = block_sum(s_g, red);
-    dg2 = (double)dgs;
     if (a.period > 0 && (t % a.period) == 0) branch = WBRZF_BRANCH_PERIODIC;
-    else if (sqrt(dg2) <= a.dg_floor_rel * sqrt((double)gs)) branch = WBRZF_BRANCH_KEEP;
+    else if (sqrt(dgs) <= (T)a.dg_floor_rel * sqrt(gs)) branch = WBRZF_BRANCH_KEEP;
     else branch = -1;   // decided by the low-rank step
   } else {
     if (a.mode == MODE_INIT) {
@@ -496,11 +501,10 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
     // Bring dG to unit Frobenius norm by an exact power of two so that the squared
     // quantities of the sketch, CholQR and Jacobi steps stay far from FP32 underflow
     // whatever the scale of the channel; every result is rescaled exactly afterwards.
-    frexp(sqrt(dg2), &dg_exp);
-    const T down = (T)ldexp(1.0, -dg_exp);
+    dg_exp = exponent_of(sqrt(dgs));
+    const T down = pow2(-dg_exp, T(0));
     for (int idx = tid; idx < KK; idx += kThreads) D[idx] = cscale(D[idx], down);
     __syncthreads();
-    const double E_target = a.eta * ldexp(dg2, -2 * dg_exp);
     int k0 = a.k_init;
     bool met = false;
     for (int it = 0; it < a.i_max; ++it) {
@@ -598,7 +602,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       }
       __syncthreads();
       hestenes_jacobi<T>(Bm, K, Uh, dmax, d, (sizeof(T) == 4) ? T(1e-10) : T(1e-28),
-                         (sizeof(T) == 4) ? 12 : 20, misc + 4, red);
+                         (sizeof(T) == 4) ? 12 : 20, misc + 6, red);
       // 3f. sigma_hat^2 (squared row norms of the rotated B) sorted descending
       for (int j = tid >> 4; j < d; j += kThreads / 16) {
         T v = 0;
@@ -615,8 +619,11 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
         perm[rk] = tid;
       }
       __syncthreads();
-      // 3g. energy rule: smallest r with sum_{j <= r} sigma_j^2 >= eta ||dG||_F^2
+      // 3g. energy rule: smallest r with sum_{j <= r} sigma_j^2 >= eta ||dG||_F^2 (in the
+      // scaled units of dG); one thread decides, in FP64, and also takes the branch of eq. 12
+      // vs a direct inverse for the r it would return (all d components on the last pass)
       if (tid == 0) {
+        const double E_target = a.eta * ldexp((double)dgs, -2 * dg_exp);
         double cum = 0.0;
         int rf = 0;
         for (int j = 0; j < d; ++j) {
@@ -624,6 +631,9 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
           if (cum >= E_target) { rf = j + 1; break; }
         }
         misc[0] = rf;
+        const int rr = rf > 0 ? rf : d;
+        misc[4] = (rr > a.r_max || (double)rr / (double)K > a.switch_ratio)
+                      ? WBRZF_BRANCH_RANK : WBRZF_BRANCH_WOODBURY;
       }
       __syncthreads();
       iters = it + 1;
@@ -631,8 +641,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       k0 *= 2;
     }
     if (!met) r = d;    // fall-through: all d components of the last iteration
-    branch = (r > a.r_max || (double)r / (double)K > a.switch_ratio) ? WBRZF_BRANCH_RANK
-                                                                       : WBRZF_BRANCH_WOODBURY;
+    branch = misc[4];
     if (a.trace != nullptr) {
       T* tr = reinterpret_cast<T*>(a.trace + (size_t)b * a.trace_stride);
       for (int j = tid; j < dmax; j += kThreads)
@@ -651,7 +660,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       for (int k = 0; k < d; ++k) cfma(acc, Q[i * dmax + k], Uh[k * dmax + pc]);
       Lm[i * rcap + c] = acc;
     }
-    const T up = (T)ldexp(1.0, dg_exp);      // undo the scaling of dG: dG = L (up R^H)
+    const T up = pow2(dg_exp, T(0));         // undo the scaling of dG: dG = L (up R^H)
     // R^H = U_r^H B: the leading rows of the rotated B (which holds U^H B)
     for (int idx = tid; idx < r * K; idx += kThreads) {
       const int c = idx / K, j = idx - c * K;
@@ -893,7 +902,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
     inf.r = r;
     inf.iters = iters;
     inf.d = d;
-    inf.dg_fro2 = (float)dg2;
+    inf.dg_fro2 = (float)dgs;
     inf.scale = (float)s;
     inf.sum_rate = (float)R;
     inf.status = status;
