@@ -233,7 +233,9 @@ __device__ __forceinline__ void prefetch_state(const StepArgs<T>& a, int b, cx<T
 // s = t c; columns p, q of J are (c, -s f) and (s, c f) with f = e^{-i phi}.  Returns false
 // (identity) when E_pq is zero.  Single precision uses the hardware reciprocal square root:
 // dG is scaled to unit norm, so |E_pq|^2 below 1e-30 is negligible and dropped instead of
-// being squared into the denormal range.
+// being squared into the denormal range.  Any rotation that is orthogonal to working precision
+// serves (c = 1 / sqrt(1 + t^2) and s = t c keep c^2 + s^2 = 1 whatever t's rounding), so the
+// square root of 1 + tau^2 is taken from the reciprocal square root as well.
 template <class T>
 __device__ __forceinline__ bool jacobi_rotation(cx<T> bpq, T epp, T eqq, T& c, T& s,
                                                 cx<T>& f);
@@ -245,7 +247,10 @@ __device__ __forceinline__ bool jacobi_rotation<float>(cx<float> bpq, float epp,
   const float inv = rsqrtf(a2);
   f = cmk(bpq.re * inv, -bpq.im * inv);
   const float tau = (eqq - epp) * (0.5f * inv);
-  const float t = __fdividef(copysignf(1.f, tau), fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+  // sqrt(1 + tau^2) as v rsqrt(v); past 1e30 (tau^2 near overflow) it is |tau| to FP32
+  const float v = fmaf(tau, tau, 1.f);
+  const float rt = v < 1e30f ? v * rsqrtf(v) : fabsf(tau);
+  const float t = __fdividef(copysignf(1.f, tau), fabsf(tau) + rt);
   c = rsqrtf(fmaf(t, t, 1.f));
   s = t * c;
   return true;
@@ -349,78 +354,107 @@ __device__ void jacobi_round(cx<T>* E, cx<T>* U, int dmax, int d, int rnd, int* 
   __syncthreads();
 }
 
-// One-sided (Hestenes) cyclic Jacobi on the rows of B (d x K, ld K) by the kThreads threads of
-// a CTA.  Each round rotates the disjoint pairs of the round-robin ordering, one pair per
-// half-warp at a time: the half-warp forms the pair's block of E = B B^H, [[|b_p|^2, b_p b_q^H],
-// [., |b_q|^2]], by 16-lane shuffle sums over the K columns, takes that block's rotation
-// (jacobi_rotation) and applies it to rows p, q of B (B <- J^H B) and to columns p, q of U
-// (U <- U J); one barrier per round.  A pair with |b_p b_q^H|^2 <= tol2 tr(E)^2 is left alone
-// (tr(E) = ||B||_F^2 does not change under the rotations); the sweeps stop when a whole sweep
-// rotated nothing, so the off-diagonal energy of E ends below d^2 / 2 tol2 tr(E)^2.  At the end the rows of B are orthogonal, B = U^H B_in, and the squared row
-// norms are the eigenvalues of B_in B_in^H with eigenvectors the columns of U (U starts as I).
+// One-sided (Hestenes) cyclic Jacobi on the rows of B (d x K, ld K; K <= 8 EPL, d <= 64) by
+// the kThreads threads of a CTA.  Each round rotates the disjoint pairs of the round-robin
+// ordering at once, pair k on the eight lanes 8k .. 8k + 7: lane l holds columns l + 8 e
+// (e < EPL) of rows p and q in registers (the four groups of a warp start at different column
+// blocks, so their loads fall on different banks), the group forms the pair's block of
+// E = B B^H, [[|b_p|^2, b_p b_q^H], [., |b_q|^2]], by 8-lane shuffle sums, takes that block's
+// rotation (jacobi_rotation) and applies it to rows p, q of B (B <- J^H B) and to columns p, q
+// of U (U <- U J); one barrier per round.  A pair with |b_p b_q^H|^2 <= tol2 tr(E)^2 is left
+// alone (tr(E) = ||B||_F^2 does not change under the rotations); the sweeps stop when a whole
+// sweep rotated nothing, so the off-diagonal energy of E ends below d^2 / 2 tol2 tr(E)^2.  At
+// the end the rows of B are orthogonal, B = U^H B_in, and the squared row norms are the
+// eigenvalues of B_in B_in^H with eigenvectors the columns of U (U starts as I).
 // flags: two ints of shared scratch; red: the block_sum scratch.
-template <class T>
+template <class T, int EPL>
 __device__ void hestenes_jacobi(cx<T>* Bm, int K, cx<T>* U, int dmax, int d, T tol2,
                                 int max_sweeps, int* flags, T* red) {
-  const int tid = threadIdx.x, hw = tid >> 4, hl = tid & 15;
-  const unsigned hmask = 0xFFFFu << (tid & 16);
+  static_assert(kThreads / 8 >= 32, "one group of eight lanes per pair, d <= 64");
+  constexpr bool HOLD = false;   // rows kept in registers for the rotation (else re-read)
+  const int tid = threadIdx.x, pk = tid >> 3, l8 = tid & 7, grp = pk & 3;
   const int dd = d + (d & 1), npairs = dd >> 1, dm1 = dd - 1;
   T part = 0;
   for (int e = tid; e < d * K; e += kThreads) part += cabs2(Bm[e]);
   const T tr = block_sum(part, red);
   const T thr = tol2 * tr * tr;
+  // rows (p < q) of pair pk in round rnd: (0, 1 + rnd) and (1 + (pk + rnd) mod (dd - 1),
+  // 1 + (dd - 1 - pk + rnd) mod (dd - 1))
+  auto pair_of = [&](int rnd, int& p, int& q) {
+    int p0, q0;
+    if (pk == 0) { p0 = 0; q0 = 1 + rnd; }
+    else {
+      int a1 = pk + rnd, a2 = dm1 - pk + rnd;
+      if (a1 >= dm1) a1 -= dm1;
+      if (a2 >= dm1) a2 -= dm1;
+      p0 = 1 + a1;
+      q0 = 1 + a2;
+    }
+    p = min(p0, q0);
+    q = max(p0, q0);
+  };
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int* const flag = flags + (sweep & 1);
     if (tid == 0) *flag = 0;
     __syncthreads();
+    int p, q;
+    pair_of(0, p, q);
     for (int rnd = 0; rnd < dm1; ++rnd) {
-      for (int pk = hw; pk < npairs; pk += kThreads / 16) {   // pairs beyond 16 in turn
-        int p0, q0;
-        if (pk == 0) { p0 = 0; q0 = 1 + rnd; }
-        else {
-          int a1 = pk + rnd, a2 = dm1 - pk + rnd;
-          if (a1 >= dm1) a1 -= dm1;
-          if (a2 >= dm1) a2 -= dm1;
-          p0 = 1 + a1;
-          q0 = 1 + a2;
-        }
-        const int p = min(p0, q0), q = max(p0, q0);
-        if (q < d) {
-          cx<T>* const bp = Bm + (size_t)p * K;
-          cx<T>* const bq = Bm + (size_t)q * K;
-          T al = 0, be = 0;
-          cx<T> ga = cmk<T>(0, 0);
-          for (int k = hl; k < K; k += 16) {
-            const cx<T> x = bp[k], y = bq[k];
-            al += cabs2(x);
-            be += cabs2(y);
-            cfma_cj(ga, x, y);                        // b_p b_q^H
-          }
+      // whole warps run the sums and shuffles (full-warp masks: converged shuffles); a group
+      // without a pair this round sums zeros
+      if (4 * (tid >> 5) < npairs) {
+        const bool act = pk < npairs && q < d;     // uniform over the group
+        cx<T>* const bp = Bm + (size_t)(act ? p : 0) * K;
+        cx<T>* const bq = Bm + (size_t)(act ? q : 0) * K;
+        cx<T> x[EPL], y[EPL];
 #pragma unroll
-          for (int o = 8; o > 0; o >>= 1) {
-            al += __shfl_xor_sync(hmask, al, o);
-            be += __shfl_xor_sync(hmask, be, o);
-            ga.re += __shfl_xor_sync(hmask, ga.re, o);
-            ga.im += __shfl_xor_sync(hmask, ga.im, o);
-          }
-          T c, sn;
-          cx<T> f;
-          if (cabs2(ga) > thr && jacobi_rotation<T>(ga, al, be, c, sn, f)) {
-            const cx<T> fc = cconj(f);
-            for (int k = hl; k < K; k += 16) {    // rows: b_p <- c b_p - s conj(f) b_q, ...
-              const cx<T> x = bp[k], y = cmul(fc, bq[k]);
-              bp[k] = csub(cscale(x, c), cscale(y, sn));
-              bq[k] = cadd(cscale(x, sn), cscale(y, c));
+        for (int e = 0; e < EPL; ++e) {
+          int eb = e + grp;
+          if (eb >= EPL) eb -= EPL;
+          const int k = l8 + 8 * eb;
+          x[e] = (act && k < K) ? bp[k] : cmk<T>(0, 0);
+          y[e] = (act && k < K) ? bq[k] : cmk<T>(0, 0);
+        }
+        T al = 0, be = 0;
+        cx<T> ga = cmk<T>(0, 0);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          al += cabs2(x[e]);
+          be += cabs2(y[e]);
+          cfma_cj(ga, x[e], y[e]);                   // b_p b_q^H
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
+          ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
+        }
+        T c, sn;
+        cx<T> f;
+        if (act && cabs2(ga) > thr && jacobi_rotation<T>(ga, al, be, c, sn, f)) {
+          const cx<T> fc = cconj(f);
+#pragma unroll
+          for (int e = 0; e < EPL; ++e) {            // rows: b_p <- c b_p - s conj(f) b_q, ...
+            int eb = e + grp;
+            if (eb >= EPL) eb -= EPL;
+            const int k = l8 + 8 * eb;
+            if (k < K) {
+              const cx<T> xr = HOLD ? x[e] : bp[k];
+              const cx<T> yf = cmul(fc, HOLD ? y[e] : bq[k]);
+              bp[k] = csub(cscale(xr, c), cscale(yf, sn));
+              bq[k] = cadd(cscale(xr, sn), cscale(yf, c));
             }
-            for (int i = hl; i < d; i += 16) {    // U columns: u_p <- c u_p - s f u_q, ...
-              const cx<T> x = U[i * dmax + p], y = cmul(f, U[i * dmax + q]);
-              U[i * dmax + p] = csub(cscale(x, c), cscale(y, sn));
-              U[i * dmax + q] = cadd(cscale(x, sn), cscale(y, c));
-            }
-            if (hl == 0) *flag = 1;
           }
+          for (int i = l8; i < d; i += 8) {          // U columns: u_p <- c u_p - s f u_q, ...
+            const cx<T> u0 = U[i * dmax + p], u1 = cmul(f, U[i * dmax + q]);
+            U[i * dmax + p] = csub(cscale(u0, c), cscale(u1, sn));
+            U[i * dmax + q] = cadd(cscale(u0, sn), cscale(u1, c));
+          }
+          if (l8 == 0) *flag = 1;
         }
       }
+      pair_of(rnd + 1 < dm1 ? rnd + 1 : 0, p, q);   // the next round's pair, before the barrier
       __syncthreads();
     }
     if (*flag == 0) break;           // (the flag of the next sweep is the other int)
@@ -431,7 +465,8 @@ __device__ void hestenes_jacobi(cx<T>* Bm, int K, cx<T>* U, int dmax, int d, T t
 // Given G_t in w.G (Hermitian, alpha on the diagonal), run the perturbation, the low-rank
 // step, the Woodbury update or direct inverse, the state write-back, the power scale and the
 // SINR / sum-rate.  Leaves X in w.X and returns the precoder scale s.
-template <class T>
+// JEPL: columns of B per lane in the Jacobi step (K <= 8 JEPL).
+template <class T, int JEPL>
 __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
   // On entry for MODE_UPDATE, w.D holds G_{t-1} and w.X holds X_{t-1}: the kernels copy them
   // from the resident state with cp.async (prefetch_state) while the Gram matrix is formed.
@@ -601,15 +636,21 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
         Uh[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
       }
       __syncthreads();
-      hestenes_jacobi<T>(Bm, K, Uh, dmax, d, (sizeof(T) == 4) ? T(1e-10) : T(1e-28),
-                         (sizeof(T) == 4) ? 12 : 20, misc + 6, red);
+      {
+        const T tol2 = (sizeof(T) == 4) ? T(1e-10) : T(1e-28);
+        const int sweeps = (sizeof(T) == 4) ? 12 : 20;
+        if (JEPL == 4 || K <= 32) hestenes_jacobi<T, 4>(Bm, K, Uh, dmax, d, tol2, sweeps, misc + 6, red);
+        else hestenes_jacobi<T, JEPL>(Bm, K, Uh, dmax, d, tol2, sweeps, misc + 6, red);
+      }
       // 3f. sigma_hat^2 (squared row norms of the rotated B) sorted descending
-      for (int j = tid >> 4; j < d; j += kThreads / 16) {
+      for (int j0 = (tid >> 5) * 2; j0 < d; j0 += kThreads / 16) {   // warp-uniform loop
+        const int j = j0 + ((tid >> 4) & 1);
         T v = 0;
-        for (int k = tid & 15; k < K; k += 16) v += cabs2(Bm[j * K + k]);
+        if (j < d)
+          for (int k = tid & 15; k < K; k += 16) v += cabs2(Bm[j * K + k]);
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFu << (tid & 16), v, o);
-        if ((tid & 15) == 0) lam[j] = v;
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 15) == 0 && j < d) lam[j] = v;
       }
       __syncthreads();
       if (tid < d) {
@@ -983,7 +1024,8 @@ __global__ void __launch_bounds__(kThreads, 2) wbrzf_step_kernel(const StepArgs<
     __syncthreads();
   }
 
-  const T s = core_phases<T>(a, w, b);
+  static_assert(8 * 8 >= kMaxK, "Jacobi columns per lane");
+  const T s = core_phases<T, 8>(a, w, b);
   cx<T>* const X = w.X;
 
   // ---------------------------------------------------------------- 7. precoder W = s H^H X

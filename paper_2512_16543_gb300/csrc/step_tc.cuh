@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 4) wbrzf_step_tc_kernel(const StepAr
   cp_async_wait<0>();
   __syncthreads();
   const Work<float> w = carve_work<float>(uni, K, a.dmax, a.rcap, G, X, Dm);
-  const float s = core_phases<float>(a, w, b);
+  const float s = core_phases<float, 4>(a, w, b);   // K <= 32
   __syncthreads();
 
   // ------------------------------------------------------------ 7. W = s H^H X on tensor cores
@@ -191,8 +191,10 @@ __global__ void __launch_bounds__(kThreads, 4) wbrzf_step_tc_kernel(const StepAr
     unsigned char* const At = uni;              // one 16-user half: 128 rows x 128 B
     unsigned char* const Bt = sm + Ly.oGXD;     // 2 K-blocks x 64 rows x 128 B (G, dG dead)
     // B[(j, c')][(k, c)]: rows 2j (Re W), 2j + 1 (Im W); columns 2k (Re H), 2k + 1 (Im H)
+    // thread -> (row, chunk): consecutive lanes take consecutive rows of one chunk, so they
+    // read X[k][j] at consecutive j (one bank each) and fill the swizzled rows conflict-free
     for (int e = tid; e < 64 * 16; e += kThreads) {
-      const int row = e >> 4, qq = e & 15;            // 16 chunks of 4 floats per row
+      const int row = e & 63, qq = e >> 6;            // 16 chunks of 4 floats per row
       const int j = row >> 1, cre = row & 1;
       float v[4];
 #pragma unroll
@@ -213,6 +215,7 @@ __global__ void __launch_bounds__(kThreads, 4) wbrzf_step_tc_kernel(const StepAr
     const int nh = K > 16 ? 2 : 1;              // 16-user halves of the reduction
     int wph = 0;                                // precoder MMA commits so far
     cx<float>* const Wb = a.W + (size_t)b * N * K;
+    const bool w16 = (K & 1) == 0 && (reinterpret_cast<uintptr_t>(a.W) & 15) == 0;
     for (int mt = 0; mt < nmt; ++mt) {
       // H^T of this M-tile straight from global memory (H was read once in the Gram phase
       // and sits in L2): a thread's 16 loads are all in flight before the first is used.
@@ -265,10 +268,20 @@ __global__ void __launch_bounds__(kThreads, 4) wbrzf_step_tc_kernel(const StepAr
         tmem_ld32(tmem + ((uint32_t)(32 * qa) << 16) + (uint32_t)(32 * h), v);
         if (n < N) {
           cx<float>* wr = Wb + (size_t)n * K;
+          if (w16) {                   // user pairs are 16-byte aligned
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int j = 16 * h + jj;
-            if (j < K) wr[j] = cmk(v[2 * jj], v[2 * jj + 1]);
+            for (int m = 0; m < 8; ++m) {
+              const int j = 16 * h + 2 * m;
+              if (j < K)
+                *reinterpret_cast<float4*>(wr + j) =
+                    make_float4(v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int j = 16 * h + jj;
+              if (j < K) wr[j] = cmk(v[2 * jj], v[2 * jj + 1]);
+            }
           }
         }
       }
