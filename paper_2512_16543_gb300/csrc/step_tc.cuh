@@ -266,22 +266,36 @@ __global__ void __launch_bounds__(kThreads, 4) wbrzf_step_tc_kernel(const StepAr
         const int n = 128 * mt + 32 * qa + lane;
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(32 * qa) << 16) + (uint32_t)(32 * h), v);
-        if (n < N) {
-          cx<float>* wr = Wb + (size_t)n * K;
-          if (w16) {                   // user pairs are 16-byte aligned
+        if (w16) {
+          // W rows leave through the A half, free now that the tile's MMAs have completed:
+          // per 16-user half, the four warps holding it write their antennas' 128-byte rows
+          // (16-byte chunks rotated by row % 8: conflict-free), then every thread stores whole
+          // rows, eight threads to a row (full sectors)
+          float4* const st = reinterpret_cast<float4*>(At);
+          for (int hp = 0; hp < nh; ++hp) {
+            if (h == hp) {
+              const int row = 32 * qa + lane;
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-              const int j = 16 * h + 2 * m;
-              if (j < K)
-                *reinterpret_cast<float4*>(wr + j) =
+              for (int m = 0; m < 8; ++m)
+                st[row * 8 + (m ^ (row & 7))] =
                     make_float4(v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
             }
-          } else {
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const int j = 16 * h + jj;
-              if (j < K) wr[j] = cmk(v[2 * jj], v[2 * jj + 1]);
+            __syncthreads();
+            const int nc = min(16, K - 16 * hp) >> 1;     // user pairs in this half
+            for (int e = tid; e < 128 * 8; e += kThreads) {
+              const int row = e >> 3, c = e & 7, nn = 128 * mt + row;
+              if (c < nc && nn < N)
+                *reinterpret_cast<float4*>(Wb + (size_t)nn * K + 16 * hp + 2 * c) =
+                    st[row * 8 + (c ^ (row & 7))];
             }
+            __syncthreads();
+          }
+        } else if (n < N) {
+          cx<float>* wr = Wb + (size_t)n * K;
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = 16 * h + jj;
+            if (j < K) wr[j] = cmk(v[2 * jj], v[2 * jj + 1]);
           }
         }
       }
