@@ -115,7 +115,8 @@ constexpr uint32_t kTmemCols = 128;           // Gram D: 128 x 128; W D: 128 x 6
 //   GXD   G (K x K) at 0, dG right after it, X at the end of the region; after the SINR phase
 //         the first 16 KiB hold the B operand of the precoder product (G and dG are dead, X is
 //         read while B is written, so the region is at least 16 KiB + K^2 complex)
-//   union the Gram split tile (16 KiB) / Gram epilogue slices / SIMT workspace / one 16-user
+//   union the Gram split tile (16 KiB) / Gram epilogue slices (3 K (K + 1) complex) / SIMT
+//         workspace / one 16-user
 //         half of the precoder's A operand (16 KiB)
 struct TcLayout {
   size_t oGXD, gxd_bytes, oX, oUnion, oBar, bytes_unpadded, union_bytes;
@@ -134,7 +135,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int dmax, int rcap) {
   size_t u = 16384;                                       // split tile / A-operand half
   const size_t wk = work_bytes(K, dmax, rcap, false, 8, 4);
   if (wk > u) u = wk;
-  const size_t sl = 2 * (size_t)K * (K + 1) * 8;          // Gram epilogue: two padded slices
+  const size_t sl = 3 * (size_t)K * (K + 1) * 8;          // Gram epilogue: three padded slices
   if (sl > u) u = sl;
   L.union_bytes = align_up(u, 1024);
   o += L.union_bytes;

@@ -152,6 +152,7 @@ __device__ void mm(int m, int n, int kk, const cx<T>* A, int lda, const cx<T>* B
   for (int idx = threadIdx.x; idx < m * n; idx += kThreads) {
     const int i = idx / n, j = idx - i * n;
     cx<T> acc = cmk<T>(0, 0);
+#pragma unroll 4
     for (int k = 0; k < kk; ++k) {
       cx<T> a = AH ? cconj(A[k * lda + i]) : A[i * lda + k];
       cx<T> b = BH ? cconj(B[j * ldb + k]) : B[k * ldb + j];
@@ -893,6 +894,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       cx<T> acc[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] = cmk<T>(0, 0);
+#pragma unroll 4
       for (int k = 0; k < K; ++k) {
         const cx<T> xk = X[k * K + j];
 #pragma unroll
@@ -923,17 +925,26 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
   }
   const T wn2 = block_sum(part, red);
   const T s = sqrt(a.p_t / wn2);
+  // SINR_n = s^2 |M_nn|^2 / (s^2 sum_{i != n} |M_ni|^2 + sigma^2): warp w takes rows
+  // w, w + 8, ...; its lanes read a row's consecutive entries and sum them by shuffles
   T rate = 0;
-  if (tid < K) {
-    const int n = tid;
-    const T sig = s * s * cabs2(D[n * K + n]);
-    T intf = 0;
-    for (int i = 0; i < K; ++i)
-      if (i != n) intf += cabs2(D[n * K + i]);
-    intf *= s * s;
-    const T sinr = sig / (intf + sigma2);
-    a.sinr[(size_t)b * K + n] = (float)sinr;
-    rate = log2(T(1) + sinr);
+  {
+    const int wp = tid >> 5, ln = tid & 31;
+    for (int n = wp; n < K; n += kThreads / 32) {
+      T sig = 0, intf = 0;
+      for (int i = ln; i < K; i += 32) {
+        const T v = cabs2(D[n * K + i]);
+        if (i == n) sig = v;
+        else intf += v;
+      }
+      sig = warp_sum(sig);
+      intf = warp_sum(intf);
+      if (ln == 0) {
+        const T sinr = (s * s * sig) / (s * s * intf + sigma2);
+        a.sinr[(size_t)b * K + n] = (float)sinr;
+        rate += log2(T(1) + sinr);
+      }
+    }
   }
   const T R = block_sum(rate, red);
   if (!isfinite(s) || !isfinite(R)) status |= WBRZF_STATUS_NONFINITE;

@@ -132,50 +132,81 @@ __global__ void __launch_bounds__(kThreads, 4) wbrzf_step_tc_kernel(const StepAr
   mbar_wait(bar_mma, (uint32_t)((nblk - 1) & 1), abort_flag);
   tc_fence_after();
   {
-    // Gram epilogue.  Warp (quadrant qa = part a of the rows, half h) reads D rows 32a + k,
-    // column blocks 2h (a Re part) and 2h + 1 (an Im part).  Part a contributes
-    //   a even (Re_*): Re G += D[a][Re_*], Im G -= D[a][Im_*]
-    //   a odd  (Im_*): Re G += D[a][Im_*], Im G += D[a][Re_*]
-    // Each half h accumulates into its own padded slice, one quadrant after another (fixed
-    // order, so the result is deterministic); the two slices are then added.
+    // Gram epilogue.  D rows (quadrant a) and column blocks c are the parts Re_hi, Im_hi,
+    // Re_lo, Im_lo of H; with "Re" parts {0, 2} and "Im" parts {1, 3}
+    //   Re G = sum_{a, c Re} D[a][c] + sum_{a, c Im} D[a][c]
+    //   Im G = sum_{a Im, c Re} D[a][c] - sum_{a Re, c Im} D[a][c].
+    // Warp (qa, h) takes quadrant qa (its tensor-memory lanes) and component h (0: Re, 1: Im):
+    // the two column blocks that feed it, added in registers.  Quadrants 1-3 store their
+    // partial row into padded slices (write only, all at once); quadrant 0 then reads its
+    // partial from tensor memory, adds the three slices and leaves the sum in slice 1; the
+    // last pass copies it into G with the lower triangle taken from the upper (exactly
+    // Hermitian) and alpha on the diagonal.  Fixed order throughout: deterministic.
     const int qa = warp & 3, h = warp >> 2, k = lane;
     const int KS = K + 1;                  // padded row stride: spreads lanes over banks
-    float* slice = reinterpret_cast<float*>(uni) + (size_t)h * 2 * K * KS;   // re/im pairs
+    float* const slices = reinterpret_cast<float*>(uni);          // 3 x [K][KS] complex
+    const int PS = 2 * K * KS;                                     // floats per slice
     const bool odd = qa & 1;
-    for (int pass = 0; pass < 4; ++pass) {
-      if (qa == pass) {
-        for (int blk = 0; blk < 2; ++blk) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * qa) << 16) + (uint32_t)(64 * h + 32 * blk), v);
-          const int comp = (blk == 0) ? (odd ? 1 : 0) : (odd ? 0 : 1);   // 0: re, 1: im
-          const float sgn = (blk == 1 && !odd) ? -1.f : 1.f;
-          if (k < K) {
+    const int cb = (odd != (h == 1)) ? 1 : 0;                      // blocks cb and cb + 2
+    const float sgn = (!odd && h == 1) ? -1.f : 1.f;
+    const uint32_t ta = tmem + ((uint32_t)(32 * qa) << 16) + (uint32_t)(32 * cb);
+    // this warp's partial of row k, columns 16 half .. 16 half + 15
+    auto partial16 = [&](int half, float (&p)[16]) {
+      float w[16];
+      tmem_ld16(ta + 16 * half, p);
+      tmem_ld16(ta + 64 + 16 * half, w);
 #pragma unroll
-            for (int l = 0; l < 32; ++l) {
-              if (l < K) {
-                float* dst = slice + 2 * (k * KS + l) + comp;
-                *dst = (pass == 0 ? 0.f : *dst) + sgn * v[l];
-              }
-            }
+      for (int l = 0; l < 16; ++l) p[l] = sgn * (p[l] + w[l]);
+    };
+    if (qa > 0) {
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float p[16];
+        partial16(half, p);
+        if (k < K) {
+          float* const dst = slices + (qa - 1) * PS + 2 * k * KS + h;
+#pragma unroll
+          for (int l = 0; l < 16; ++l)
+            if (16 * half + l < K) dst[2 * (16 * half + l)] = p[l];
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (qa == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float p[16];
+        partial16(half, p);
+        if (k < K) {
+          float* const s1 = slices + 2 * k * KS + h;
+          float o[16];
+#pragma unroll
+          for (int l = 0; l < 16; ++l) {
+            const int c = 16 * half + l;
+            o[l] = c < K ? (s1[2 * c] + s1[PS + 2 * c]) + s1[2 * PS + 2 * c] : 0.f;
+          }
+#pragma unroll
+          for (int l = 0; l < 16; ++l) {
+            const int c = 16 * half + l;
+            if (c < K) s1[2 * c] = p[l] + o[l];
           }
         }
       }
-      __syncthreads();
     }
     tc_fence_before();
-    const cx<float>* sl = reinterpret_cast<const cx<float>*>(uni);
-    const int PS = K * KS;
-    for (int idx = tid; idx < KK; idx += kThreads) {
-      const int kr = idx / K, o = kr * KS + (idx - kr * K);
-      G[idx] = cadd(sl[o], sl[PS + o]);
-    }
     __syncthreads();
-    for (int idx = tid; idx < KK; idx += kThreads) {
-      const int kr = idx / K, l = idx - kr * K;
-      if (kr > l) G[idx] = cconj(G[l * K + kr]);
+    {
+      const cx<float>* const sl = reinterpret_cast<const cx<float>*>(slices);
+      const float al = a.alpha[b];
+      for (int idx = tid; idx < KK; idx += kThreads) {
+        const int kr = idx / K, l = idx - kr * K;
+        cx<float> g = kr <= l ? sl[kr * KS + l] : cconj(sl[l * KS + kr]);
+        if (kr == l) g = cmk(g.re + al, 0.f);
+        G[idx] = g;
+      }
     }
-    __syncthreads();
-    if (tid < K) G[tid * K + tid] = cmk(G[tid * K + tid].re + a.alpha[b], 0.f);
     __syncthreads();
   }
 
