@@ -11,6 +11,7 @@ namespace wbk {
 constexpr int kThreads = 256;     // threads per CTA of the per-snapshot kernel
 constexpr int kMaxK = 64;         // largest K the single-CTA kernel supports
 constexpr int kChunk = 32;        // antenna columns of H staged per pipeline stage
+constexpr int kCqRegs = 10;       // sketch widths d up to this run CholQR from registers
 
 enum StepMode : int { MODE_UPDATE = 0, MODE_INIT = 1, MODE_FULL = 2 };
 

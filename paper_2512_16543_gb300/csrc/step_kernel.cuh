@@ -19,6 +19,8 @@
 #pragma once
 #include <math.h>
 
+#include <utility>
+
 #include "step_common.cuh"
 
 namespace wbk {
@@ -363,11 +365,12 @@ __device__ void jacobi_round(cx<T>* E, cx<T>* U, int dmax, int d, int rnd, int* 
 // E = B B^H, [[|b_p|^2, b_p b_q^H], [., |b_q|^2]], by 8-lane shuffle sums, takes that block's
 // rotation (jacobi_rotation) and applies it to rows p, q of B (B <- J^H B) and to columns p, q
 // of U (U <- U J); one barrier per round.  A pair with |b_p b_q^H|^2 <= tol2 tr(E)^2 is left
-// alone (tr(E) = ||B||_F^2 does not change under the rotations); the sweeps stop when a whole
-// sweep rotated nothing, so the off-diagonal energy of E ends below d^2 / 2 tol2 tr(E)^2.  At
+// alone (tr(E) = ||B||_F^2 does not change under the rotations); the rounds stop once every
+// pair has been left alone since the last rotation, so the off-diagonal energy of E ends below
+// d^2 / 2 tol2 tr(E)^2.  At
 // the end the rows of B are orthogonal, B = U^H B_in, and the squared row norms are the
 // eigenvalues of B_in B_in^H with eigenvectors the columns of U (U starts as I).
-// flags: two ints of shared scratch; red: the block_sum scratch.
+// flags: three ints of shared scratch; red: the block_sum scratch.
 template <class T, int EPL>
 __device__ void hestenes_jacobi(cx<T>* Bm, int K, cx<T>* U, int dmax, int d, T tol2,
                                 int max_sweeps, int* flags, T* red) {
@@ -394,16 +397,23 @@ __device__ void hestenes_jacobi(cx<T>* Bm, int K, cx<T>* U, int dmax, int d, T t
     p = min(p0, q0);
     q = max(p0, q0);
   };
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    int* const flag = flags + (sweep & 1);
-    if (tid == 0) *flag = 0;
-    __syncthreads();
-    int p, q;
-    pair_of(0, p, q);
-    for (int rnd = 0; rnd < dm1; ++rnd) {
+  // Every dm1 consecutive rounds visit every pair once, so dm1 consecutive rounds without a
+  // rotation mean no pair is above the threshold: stop there (or after max_sweeps sweeps).
+  // Round it sets flags[it % 3]; thread 0 clears flags[(it + 1) % 3], last read before the
+  // previous barrier, for the next round.
+  if (tid < 3) flags[tid] = 0;
+  __syncthreads();
+  // Only the warps that hold pairs take part (four pairs per warp); they meet at a named
+  // barrier of their own each round and the others wait at the closing barrier.
+  const int nwp = (npairs + 3) >> 2;
+  int p, q, rnd = 0, quiet = 0;
+  pair_of(0, p, q);
+  for (int it = 0; (tid >> 5) < nwp && it < max_sweeps * dm1; ++it) {
+    int* const flag = flags + it % 3;
+    {
       // whole warps run the sums and shuffles (full-warp masks: converged shuffles); a group
       // without a pair this round sums zeros
-      if (4 * (tid >> 5) < npairs) {
+      {
         const bool act = pk < npairs && q < d;     // uniform over the group
         cx<T>* const bp = Bm + (size_t)(act ? p : 0) * K;
         cx<T>* const bq = Bm + (size_t)(act ? q : 0) * K;
@@ -455,10 +465,90 @@ __device__ void hestenes_jacobi(cx<T>* Bm, int K, cx<T>* U, int dmax, int d, T t
           if (l8 == 0) *flag = 1;
         }
       }
-      pair_of(rnd + 1 < dm1 ? rnd + 1 : 0, p, q);   // the next round's pair, before the barrier
-      __syncthreads();
+      if (tid == 0) flags[(it + 1) % 3] = 0;
+      rnd = rnd + 1 < dm1 ? rnd + 1 : 0;
+      pair_of(rnd, p, q);                            // the next round's pair, before the barrier
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * nwp) : "memory");
     }
-    if (*flag == 0) break;           // (the flag of the next sweep is the other int)
+    if (*flag) quiet = 0;
+    else if (++quiet >= dm1) break;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ CholQR steps, d <= DM
+// Right-looking Cholesky Gy = R^H R of the d x d Gram matrix (upper triangle, ld dmax) on warp
+// 0 with lane c holding column c in registers: step j takes the pivot from lane j and row j
+// of R from lanes j+1.. by shuffles, so the d steps need no shared-memory round trip.  Same
+// pivot test, column drop and results as the shared-memory form (cn: the column's diagonal
+// before the factorisation; drop: persistent drop flags; rs: 1 / R_jj, 0 for a dropped
+// column, whose row of R becomes zero).  The steps are expanded at compile time (index
+// sequence), so the column stays in registers; steps j >= d return at once.
+template <class T, int DM, int J>
+__device__ __forceinline__ void cholesky_step(cx<T> (&g)[DM], int& dropl, T cnl, int d,
+                                              int* drop, T* rs, T tol_rel) {
+  if (J >= d) return;                                              // warp-uniform
+  const int cl = threadIdx.x;
+  const T piv = __shfl_sync(0xffffffffu, g[J].re, J);
+  const T cnj = __shfl_sync(0xffffffffu, cnl, J);
+  const int d0 = __shfl_sync(0xffffffffu, dropl, J);
+  const bool dj = d0 || !(cnj > T(0)) || !(piv > tol_rel * cnj) || !isfinite(piv);
+  T rinv;
+  if constexpr (sizeof(T) == 4) rinv = dj ? 0.f : rsqrtf(piv);
+  else rinv = dj ? 0.0 : 1.0 / sqrt(piv);
+  if (cl == J) dropl = dj ? 1 : 0;
+  if (cl == 0) { drop[J] = dj ? 1 : 0; rs[J] = rinv; }
+  g[J] = cl >= J ? cscale(g[J], rinv) : cmk<T>(0, 0);             // row J of R
+#pragma unroll
+  for (int a = J + 1; a < DM; ++a) {
+    const cx<T> rja = cmk<T>(__shfl_sync(0xffffffffu, g[J].re, a),
+                             __shfl_sync(0xffffffffu, g[J].im, a));
+    if (cl >= a) cfma_jc(g[a], cscale(rja, T(-1)), g[J]);          // G_ac -= conj(R_Ja) R_Jc
+  }
+}
+template <class T, int DM, int... J>
+__device__ __forceinline__ void cholesky_steps(cx<T> (&g)[DM], int& dropl, T cnl, int d,
+                                               int* drop, T* rs, T tol_rel,
+                                               std::integer_sequence<int, J...>) {
+  (cholesky_step<T, DM, J>(g, dropl, cnl, d, drop, rs, tol_rel), ...);
+}
+template <class T, int DM>
+__device__ __forceinline__ void cholesky_regs(cx<T>* Gy, int dmax, int d, int* drop, T* rs,
+                                              T tol_rel) {
+  const int cl = threadIdx.x;
+  cx<T> g[DM];
+#pragma unroll
+  for (int a = 0; a < DM; ++a)
+    g[a] = (a < d && cl < d && a <= cl) ? Gy[a * dmax + cl] : cmk<T>(0, 0);
+  const T cnl = cl < d ? Gy[cl * dmax + cl].re : T(0);
+  int dropl = cl < d ? drop[cl] : 1;
+  cholesky_steps<T, DM>(g, dropl, cnl, d, drop, rs, tol_rel, std::make_integer_sequence<int, DM>{});
+#pragma unroll
+  for (int a = 0; a < DM; ++a)
+    if (a < d && cl < d && a <= cl) Gy[a * dmax + cl] = g[a];
+}
+
+// Q <- Q R^{-1} for the K rows of Q (ld dmax), one row per thread of warp 0 (K <= 32):
+// right-looking, q_c = acc_c / R_cc and acc_c' -= q_c R_cc' for c' > c, with the running
+// sums in registers.  Rows of R of dropped columns are zero and rs[c] = 0 for them.
+template <class T, int DM>
+__device__ __forceinline__ void fwd_subst_regs(cx<T>* Q, int dmax, int d, int K,
+                                               const cx<T>* Gy, const T* rs) {
+  const int i = threadIdx.x;
+  if (i >= K) return;
+  cx<T>* const qi = Q + i * dmax;
+  cx<T> acc[DM];
+#pragma unroll
+  for (int c = 0; c < DM; ++c) acc[c] = c < d ? qi[c] : cmk<T>(0, 0);
+#pragma unroll
+  for (int c = 0; c < DM; ++c) {
+    if (c < d) {
+      const cx<T> qc = cscale(acc[c], rs[c]);
+      qi[c] = qc;
+#pragma unroll
+      for (int c2 = c + 1; c2 < DM; ++c2)
+        if (c2 < d) cfma(acc[c2], cscale(qc, T(-1)), Gy[c * dmax + c2]);
+    }
   }
 }
 
@@ -568,6 +658,13 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       for (int pass = 0; pass < 2; ++pass) {
         mm<T, true, false, MM_SET>(d, d, K, Q, dmax, Q, dmax, Gy, dmax);   // Y^H Y
         __syncthreads();
+        if (d <= kCqRegs && K <= 32) {
+          if (tid < 32) cholesky_regs<T, kCqRegs>(Gy, dmax, d, drop, rs, tol_rel);
+          __syncthreads();
+          if (tid < 32) fwd_subst_regs<T, kCqRegs>(Q, dmax, d, K, Gy, rs);
+          __syncthreads();
+          continue;
+        }
         if (tid < 32) {   // one warp factors the d x d Gram matrix; lane c owns column c
           const int cl = tid;
           if (cl < d) cn[cl] = Gy[cl * dmax + cl].re;
@@ -627,18 +724,19 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       __syncthreads();
       // 3e. svd(B): one-sided Jacobi on B's rows.  B becomes U^H B with orthogonal rows, its
       // squared row norms are sigma_hat^2 and U's columns the left singular vectors.
-      // Converged when no pair has |b_p b_q^H|^2 above tol2 tr(B B^H)^2: FP32 1e-10 (the
-      // off-diagonal of E = B B^H then at most about 1e-4 of its trace for d <= 32, which
-      // leaves the eigenvalues -- the energy rule's input -- exact to second order, about
-      // 1e-8, and turns the singular vectors by about 1e-4, a change far below the FP32
-      // rounding of X once scaled by ||dG|| / ||G|| ~ 1e-5); FP64 1e-28.
+      // Converged when no pair has |b_p b_q^H|^2 above tol2 tr(B B^H)^2: FP32 1e-8 (each
+      // off-diagonal entry of E = B B^H then at most 1e-4 of its trace, which leaves the
+      // eigenvalues -- the energy rule's input -- exact to second order, about 1e-8 relative
+      // to their gaps, and turns the singular vectors by about 1e-4; the Woodbury correction
+      // is ||dG|| / ||G|| ~ 1e-5 of X, so that moves X by about 1e-9 relative, far below its
+      // FP32 rounding); FP64 1e-28.
       for (int e = tid; e < d * d; e += kThreads) {
         const int i = e / d, j = e - i * d;
         Uh[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
       }
       __syncthreads();
       {
-        const T tol2 = (sizeof(T) == 4) ? T(1e-10) : T(1e-28);
+        const T tol2 = (sizeof(T) == 4) ? T(1e-8) : T(1e-28);
         const int sweeps = (sizeof(T) == 4) ? 12 : 20;
         if (JEPL == 4 || K <= 32) hestenes_jacobi<T, 4>(Bm, K, Uh, dmax, d, tol2, sweeps, misc + 6, red);
         else hestenes_jacobi<T, JEPL>(Bm, K, Uh, dmax, d, tol2, sweeps, misc + 6, red);
