@@ -512,6 +512,182 @@ __global__ void __launch_bounds__(256) rank_kernel(const StepArgs<T> a, const Bu
   }
 }
 
+// Fused Algorithm 1 iterations (K <= 128, the leading nf iterations, whose sketch widths fit
+// the shared-memory layout of width df): one CTA of kThreads threads per instance runs them
+// with the one-CTA engines' device code -- Omega from the same Philox counters, Y = 2^-e dG
+// Omega and B = Q^H 2^-e dG with dG streamed from global memory in 16-wide chunks, CholQR2,
+// the one-sided Jacobi on B's rows (B <- U^H B; U accumulated) and the energy rule -- in
+// place of a dozen batched launches per iteration.  It leaves what the per-step kernels leave
+// for the Woodbury stage: the control words, perm, lam, the trace, the unrotated B, and for a
+// Woodbury instance Q and U_r.  An instance still short of its target after the nf
+// iterations stays active and continues on the per-step kernels.
+template <class T, int EPL>
+__global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs<T> a,
+                                                                  const Bufs<T> w, int nf,
+                                                                  int df) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int b = blockIdx.x, tid = threadIdx.x, K = a.K, dmax = w.dmax, rcap = w.rcap;
+  if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
+  const FusedLayout F = fused_layout(K, df, sizeof(cx<T>), sizeof(T));
+  cx<T>* const Om = reinterpret_cast<cx<T>*>(sm + F.oOm);
+  cx<T>* const Q = reinterpret_cast<cx<T>*>(sm + F.oQ);
+  cx<T>* const Bm = reinterpret_cast<cx<T>*>(sm + F.oB);
+  cx<T>* const S = reinterpret_cast<cx<T>*>(sm + F.oS);
+  cx<T>* const Gy = reinterpret_cast<cx<T>*>(sm + F.oGy);
+  cx<T>* const Uh = reinterpret_cast<cx<T>*>(sm + F.oUh);
+  T* const lam = reinterpret_cast<T*>(sm + F.oLam);
+  T* const rs = reinterpret_cast<T*>(sm + F.oRs);
+  T* const cn = reinterpret_cast<T*>(sm + F.oCn);
+  T* const red = reinterpret_cast<T*>(sm + F.oRed);
+  int* const perm = reinterpret_cast<int*>(sm + F.oPerm);
+  int* const drop = reinterpret_cast<int*>(sm + F.oDrop);
+  int* const flags = reinterpret_cast<int*>(sm + F.oFlags);
+  const cx<T>* const D = w.D + (size_t)b * w.L.sD;
+  const T dsc = w.dsc[b];
+  int* const ctl = w.ctl + 8 * b;
+  const uint32_t id = a.ids[b];
+  const int t = step_index(a, b);
+  const T tol_rel = (sizeof(T) == 4) ? T(1e-4) : T(1e-12);
+  const T tol2 = (sizeof(T) == 4) ? T(1e-8) : T(1e-28);
+  const int sweeps = (sizeof(T) == 4) ? 12 : 20;
+  long long k0 = a.k_init;
+  for (int it = 0; it < nf; ++it) {
+    const int d = (int)(k0 + a.p < K ? k0 + a.p : K);
+    const bool last = it == a.i_max - 1;
+    // Omega: entry (i, j) from counter (i, j/2, t, 16 id + it)
+    const int nq = (d + 1) >> 1;
+    for (int e = tid; e < K * nq; e += kThreads) {
+      const int i = e / nq, q = e - i * nq;
+      const uint4 x = philox4x32_10(
+          make_uint4((uint32_t)i, (uint32_t)q, (uint32_t)t, 16u * id + (uint32_t)it),
+          a.seed_lo, a.seed_hi);
+      Om[i * df + 2 * q] = box_muller(x.x, x.y, T(0));
+      if (2 * q + 1 < d) Om[i * df + 2 * q + 1] = box_muller(x.z, x.w, T(0));
+    }
+    __syncthreads();
+    // Y = 2^-e dG Omega (K x d, ld df): dG by 16-column chunks through S (K x 16)
+    for (int c0 = 0; c0 < K; c0 += 16) {
+      for (int e = tid; e < K * 16; e += kThreads) {
+        const int i = e >> 4, k = c0 + (e & 15);
+        S[e] = k < K ? D[(size_t)i * K + k] : cmk<T>(0, 0);
+      }
+      __syncthreads();
+      const int kn = min(16, K - c0);
+      for (int o = tid; o < K * d; o += kThreads) {
+        const int i = o / d, c = o - i * d;
+        cx<T> acc = c0 == 0 ? cmk<T>(0, 0) : Q[i * df + c];
+        for (int kk = 0; kk < kn; ++kk) cfma(acc, S[i * 16 + kk], Om[(c0 + kk) * df + c]);
+        Q[i * df + c] = c0 + 16 >= K ? cscale(acc, dsc) : acc;
+      }
+      __syncthreads();
+    }
+    // Q = orth(Y): CholQR twice, numerically dependent columns dropped
+    if (tid < d) drop[tid] = 0;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      mm<T, true, false, MM_SET>(d, d, K, Q, df, Q, df, Gy, df);      // Q^H Q
+      __syncthreads();
+      cholqr_pass_smem<T>(Q, df, K, d, Gy, df, drop, rs, cn, tol_rel);
+    }
+    // B = 2^-e Q^H dG (d x K, ld K): dG by 16-row chunks through S (16 x K); the unrotated B
+    // (rows >= d zero) goes to the global buffer the Woodbury products read
+    for (int r0 = 0; r0 < K; r0 += 16) {
+      for (int e = tid; e < 16 * K; e += kThreads) {
+        const int i = r0 + e / K;
+        S[e] = i < K ? D[(size_t)i * K + (e - (e / K) * K)] : cmk<T>(0, 0);
+      }
+      __syncthreads();
+      const int in = min(16, K - r0);
+      for (int o = tid; o < d * K; o += kThreads) {
+        const int c = o / K, j = o - c * K;
+        cx<T> acc = r0 == 0 ? cmk<T>(0, 0) : Bm[o];
+        for (int ii = 0; ii < in; ++ii) cfma_jc(acc, Q[(r0 + ii) * df + c], S[ii * K + j]);
+        Bm[o] = r0 + 16 >= K ? cscale(acc, dsc) : acc;
+      }
+      __syncthreads();
+    }
+    {
+      cx<T>* const Bg = w.Bm + (size_t)b * w.L.sBm;
+      for (int o = tid; o < dmax * K; o += kThreads) Bg[o] = o < d * K ? Bm[o] : cmk<T>(0, 0);
+    }
+    // svd(B): one-sided Jacobi on B's rows; U (d x d, ld df) starts as I
+    for (int e = tid; e < d * d; e += kThreads) {
+      const int i = e / d, j = e - i * d;
+      Uh[i * df + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
+    }
+    __syncthreads();
+    hestenes_jacobi<T, EPL>(Bm, K, Uh, df, d, tol2, sweeps, flags, red);
+    // sigma_hat^2 (squared row norms of the rotated B), sorted descending
+    for (int j0 = (tid >> 5) * 2; j0 < d; j0 += kThreads / 16) {   // warp-uniform loop
+      const int j = j0 + ((tid >> 4) & 1);
+      T v = 0;
+      if (j < d)
+        for (int k = tid & 15; k < K; k += 16) v += cabs2(Bm[j * K + k]);
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((tid & 15) == 0 && j < d) lam[j] = v;
+    }
+    __syncthreads();
+    if (tid < d) {
+      const T v = lam[tid];
+      int rk = 0;
+      for (int i = 0; i < d; ++i) rk += (lam[i] > v || (lam[i] == v && i < tid)) ? 1 : 0;
+      perm[rk] = tid;
+    }
+    __syncthreads();
+    // energy rule (eq. 14) and Algorithm 2's test, as rank_kernel
+    if (tid == 0) {
+      double cum = 0.0;
+      int rf = 0;
+      for (int j = 0; j < d; ++j) {
+        cum += (double)lam[perm[j]];
+        if (cum >= w.et[b]) { rf = j + 1; break; }
+      }
+      int rw = -1;
+      if (rf > 0 || last) {
+        const int r = rf > 0 ? rf : d;
+        ctl[C_R] = r;
+        ctl[C_D] = d;
+        ctl[C_ITERS] = it + 1;
+        ctl[C_ACTIVE] = 0;
+        const bool wb = !(r > a.r_max || (double)r / (double)a.K > a.switch_ratio);
+        ctl[C_BRANCH] = wb ? WBRZF_BRANCH_WOODBURY : WBRZF_BRANCH_RANK;
+        rw = wb ? r : -1;
+        if (a.trace != nullptr) {
+          T* tr = reinterpret_cast<T*>(a.trace + (size_t)b * a.trace_stride);
+          const int e2 = 2 * ctl[C_EXP];
+          for (int j = 0; j < dmax; ++j) tr[j] = (j < d) ? (T)ldexp((double)lam[perm[j]], e2) : T(0);
+        }
+      } else {
+        ctl[C_K0] *= 2;
+      }
+      for (int j = 0; j < d; ++j) {
+        w.perm[(size_t)b * dmax + j] = perm[j];
+        w.lam[(size_t)b * dmax + j] = lam[j];
+      }
+      flags[4] = rw;
+      flags[5] = (rf > 0 || last) ? 1 : 0;
+    }
+    __syncthreads();
+    const int r = flags[4], decided = flags[5];
+    if (r >= 0) {   // Woodbury: U_r = U[:, perm[0..r)] (dmax x rcap) and Q (K x dmax)
+      cx<T>* const Ur = w.Ur + (size_t)b * w.L.sUr;
+      for (int e = tid; e < dmax * rcap; e += kThreads) {
+        const int i = e / rcap, c = e - i * rcap;
+        Ur[e] = (i < d && c < r) ? Uh[i * df + perm[c]] : cmk<T>(0, 0);
+      }
+      cx<T>* const Qg = w.Q + (size_t)b * w.L.sOm;
+      for (int e = tid; e < K * dmax; e += kThreads) {
+        const int i = e / dmax, c = e - i * dmax;
+        Qg[e] = c < d ? Q[i * df + c] : cmk<T>(0, 0);
+      }
+    }
+    if (decided) return;
+    __syncthreads();
+    if (k0 < K) k0 *= 2;
+  }
+}
+
 // Capacitance matrix: Cm <- (I + Cm)^{-1} on the leading r x r block (r = the instance's rank;
 // the rest of the rcap x rcap buffer becomes zero, as T and Z vanish there) by Gauss-Jordan
 // with partial pivoting; a numerically singular pivot sends the instance to the direct
@@ -763,6 +939,24 @@ __global__ void __launch_bounds__(256) sinr_final_kernel(const StepArgs<T> a, co
   }
 }
 
+template <class T>
+cudaError_t launch_arsvd_fused(const StepArgs<T>& a, const Bufs<T>& w, int nf, int df,
+                               cudaStream_t s) {
+  const int bytes = (int)fused_layout(a.K, df, sizeof(cx<T>), sizeof(T)).bytes;
+  cudaError_t e;
+  if (a.K <= 32) {
+    e = cudaFuncSetAttribute(arsvd_fused_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) arsvd_fused_kernel<T, 4><<<a.batch, kThreads, bytes, s>>>(a, w, nf, df);
+  } else if (a.K <= 64) {
+    e = cudaFuncSetAttribute(arsvd_fused_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) arsvd_fused_kernel<T, 8><<<a.batch, kThreads, bytes, s>>>(a, w, nf, df);
+  } else {
+    e = cudaFuncSetAttribute(arsvd_fused_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) arsvd_fused_kernel<T, 16><<<a.batch, kThreads, bytes, s>>>(a, w, nf, df);
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- the snapshot sequence
 template <class T>
 cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t s, int* launches,
@@ -812,7 +1006,27 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
   if ((e = mark(1)) != cudaSuccess) return e;
   if (a.mode == MODE_UPDATE) {
     long long k0 = a.k_init;
-    for (int it = 0; it < a.i_max; ++it) {
+    int it0 = 0;
+    // the leading iterations whose sketch width fits the fused kernel's shared memory (two
+    // CTAs per SM) run in one launch; the rest, for instances still short of their target,
+    // on the per-step kernels below
+    int nf = 0, df = 0;
+    if (K <= 128) {
+      long long kk = a.k_init;
+      for (int it = 0; it < a.i_max; ++it) {
+        const int d = (int)(kk + a.p < K ? kk + a.p : K);
+        if (fused_layout(K, d, sizeof(cx<T>), sizeof(T)).bytes > kFusedSmemCap) break;
+        nf = it + 1;
+        df = d;
+        if (kk < K) kk *= 2;
+      }
+    }
+    if (nf > 0) {
+      WB_TRY(launch_arsvd_fused<T>(a, w, nf, df, s));
+      for (; it0 < nf; ++it0)
+        if (k0 < K) k0 *= 2;
+    }
+    for (int it = it0; it < a.i_max; ++it) {
       const int d = (int)(k0 + a.p < K ? k0 + a.p : K);
       const int last = it == a.i_max - 1;
       const int nq = (dmax + 1) / 2;

@@ -242,6 +242,34 @@ __host__ __device__ inline BlockedSmem blocked_smem(int dmax, int rcap, size_t c
   return s;
 }
 
+// Shared memory of the blocked engine's fused Algorithm 1 kernel (K <= 128, sketch width up
+// to df): Omega and Q (K x df), B (df x K), a 16 x K staging block of dG, the d x d Gram /
+// eigenvector blocks, and the small per-column arrays.
+struct FusedLayout {
+  size_t oOm, oQ, oB, oS, oGy, oUh, oLam, oRs, oCn, oRed, oPerm, oDrop, oFlags, bytes;
+};
+__host__ __device__ inline FusedLayout fused_layout(int K, int df, size_t cxb, size_t tb) {
+  FusedLayout F;
+  size_t o = 0;
+  auto take = [&](size_t n) { const size_t at = o; o = align_up(o + n, 16); return at; };
+  F.oOm = take((size_t)K * df * cxb);
+  F.oQ = take((size_t)K * df * cxb);
+  F.oB = take((size_t)df * K * cxb);
+  F.oS = take((size_t)16 * K * cxb);
+  F.oGy = take((size_t)df * df * cxb);
+  F.oUh = take((size_t)df * df * cxb);
+  F.oLam = take((size_t)df * tb);
+  F.oRs = take((size_t)df * tb);
+  F.oCn = take((size_t)df * tb);
+  F.oRed = take(40 * tb);
+  F.oPerm = take((size_t)df * sizeof(int));
+  F.oDrop = take((size_t)df * sizeof(int));
+  F.oFlags = take(8 * sizeof(int));
+  F.bytes = o;
+  return F;
+}
+constexpr size_t kFusedSmemCap = 110 * 1024;   // two CTAs per SM
+
 // Trace record of one instance: sigma_hat^2 [dmax] (T), L [K][rcap] and R^H [rcap][K] (cx<T>).
 __host__ __device__ inline size_t trace_record_bytes(int K, int dmax, int rcap, size_t cx_bytes,
                                                      size_t t_bytes) {

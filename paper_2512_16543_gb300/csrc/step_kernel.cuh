@@ -552,6 +552,70 @@ __device__ __forceinline__ void fwd_subst_regs(cx<T>* Q, int dmax, int d, int K,
   }
 }
 
+// One CholQR pass on the K x d block Q (ld ldq, shared memory): Gy (ld ldg) holds Q^H Q on
+// entry; warp 0 factors it Gy = R^H R in place (right-looking, column drop for pivots below
+// tol_rel of the column's diagonal or non-finite; drop: persistent flags; rs: 1 / R_jj, 0 for
+// a dropped column; cn: scratch), then Q <- Q R^{-1} row by row.  Called by all threads of a
+// kNT-thread CTA; ends with a barrier.
+template <class T, int kNT = kThreads>
+__device__ void cholqr_pass_smem(cx<T>* Q, int ldq, int K, int d, cx<T>* Gy, int ldg,
+                                 int* drop, T* rs, T* cn, T tol_rel) {
+  const int tid = threadIdx.x;
+  if (tid < 32) {   // one warp factors the d x d Gram matrix; lane c owns column c
+    const int cl = tid;
+    if (cl < d) cn[cl] = Gy[cl * ldg + cl].re;
+    __syncwarp();
+    // right-looking Cholesky Gy = R^H R (R upper, stored in the upper triangle)
+    for (int j = 0; j < d; ++j) {
+      const T piv = Gy[j * ldg + j].re;
+      const bool dj = drop[j] || !(cn[j] > T(0)) || !(piv > tol_rel * cn[j]) || !isfinite(piv);
+      const T rinv = dj ? T(0) : T(1) / sqrt(piv);
+      __syncwarp();
+      if (cl == 0) { drop[j] = dj ? 1 : 0; rs[j] = rinv; }
+      if (cl >= j && cl < d) Gy[j * ldg + cl] = cscale(Gy[j * ldg + cl], rinv);
+      __syncwarp();
+      if (cl > j && cl < d) {
+        const cx<T> rjc = Gy[j * ldg + cl];
+        for (int ai = j + 1; ai <= cl; ai += 4) {     // independent rows, loads first
+          cx<T> v[4], rr[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (ai + u <= cl) {
+              v[u] = Gy[(ai + u) * ldg + cl];
+              rr[u] = Gy[j * ldg + ai + u];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (ai + u <= cl) {
+              cfma_jc(v[u], cscale(rr[u], T(-1)), rjc);
+              Gy[(ai + u) * ldg + cl] = v[u];
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // Q <- Q R^{-1} row by row (forward substitution on x R = q)
+  // (rows of R of dropped columns are zero and rs[c] = 1 / R_cc is zero for them)
+  for (int i = tid; i < K; i += kNT) {
+    cx<T>* qi = Q + i * ldq;
+    for (int c = 0; c < d; ++c) {
+      cx<T> v0 = qi[c], v1 = cmk<T>(0, 0);
+      int a2 = 0;
+      for (; a2 + 1 < c; a2 += 2) {
+        cfma(v0, cscale(qi[a2], T(-1)), Gy[a2 * ldg + c]);
+        cfma(v1, cscale(qi[a2 + 1], T(-1)), Gy[(a2 + 1) * ldg + c]);
+      }
+      if (a2 < c) cfma(v0, cscale(qi[a2], T(-1)), Gy[a2 * ldg + c]);
+      qi[c] = cscale(cadd(v0, v1), rs[c]);
+    }
+  }
+  __syncthreads();
+}
+
 // ------------------------------------------------------------------ phases 2-6
 // Given G_t in w.G (Hermitian, alpha on the diagonal), run the perturbation, the low-rank
 // step, the Woodbury update or direct inverse, the state write-back, the power scale and the
@@ -665,59 +729,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
           __syncthreads();
           continue;
         }
-        if (tid < 32) {   // one warp factors the d x d Gram matrix; lane c owns column c
-          const int cl = tid;
-          if (cl < d) cn[cl] = Gy[cl * dmax + cl].re;
-          __syncwarp();
-          // right-looking Cholesky Gy = R^H R (R upper, stored in the upper triangle)
-          for (int j = 0; j < d; ++j) {
-            const T piv = Gy[j * dmax + j].re;
-            const bool dj = drop[j] || !(cn[j] > T(0)) || !(piv > tol_rel * cn[j]) || !isfinite(piv);
-            const T rinv = dj ? T(0) : T(1) / sqrt(piv);
-            __syncwarp();
-            if (cl == 0) { drop[j] = dj ? 1 : 0; rs[j] = rinv; }
-            if (cl >= j && cl < d) Gy[j * dmax + cl] = cscale(Gy[j * dmax + cl], rinv);
-            __syncwarp();
-            if (cl > j && cl < d) {
-              const cx<T> rjc = Gy[j * dmax + cl];
-              for (int ai = j + 1; ai <= cl; ai += 4) {     // independent rows, loads first
-                cx<T> v[4], rr[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  if (ai + u <= cl) {
-                    v[u] = Gy[(ai + u) * dmax + cl];
-                    rr[u] = Gy[j * dmax + ai + u];
-                  }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  if (ai + u <= cl) {
-                    cfma_jc(v[u], cscale(rr[u], T(-1)), rjc);
-                    Gy[(ai + u) * dmax + cl] = v[u];
-                  }
-                }
-              }
-            }
-            __syncwarp();
-          }
-        }
-        __syncthreads();
-        // Q <- Q R^{-1} row by row (forward substitution on x R = q)
-        // (rows of R of dropped columns are zero and rs[c] = 1 / R_cc is zero for them)
-        for (int i = tid; i < K; i += kThreads) {
-          cx<T>* qi = Q + i * dmax;
-          for (int c = 0; c < d; ++c) {
-            cx<T> v0 = qi[c], v1 = cmk<T>(0, 0);
-            int a2 = 0;
-            for (; a2 + 1 < c; a2 += 2) {
-              cfma(v0, cscale(qi[a2], T(-1)), Gy[a2 * dmax + c]);
-              cfma(v1, cscale(qi[a2 + 1], T(-1)), Gy[(a2 + 1) * dmax + c]);
-            }
-            if (a2 < c) cfma(v0, cscale(qi[a2], T(-1)), Gy[a2 * dmax + c]);
-            qi[c] = cscale(cadd(v0, v1), rs[c]);
-          }
-        }
-        __syncthreads();
+        cholqr_pass_smem<T>(Q, dmax, K, d, Gy, dmax, drop, rs, cn, tol_rel);
       }
       // 3d. projection B = Q^H dG  (d x K)
       mm<T, true, false, MM_SET>(d, K, K, Q, dmax, D, K, Bm, K);

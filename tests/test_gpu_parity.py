@@ -298,3 +298,39 @@ def test_full_size_batched_sampled_parity():
         for t in range(T):
             assert relerr(Ws_s[t][j], ref[t].W) < 2e-3
             assert abs(rates_s[t][j] - ref[t].sum_rate) < 1e-3
+
+
+def test_full_size_batched_full_length_at_bench_eta():
+    """The batched configuration over its full 500 snapshots (5 s of orbit, 25 periodic
+    re-inversions) at the bench's eta = 0.65, in the launch configuration the bench times:
+    sampled instances recomputed by the oracle stay within the complex64 tolerances at every
+    snapshot, so the Woodbury updates between re-inversions do not drift."""
+    sc = channel.scenario_batched_256x32()
+    B, T = 1024, 500
+    params = channel.draw_trajectories(sc, B, seed=2512)
+    rule = binding.RankRule(eta=0.65, k_init=2, p=8, r_max=16, reinverse_period=20, seed=77)
+    h = binding.WBRZF(B, sc.N, sc.K, sc.alpha, sc.sigma2, p_t=sc.p_t, rule=rule)
+    sample = [5, 511, 1000]
+    Hs_s, Ws_s, rates_s, branches = [], [], [], []
+    for t in range(T):
+        H = channel.channel_at(params, t, device="cuda", dtype=torch.complex64)
+        W = h.full_inverse(H) if t == 0 else h.update(H)
+        _, rate = h.sum_rate()
+        Hs_s.append(H[sample].cpu())
+        Ws_s.append(W[sample].cpu().numpy())
+        rates_s.append(rate[sample].cpu().numpy())
+        if t % 50 == 49:
+            info = h.step_info()
+            assert all(i["status"] == 0 for i in info), t
+            branches.append({i["branch"] for i in info})
+    assert h.last_engine == "tensor"
+    h.close()
+    assert any(1 in b for b in branches)            # Woodbury updates were taken
+    Hs = torch.stack(Hs_s)
+    for j, b in enumerate(sample):
+        ref = run_oracle(Hs[:, j].numpy().astype(np.complex128), sc.alpha, sc.sigma2, sc.p_t,
+                         rule, instance=b)
+        assert sum(r.branch == 1 for r in ref) > T // 2
+        for t in range(T):
+            assert relerr(Ws_s[t][j], ref[t].W) < 2e-3, (t, b)
+            assert abs(rates_s[t][j] - ref[t].sum_rate) < 1e-3, (t, b)
