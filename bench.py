@@ -96,11 +96,28 @@ def algorithmic_bytes_per_update(N: int, K: int, method: str) -> int:
 FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def blocked_roofline(stage_ms: dict, B: int, N: int, K: int) -> dict:
+def lowrank_flops(K: int, k_init: int, p: int, iters: float) -> float:
+    """Algorithmic flops of Algorithm 1 per instance over its first `iters` iterations (sketch
+    width d = min(k0 + p, K), k0 doubling): the sketch dG Omega and the projection Q^H dG,
+    8 K^2 d each, and CholQR2's two Gram matrices and substitutions, 24 K d^2; the small SVD's
+    iterative cost is left out."""
+    total, k0, it = 0.0, k_init, 0
+    while it < iters:
+        d = min(k0 + p, K)
+        w = min(1.0, iters - it)                # a fractional mean iteration count
+        total += w * (16.0 * K * K * d + 24.0 * K * d * d)
+        k0 = 2 * k0 if k0 < K else k0
+        it += 1
+    return total
+
+
+def blocked_roofline(stage_ms: dict, B: int, N: int, K: int, lowrank: float = 0.0) -> dict:
     """Roofline of the blocked engine's dominant stage.  Algorithmic flops per instance:
     Gram matrix (Hermitian half) 4 K^2 N; precoder W = H^H X 8 N K^2 plus M = (G - alpha I) X
-    8 K^3."""
+    8 K^3; Algorithm 1 `lowrank` (lowrank_flops)."""
     flops = {"gram": 4.0 * K * K * N, "precoder": 8.0 * N * K * K + 8.0 * K ** 3}
+    if lowrank > 0:
+        flops["lowrank"] = lowrank
     stage = max((k for k in stage_ms if k != "total"), key=lambda k: stage_ms[k])
     out = {"bound": "alu", "unit": "TFLOP/s", "peak": FP32_FMA_TFLOPS,
            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
@@ -792,7 +809,9 @@ def main():
         # ---- blocked engine: the stage that takes the most time, against FP32 FMA peak
         stage_ms = {"wb": {k: statistics.mean(v) for k, v in stages_wb.items()},
                     "full": {k: statistics.mean(v) for k, v in stages_full.items()}}
-        roofline = blocked_roofline(stage_ms["wb"], B, sc.N, sc.K)
+        iters = statistics.mean(i["iters"] for i in info)
+        roofline = blocked_roofline(stage_ms["wb"], B, sc.N, sc.K,
+                                    lowrank_flops(sc.K, 2, 8, iters))
 
     # ---- end to end through the C ABI with host buffers: snapshot i + 1's H goes up on one
     # copy stream and snapshot i - 1's W and sum-rates come down on another while snapshot i
