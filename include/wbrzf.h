@@ -348,6 +348,18 @@ wbrzf_status wbrzf_rzf_noalloc(int batch, int N, int K, wbrzf_precision prec, co
                                double alpha, double sigma2, double p_t, void* W_out,
                                float* sum_rate_out, void* cuda_stream);
 
+/*
+ * Self-test of the bounded waits (not in the paper).  The tensor-core kernels wait on
+ * shared-memory mbarriers for their TMA copies and MMAs; every such wait gives up after a
+ * fixed deadline (200 ms of %globaltimer), records WBRZF_STATUS_TIMEOUT in the instance's step
+ * info and lets the CTA finish, so that a stuck copy cannot hang the GPU.  This call runs one
+ * such wait on an mbarrier on which nothing ever arrives: on out (device, 8-byte aligned,
+ * 2 x uint64) it writes out[0] = WBRZF_STATUS_TIMEOUT and out[1] = the nanoseconds waited.
+ * Enqueued on cuda_stream (NULL = legacy default stream); returns WBRZF_ERR_INVALID_ARG for a
+ * null or misaligned out, WBRZF_ERR_CUDA if the launch fails.
+ */
+wbrzf_status wbrzf_selftest_bounded_wait(void* out, void* cuda_stream);
+
 /* Static description of a status code; the last CUDA error string seen by any handle. */
 const char* wbrzf_status_string(wbrzf_status s);
 const char* wbrzf_last_cuda_error(void);

@@ -16,6 +16,10 @@
 
 using namespace wbk;
 
+namespace wbk {
+cudaError_t launch_wait_selftest(unsigned long long* out, cudaStream_t s);   // step_tc.cu
+}
+
 namespace {
 
 thread_local char g_cuda_err[256] = "";
@@ -945,6 +949,13 @@ const char* wbrzf_status_string(wbrzf_status s) {
     case WBRZF_ERR_UNSUPPORTED: return "unsupported shape or precision";
   }
   return "unknown status";
+}
+
+wbrzf_status wbrzf_selftest_bounded_wait(void* out, void* cuda_stream) {
+  if (out == nullptr || (reinterpret_cast<uintptr_t>(out) & 7) != 0) return WBRZF_ERR_INVALID_ARG;
+  const cudaError_t e = launch_wait_selftest(static_cast<unsigned long long*>(out),
+                                             static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
 }
 
 const char* wbrzf_last_cuda_error(void) { return g_cuda_err; }
