@@ -40,3 +40,28 @@ def test_blocked_roofline_takes_the_dominant_stage():
     st3 = dict(st2, precoder=2.0)
     r3 = bench.blocked_roofline(st3, 4, 4096, 512)
     assert r3["achieved"] == pytest.approx(4 * (8.0 * 4096 * 512 ** 2 + 8.0 * 512 ** 3) / 2e-3 / 1e12)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the FP64 oracle on host cores (no GPU) and prints one
+    JSON line with the metric, unit and config of the default workload, the oracle as its
+    cpu_baseline and an e2e object with zero copy bytes."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "3"], capture_output=True, text=True,
+                         timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC
+    assert d["unit"] == "updates/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("batched_256x32")
