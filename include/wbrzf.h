@@ -210,6 +210,19 @@ wbrzf_status wbrzf_step_info_get(wbrzf* h, wbrzf_step_info* host_out, int count)
 wbrzf_status wbrzf_get_state(wbrzf* h, void* G_out, void* X_out);
 
 /*
+ * Checkpoint / resume (not in the paper): restore the state that wbrzf_get_state and
+ * wbrzf_get_steps export -- G of the last snapshot and X (device, batch contiguous K x K
+ * row-major, the handle's complex type) and each instance's snapshot index t (host
+ * int[batch], t >= 0; it keys Algorithm 1's random draws and the periodic re-inversion).  A
+ * handle of the same shape, precision, method and rule, with the same instance ids and
+ * parameters (set separately), then continues with wbrzf_update as the exporting handle
+ * would have, and is marked initialised.  Synchronises the stream.  Errors: a NULL pointer or
+ * a negative t -> WBRZF_ERR_INVALID_ARG (nothing copied).
+ */
+wbrzf_status wbrzf_set_state(wbrzf* h, const void* G_in, const void* X_in,
+                             const int* steps_host);
+
+/*
  * Optional trace of the low-rank step for testing: when `trace` is non-NULL (device memory
  * of at least wbrzf_trace_bytes() bytes, owned by the caller), each later call writes per
  * instance the squared singular values of B (descending), the factors L = U_r (K x r_max)

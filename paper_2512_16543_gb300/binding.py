@@ -124,6 +124,8 @@ def lib() -> ctypes.CDLL:
     L.wbrzf_step_info_get.argtypes = [vp, ctypes.POINTER(StepInfoC), i32]
     L.wbrzf_get_state.restype = i32
     L.wbrzf_get_state.argtypes = [vp, vp, vp]
+    L.wbrzf_set_state.restype = i32
+    L.wbrzf_set_state.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     L.wbrzf_trace_bytes.restype = sz
     L.wbrzf_trace_bytes.argtypes = [vp]
     L.wbrzf_set_trace.restype = i32
@@ -306,6 +308,21 @@ class WBRZF:
         X = torch.empty_like(G)
         _check(lib().wbrzf_get_state(self._h, _ptr(G), _ptr(X)), "wbrzf_get_state")
         return G, X
+
+    def checkpoint(self) -> tuple[torch.Tensor, torch.Tensor, list[int]]:
+        """The resident state: (G, X, per-instance snapshot indices)."""
+        G, X = self.state()
+        return G, X, self.steps()
+
+    def restore(self, G: torch.Tensor, X: torch.Tensor, steps) -> None:
+        """Load a checkpoint() of a handle of the same shape, precision, method and rule."""
+        shape = (self.batch, self.K, self.K)
+        if tuple(G.shape) != shape or tuple(X.shape) != shape or len(steps) != self.batch:
+            raise ValueError("checkpoint shape does not match the handle")
+        G = G.to(device=self.device, dtype=self.dtype).contiguous()
+        X = X.to(device=self.device, dtype=self.dtype).contiguous()
+        t = (ctypes.c_int * self.batch)(*[int(x) for x in steps])
+        _check(lib().wbrzf_set_state(self._h, _ptr(G), _ptr(X), t), "wbrzf_set_state")
 
     def enable_trace(self, on: bool = True) -> None:
         if not on:

@@ -568,6 +568,25 @@ wbrzf_status wbrzf_get_state(wbrzf* h, void* G_out, void* X_out) {
   return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
 }
 
+wbrzf_status wbrzf_set_state(wbrzf* h, const void* G_in, const void* X_in,
+                             const int* steps_host) {
+  if (!h || !G_in || !X_in || !steps_host) return WBRZF_ERR_INVALID_ARG;
+  for (int b = 0; b < h->batch; ++b)
+    if (steps_host[b] < 0) return WBRZF_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)h->batch * h->K * h->K * cx_bytes(h->prec);
+  cudaError_t e = cudaMemcpyAsync(h->ws + h->wl.oG, G_in, bytes, cudaMemcpyDeviceToDevice,
+                                  h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws + h->wl.oX, X_in, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws + h->wl.oTvec, steps_host, (size_t)h->batch * sizeof(int),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  h->initialized = true;
+  return WBRZF_OK;
+}
+
 size_t wbrzf_trace_bytes(const wbrzf* h) {
   return h ? h->trace_stride * (size_t)h->batch : 0;
 }
