@@ -53,7 +53,7 @@ typedef enum {
   WBRZF_ERR_WORKSPACE = 3,       /* workspace smaller than wbrzf_workspace_bytes()           */
   WBRZF_ERR_NUMERICAL = 4,       /* an instance could not be inverted (see step info)        */
   WBRZF_ERR_CUDA = 5,            /* a CUDA runtime call failed (see wbrzf_last_cuda_error)   */
-  WBRZF_ERR_UNSUPPORTED = 6      /* shape or precision outside what this build supports      */
+  WBRZF_ERR_UNSUPPORTED = 6      /* shape or precision outside what the library supports     */
 } wbrzf_status;
 
 typedef enum {

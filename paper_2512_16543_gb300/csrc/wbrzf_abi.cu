@@ -126,7 +126,7 @@ size_t engine_bytes(int batch, int N, int K, wbrzf_precision prec, const Resolve
 
 }  // namespace
 
-// cuTensorMapEncodeTiled from the driver, looked up once.
+// cuTensorMapEncodeTiled from the CUDA driver, looked up once.
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
