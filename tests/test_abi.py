@@ -74,6 +74,9 @@ def test_host_side_validation_without_gpu(libpath):
     assert L.wbrzf_create(1, 64, 8, a, s, 1.0, ctypes.byref(rule), 0, 1, 256, 16, None,
                           ctypes.byref(h)) == 3          # workspace too small
     assert L.wbrzf_update(None, None, None) == 1
+    assert L.wbrzf_set_state(None, None, None, None) == 1          # checkpoint restore
+    L.wbrzf_selftest_bounded_wait.restype = ctypes.c_int
+    assert L.wbrzf_selftest_bounded_wait(None, None) == 1           # no output buffer
     assert L.wbrzf_status_string(0) == b"ok"
     L.wbrzf_destroy(None)
 
