@@ -341,10 +341,17 @@ void wbrzf_group_destroy(wbrzf_group* g);
  * plug-ins whose host framework owns all device memory.
  *
  * For each of `batch` instances: G = H H^H + alpha I, X = G^{-1} (direct), W_out = s H^H X
- * with ||W||_F^2 = p_t, and, when sum_rate_out is not NULL, R_sum of eq. 15 per instance
- * (device float[batch]); the same kernel as a WBRZF_METHOD_FULL_INVERSE handle on
- * WBRZF_ENGINE_SIMT, so the same results.  H_t / W_out: device, layouts as for wbrzf_update; alpha, sigma2 are shared by all
- * instances.  Work is enqueued on cuda_stream (cudaStream_t, NULL = legacy default stream).
+ * with ||W||_F^2 = p_t, and, when sum_rate_out is not NULL, the same per-instance sum-rate
+ * as wbrzf_sum_rate reports (device float[batch]); the same kernel as a
+ * WBRZF_METHOD_FULL_INVERSE handle on WBRZF_ENGINE_SIMT, so the same results.  H_t / W_out:
+ * device, layouts as for wbrzf_update; alpha >= 0, sigma2 > 0 and p_t > 0 (all finite) are
+ * shared by all instances.  Work is enqueued on cuda_stream (cudaStream_t, NULL = legacy
+ * default stream).
+ *
+ * Failures: this call returns no step info, so an instance whose step fails -- G not
+ * Hermitian positive definite (alpha = 0 with linearly dependent or all-zero user channels)
+ * or a non-finite power scale -- gets NaN in every entry of its W_out and in its sum-rate;
+ * the call still returns WBRZF_OK, and the other instances' results are unaffected.
  *
  * Scratch: a fixed array of WBRZF_NOALLOC_SCRATCH_BYTES compiled into the library (held by
  * every GPU that loads it until the process exits).  The first call on a device looks up the

@@ -61,6 +61,26 @@ __global__ void fill_instance_params(T* alpha, T* sigma2, uint32_t* ids, int bat
   }
 }
 
+// Hand the per-instance outcome to the caller, who gets no step info from this entry point:
+// the sum-rate where asked, and for an instance whose step reported a failure (G_t not
+// Hermitian positive definite, e.g. alpha = 0 with linearly dependent users, or a non-finite
+// scale) NaN in its sum-rate and in every entry of its precoder.
+template <class T>
+__global__ void noalloc_finish(const wbrzf_step_info* info, float* rate, cx<T>* W, size_t nk) {
+  const int b = blockIdx.y;
+  const bool bad = info[b].status != WBRZF_STATUS_OK;
+  if (rate != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+    rate[b] = bad ? __int_as_float(0x7fc00000) : info[b].sum_rate;
+  if (!bad) return;
+  const T nan = (T)__int_as_float(0x7fc00000);
+  cx<T>* const Wb = W + (size_t)b * nk;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk;
+       e += (size_t)gridDim.x * blockDim.x) {
+    Wb[e].re = nan;
+    Wb[e].im = nan;
+  }
+}
+
 // Device address of the scratch array on the current device (resolved once per device).
 cudaError_t scratch_address(unsigned char** out) {
   int dev = 0;
@@ -133,13 +153,12 @@ wbrzf_status run_noalloc(int batch, int N, int K, const void* H, double alpha, d
   if constexpr (sizeof(T) == 8) e = launch_step_f64(a, smem, stream);
   else e = launch_step_f32(a, smem, stream);
   if (e != cudaSuccess) return WBRZF_ERR_CUDA;
-  if (sum_rate_out) {
-    e = cudaMemcpy2DAsync(sum_rate_out, sizeof(float),
-                          base + sl.oInfo + offsetof(wbrzf_step_info, sum_rate),
-                          sizeof(wbrzf_step_info), sizeof(float), batch,
-                          cudaMemcpyDeviceToDevice, stream);
-    if (e != cudaSuccess) return WBRZF_ERR_CUDA;
-  }
+  const size_t nk = (size_t)N * K;
+  const unsigned gx = (unsigned)((nk + 255) / 256 < 8 ? (nk + 255) / 256 : 8);
+  noalloc_finish<T><<<dim3(gx, batch), 256, 0, stream>>>(
+      reinterpret_cast<const wbrzf_step_info*>(base + sl.oInfo), sum_rate_out,
+      static_cast<cx<T>*>(W_out), nk);
+  if (cudaGetLastError() != cudaSuccess) return WBRZF_ERR_CUDA;
   return WBRZF_OK;
 }
 
@@ -151,7 +170,7 @@ extern "C" wbrzf_status wbrzf_rzf_noalloc(int batch, int N, int K, wbrzf_precisi
                                           void* cuda_stream) {
   if (batch < 1 || N < 1 || K < 1 || !H_t || !W_out) return WBRZF_ERR_INVALID_ARG;
   if (!(alpha >= 0.0) || !isfinite(alpha) || !(sigma2 > 0.0) || !isfinite(sigma2) ||
-      !(p_t > 0.0))
+      !(p_t > 0.0) || !isfinite(p_t))
     return WBRZF_ERR_INVALID_ARG;
   if (prec != WBRZF_C64 && prec != WBRZF_C128) return WBRZF_ERR_INVALID_ARG;
   const size_t cxb = prec == WBRZF_C128 ? 16 : 8;

@@ -4,13 +4,11 @@
 namespace wbk {
 
 cudaError_t launch_step_f32(const StepArgs<float>& a, size_t smem, cudaStream_t s) {
-  static size_t smem_set = 0;
-  if (smem > smem_set) {
-    cudaError_t e = cudaFuncSetAttribute(wbrzf_step_kernel<float>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    smem_set = smem;
-  }
+  // The limit is a per-device attribute of the function: set it on every launch (a cheap
+  // host call), so that a kernel launched on another device than the last one gets it too.
+  cudaError_t e = cudaFuncSetAttribute(wbrzf_step_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   wbrzf_step_kernel<float><<<a.batch, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
