@@ -109,6 +109,20 @@ def test_blocked_beyond_one_cta(K, N, prec, engine):
     _check(gpu, Hs, sc, rule, prec, engine=meta["engine"])
 
 
+def test_blocked_uneven_class_1024x128():
+    """The largest class of the uneven population (32x32 UPA, N = 1024, K = 128) with the
+    bench's rule (p = 8, k_init = 2, r_max = 64, eta = 0.65, re-inverse every 20), through the
+    fused Algorithm 1 path of the blocked engine, against the oracle: two instances over ten
+    snapshots, Woodbury updates included."""
+    sc = channel.LeoScenario(n_x=32, n_y=32, K=128, disc_radius=50e3)
+    Hs = _traj(sc, 2, 10, seed=1024)
+    rule = binding.RankRule(eta=0.65, k_init=2, p=8, r_max=64, reinverse_period=20, seed=77)
+    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64")
+    assert meta["engine"] == "blocked"
+    assert _check(gpu, Hs, sc, rule, "c64", engine="blocked") <= 2
+    assert sum(g["info"][b]["branch"] == 1 for g in gpu for b in range(2)) >= 12
+
+
 def test_blocked_full_inversion_method():
     sc = channel.LeoScenario(n_x=50, n_y=4, K=96, disc_radius=100e3)
     Hs = _traj(sc, 2, 3, seed=9)
