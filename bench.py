@@ -241,6 +241,41 @@ def cpu_oracle_baseline(params, sc, rule_kw, n_inst: int, n_steps: int, method: 
             "value": n / busy}
 
 
+def host_link_gbs(dev, host_src, dev_src, reps: int = 5) -> dict:
+    """Pinned host <-> device copy rates of this process, measured in the same run with the
+    bench's own buffers (CUDA events): H2D alone, D2H alone, and both at once on two streams
+    (what the end-to-end leg overlaps).  Best of `reps`."""
+    import torch
+    dst_d = torch.empty_like(host_src, device=dev)
+    dst_h = torch.empty_like(dev_src, device="cpu").pin_memory()
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(up: bool, down: bool) -> float:
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s1)
+            s2.wait_event(e0)
+            if up:
+                with torch.cuda.stream(s1):
+                    dst_d.copy_(host_src, non_blocking=True)
+            if down:
+                with torch.cuda.stream(s2):
+                    dst_h.copy_(dev_src, non_blocking=True)
+            s1.wait_stream(s2)
+            e1.record(s1)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return best
+    nb_up, nb_down = host_src.numel() * host_src.element_size(), dev_src.numel() * dev_src.element_size()
+    t_up, t_down, t_both = timed(True, False), timed(False, True), timed(True, True)
+    return {"h2d_gbs": nb_up / t_up / 1e9, "d2h_gbs": nb_down / t_down / 1e9,
+            "both_directions_gbs": (nb_up + nb_down) / t_both / 1e9,
+            "bytes": [nb_up, nb_down], "how": "pinned buffers of one step, best of 5, events"}
+
+
 # ---------------------------------------------------------------------------- main
 def parse():
     ap = argparse.ArgumentParser()
@@ -253,7 +288,7 @@ def parse():
                     help="instances (default: the workload's)")
     ap.add_argument("--workload", default="batched_256x32",
                     choices=sorted(WORKLOADS) + ["uneven_4096", "serving_2000",
-                                                 "paper_table5"])
+                                                 "paper_table5", "single_64x8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=2512)
@@ -284,7 +319,12 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2512_16543_gb300 import channel
-    if args.workload == "uneven_4096":       # the oracle on the first (N, K) class
+    if args.workload == "single_64x8":       # the whole small trajectory
+        sc = channel.scenario_single_small()
+        wl = {"desc": SINGLE["desc"], "cpu_sample": (1, 100)}
+        B, params = 1, channel.draw_trajectories(sc, 1, seed=args.seed)
+        rule_kw = dict(eta=args.eta or 0.9, k_init=2, p=1, reinverse_period=20, seed=11)
+    elif args.workload == "uneven_4096":     # the oracle on the first (N, K) class
         c = channel.uneven_population(args.batch or UNEVEN["count"], seed=args.seed)[0]
         wl = {"desc": UNEVEN["desc"], "cpu_sample": (16, 6)}
         sc, B, params = c.scenario, c.batch, c.params
@@ -655,6 +695,102 @@ def main_paper(args):
               flush=True)
 
 
+SINGLE = {"desc": ("single_64x8: 1 trajectory x (8x8 UPA, N=64, K=8, 50 km disc), complex128/FP64, "
+                   "p=1, k_init=2, eta=0.9, re-inverse every 20 snapshots, 100 snapshots of "
+                   "10 ms; each update replayed from a captured CUDA graph")}
+
+
+def main_single(args):
+    """Latency of one small trajectory in complex128: per-snapshot p50 / p99 of graph-replayed
+    updates over the 100-snapshot trajectory, beside full-inversion RZF and the oracle."""
+    import numpy as np
+    import torch
+
+    from paper_2512_16543_gb300 import binding, channel
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    W_, K_ = args.warmup, args.steps
+    assert W_ >= 3, "at least 3 warm-up steps"
+    sc = channel.scenario_single_small()
+    T = 100                                             # the trajectory's snapshots
+    params = channel.draw_trajectories(sc, 1, seed=args.seed + 7919 * rank)
+    Hs = torch.stack([channel.channel_at(params, t, device=dev, dtype=torch.complex128)
+                      for t in range(T)])               # [T, 1, K, N] resident in HBM
+    rule_kw = dict(eta=args.eta or 0.9, k_init=2, p=1, reinverse_period=20, seed=11)
+    stream = torch.cuda.current_stream(dev)
+
+    def run(method):
+        h = binding.WBRZF(1, sc.N, sc.K, sc.alpha, sc.sigma2, p_t=sc.p_t,
+                          rule=binding.RankRule(**rule_kw), method=method,
+                          precision="c128", device=dev)
+        Hin = torch.empty_like(Hs[0])
+        Wout = torch.empty(1, sc.N, sc.K, dtype=torch.complex128, device=dev)
+        h.set_graph(True)
+        Hin.copy_(Hs[0])
+        h.full_inverse(Hin, Wout)
+        for t in range(1, 1 + W_):                      # warm-up (captures the graph)
+            Hin.copy_(Hs[t % T])
+            h.update(Hin, Wout)
+        ms = []
+        l0 = h.launches
+        for rep in range((K_ + T - 2) // (T - 1)):      # whole passes over the trajectory
+            Hin.copy_(Hs[0])
+            h.full_inverse(Hin, Wout)                   # t = 0 (not timed), then t = 1..T-1
+            torch.cuda.synchronize()
+            for t in range(1, T):
+                if len(ms) == K_:
+                    break
+                Hin.copy_(Hs[t])                        # outside the events
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.update(Hin, Wout)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        launches = h.launches - l0
+        info = h.step_info()
+        h.close()
+        return ms, launches, info
+
+    clock = ClockSampler(local)
+    clock.start()
+    ms_wb, launches, info = run("wb")
+    clk = clock.stop()
+    ms_full, _, _ = run("full")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = cpu_oracle_baseline(params, sc, rule_kw, 1, T, workers=1)
+        cpu = {"value": res["value"], "unit": "updates/s", "cores": res["cores"],
+               "kind": "oracle", "ms_per_update": 1e3 / res["value"],
+               "sample": f"the whole trajectory (1 x {T} snapshots, WB-arSVD eta="
+                         f"{rule_kw['eta']}), FP64 numpy oracle, one process"}
+    if rank == 0:
+        tot = barrier_max(sum(ms_wb) / 1e3, world)
+        line = {
+            "metric": METRIC, "value": world * len(ms_wb) / tot, "unit": "updates/s",
+            "n_gpus": world, "steps": len(ms_wb), "warmup": W_,
+            "ms_per_step": statistics.mean(ms_wb), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": SINGLE["desc"], "global_batch": world, "eta": rule_kw["eta"],
+                       "l2": "inputs of 8 KiB per snapshot: latency, not bandwidth, is measured",
+                       "parallelism": "replicas only"},
+            "p50_ms": float(np.percentile(ms_wb, 50)), "p99_ms": float(np.percentile(ms_wb, 99)),
+            "full_inverse_rzf": {"value": len(ms_full) / (sum(ms_full) / 1e3),
+                                 "unit": "updates/s",
+                                 "p50_ms": float(np.percentile(ms_full, 50)),
+                                 "p99_ms": float(np.percentile(ms_full, 99))},
+            "roofline": {"bound": "latency", "achieved": None, "peak": None, "frac": None,
+                         "traffic": None, "note": "one 8 x 64 instance: a single-CTA launch "
+                         "whose time is the dependent chain of its steps"},
+            "last_step_branch": binding.BRANCH_NAMES[info[0]["branch"]],
+            "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def collections_counter(it):
     import collections
     return collections.Counter(it)
@@ -673,6 +809,9 @@ def main():
         return
     if args.workload == "paper_table5":
         main_paper(args)
+        return
+    if args.workload == "single_64x8":
+        main_single(args)
         return
     import numpy as np
     import torch
@@ -866,10 +1005,15 @@ def main():
         torch.cuda.synchronize()
         h.close()
         t_e2e = barrier_max(e0.elapsed_time(e1) / 1e3, world)
+        h2d_b = Hh[0].numel() * 8
+        d2h_b = Wh[0].numel() * 8 + Rh[0].numel() * 4
+        link = host_link_gbs(dev, Hh[0], Wd[0])
+        moved = (h2d_b + d2h_b) * K_ / t_e2e / 1e9           # GB/s over both directions
         e2e = {"value": world * B * K_ / t_e2e, "unit": "updates/s",
-               "h2d_bytes_per_step": Hh[0].numel() * 8,
-               "d2h_bytes_per_step": Wh[0].numel() * 8 + Rh[0].numel() * 4,
-               "overlap": "H2D, compute and D2H on three streams, double-buffered"}
+               "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
+               "overlap": "H2D, compute and D2H on three streams, double-buffered",
+               "host_link": link, "copy_gbs": moved,
+               "copy_frac_of_link": moved / link["both_directions_gbs"]}
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 at N = 1 only
     cpu = None
