@@ -32,6 +32,12 @@ constexpr int kDirectMask = (1 << WBRZF_BRANCH_INIT) | (1 << WBRZF_BRANCH_PERIOD
 
 constexpr int kPending = 15;   // branch code while the low-rank step has not decided
 constexpr int kInactive = 14;  // branch code of an instance that sits this step out
+constexpr int kWoodburyWide = 13;
+// Stream accumulators per thread (dr_product / ad_product) of the fused Woodbury step and of the
+// fused Algorithm 1 kernel; each bounds the columns a stream covers to MAXA kThreads / K.
+constexpr int kWoodburyMaxA = 12;
+template <class T> constexpr int fused_max_a() { return sizeof(T) == 4 ? 12 : 6; }  // Woodbury step whose rank exceeds the fused kernel's cap:
+                                   // the batched products take it (reported as Woodbury)
 constexpr int kLiveMask = ~(1 << kInactive);
 
 template <class T>
@@ -512,6 +518,146 @@ __global__ void __launch_bounds__(256) rank_kernel(const StepArgs<T> a, const Bu
   }
 }
 
+// Stream a K x K matrix D (global memory, row-major) through two shared-memory buffers with
+// cp.async double buffering: chunk ch is loaded while chunk ch - 1 is used.  COLS: chunks of
+// CW columns, buf[i * (CW + 1) + kk] = D[i][c0 + kk] (rows padded by one entry against bank
+// conflicts); else chunks of CW rows, buf[kk * K + j] = D[c0 + kk][j].  Entries beyond the
+// matrix read zero.  step(buf, c0, n) runs once per chunk, between two CTA barriers.  CW is a
+// power of two (lg = log2 CW); each buffer holds K (CW + 1) entries.  Called by all threads.
+template <class T, bool COLS, class F>
+__device__ __forceinline__ void stream_chunks(const cx<T>* __restrict__ D, int K, int lg,
+                                              cx<T>* buf0, cx<T>* buf1, F&& step) {
+  const int CW = 1 << lg, nch = (K + CW - 1) >> lg;
+  auto issue = [&](int ch, cx<T>* buf) {
+    const int c0 = ch << lg;
+    if (COLS) {
+      for (int e = threadIdx.x; e < K * CW; e += kThreads) {
+        const int i = e >> lg, kk = e & (CW - 1);
+        cx<T>* dst = buf + i * (CW + 1) + kk;
+        if (c0 + kk < K) cp_async<sizeof(cx<T>)>(dst, D + (size_t)i * K + c0 + kk);
+        else *dst = cmk<T>(0, 0);
+      }
+    } else {
+      for (int kk = 0; kk < CW; ++kk)
+        for (int j = threadIdx.x; j < K; j += kThreads) {
+          cx<T>* dst = buf + kk * K + j;
+          if (c0 + kk < K) cp_async<sizeof(cx<T>)>(dst, D + (size_t)(c0 + kk) * K + j);
+          else *dst = cmk<T>(0, 0);
+        }
+    }
+    cp_async_commit();
+  };
+  issue(0, buf0);
+  for (int ch = 0; ch < nch; ++ch) {
+    cx<T>* const cur = (ch & 1) ? buf1 : buf0;
+    if (ch + 1 < nch) {
+      issue(ch + 1, (ch & 1) ? buf0 : buf1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    step(cur, ch << lg, min(CW, K - (ch << lg)));
+    __syncthreads();
+  }
+}
+
+// P = scale D R (K x nc) for a K x K matrix D in global memory and R (K x nc, ld ldr) in shared
+// memory, streamed by column chunks of D (stream_chunks): thread t accumulates row
+// i = t / G of P, columns g, g + G, ... (g = t mod G, G = kThreads / K, at most MAXA of them) in
+// registers.  P (ld ldp) goes to shared memory, or with CONJT its conjugate transpose P^H
+// (nc x K).  K <= kThreads / 2.  Called by all threads; ends with a barrier.
+template <class T, int MAXA, bool CONJT>
+__device__ __forceinline__ void dr_product(const cx<T>* __restrict__ D, int K, const cx<T>* R,
+                                           int ldr, int nc, cx<T>* P, int ldp, T scale, int lg,
+                                           cx<T>* buf0, cx<T>* buf1) {
+  const int G = kThreads / K, t = threadIdx.x;
+  const bool on = t < G * K;
+  const int i = on ? t / G : 0, g = t - i * G;
+  const int CW1 = (1 << lg) + 1;
+  cx<T> acc[MAXA];
+#pragma unroll
+  for (int m = 0; m < MAXA; ++m) acc[m] = cmk<T>(0, 0);
+  stream_chunks<T, true>(D, K, lg, buf0, buf1, [&](const cx<T>* buf, int c0, int n) {
+    if (!on) return;
+    for (int kk = 0; kk < n; ++kk) {
+      const cx<T> dv = buf[i * CW1 + kk];
+      const cx<T>* Rk = R + (c0 + kk) * ldr + g;
+#pragma unroll
+      for (int m = 0; m < MAXA; ++m)
+        if (g + m * G < nc) cfma(acc[m], dv, Rk[m * G]);
+    }
+  });
+  if (on) {
+#pragma unroll
+    for (int m = 0; m < MAXA; ++m) {
+      const int c = g + m * G;
+      if (c < nc) {
+        if (CONJT) P[c * ldp + i] = cscale(cconj(acc[m]), scale);
+        else P[i * ldp + c] = cscale(acc[m], scale);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Z = A D (nr x K) for A (nr x K, ld lda) in shared memory and a K x K matrix D in global
+// memory, streamed by row chunks of D: thread t accumulates column j = t mod K of Z, rows
+// g, g + G, ... (g = t / K, at most MAXA of them) in registers; Z (ld ldz) to shared memory.
+// Called by all threads; ends with a barrier.
+template <class T, int MAXA>
+__device__ __forceinline__ void ad_product(const cx<T>* __restrict__ D, int K, const cx<T>* A,
+                                           int lda, int nr, cx<T>* Z, int ldz, int lg,
+                                           cx<T>* buf0, cx<T>* buf1) {
+  const int G = kThreads / K, t = threadIdx.x;
+  const bool on = t < G * K;
+  const int g = on ? t / K : 0, j = t - g * K;
+  cx<T> acc[MAXA];
+#pragma unroll
+  for (int m = 0; m < MAXA; ++m) acc[m] = cmk<T>(0, 0);
+  stream_chunks<T, false>(D, K, lg, buf0, buf1, [&](const cx<T>* buf, int c0, int n) {
+    if (!on) return;
+    for (int kk = 0; kk < n; ++kk) {
+      const cx<T> dv = buf[kk * K + j];
+#pragma unroll
+      for (int m = 0; m < MAXA; ++m)
+        if (g + m * G < nr) cfma(acc[m], A[(g + m * G) * lda + c0 + kk], dv);
+    }
+  });
+  if (on) {
+#pragma unroll
+    for (int m = 0; m < MAXA; ++m)
+      if (g + m * G < nr) Z[(g + m * G) * ldz + j] = acc[m];
+  }
+  __syncthreads();
+}
+
+// dr_product / ad_product with the accumulator count fixed at compile time to the smallest of
+// 2, 4, 6, 8, 12 that covers ceil(n / G) (n the columns / rows covered, G = kThreads / K), so
+// that no thread issues work for accumulators it does not use.  MAXA bounds the largest.
+template <class T, int MAXA, bool CONJT>
+__device__ __forceinline__ void dr_product_n(const cx<T>* __restrict__ D, int K, const cx<T>* R,
+                                             int ldr, int nc, cx<T>* P, int ldp, T scale,
+                                             int lg, cx<T>* buf0, cx<T>* buf1) {
+  const int G = kThreads / K, na = (nc + G - 1) / G;
+  if (na <= 2) dr_product<T, 2, CONJT>(D, K, R, ldr, nc, P, ldp, scale, lg, buf0, buf1);
+  else if (na <= 4) dr_product<T, 4, CONJT>(D, K, R, ldr, nc, P, ldp, scale, lg, buf0, buf1);
+  else if (na <= 6 || MAXA <= 6) dr_product<T, (MAXA < 6 ? MAXA : 6), CONJT>(D, K, R, ldr, nc, P, ldp, scale, lg, buf0, buf1);
+  else if (na <= 8) dr_product<T, (MAXA < 8 ? MAXA : 8), CONJT>(D, K, R, ldr, nc, P, ldp, scale, lg, buf0, buf1);
+  else dr_product<T, MAXA, CONJT>(D, K, R, ldr, nc, P, ldp, scale, lg, buf0, buf1);
+}
+template <class T, int MAXA>
+__device__ __forceinline__ void ad_product_n(const cx<T>* __restrict__ D, int K, const cx<T>* A,
+                                             int lda, int nr, cx<T>* Z, int ldz, int lg,
+                                             cx<T>* buf0, cx<T>* buf1) {
+  const int G = kThreads / K, na = (nr + G - 1) / G;
+  if (na <= 2) ad_product<T, 2>(D, K, A, lda, nr, Z, ldz, lg, buf0, buf1);
+  else if (na <= 4) ad_product<T, 4>(D, K, A, lda, nr, Z, ldz, lg, buf0, buf1);
+  else if (na <= 6 || MAXA <= 6) ad_product<T, (MAXA < 6 ? MAXA : 6)>(D, K, A, lda, nr, Z, ldz, lg, buf0, buf1);
+  else if (na <= 8) ad_product<T, (MAXA < 8 ? MAXA : 8)>(D, K, A, lda, nr, Z, ldz, lg, buf0, buf1);
+  else ad_product<T, MAXA>(D, K, A, lda, nr, Z, ldz, lg, buf0, buf1);
+}
+
 // Fused Algorithm 1 iterations (K <= 128, the leading nf iterations, whose sketch widths fit
 // the shared-memory layout of width df): one CTA of kThreads threads per instance runs them
 // with the one-CTA engines' device code -- Omega from the same Philox counters, Y = 2^-e dG
@@ -521,7 +667,7 @@ __global__ void __launch_bounds__(256) rank_kernel(const StepArgs<T> a, const Bu
 // for the Woodbury stage: the control words, perm, lam, the trace, the unrotated B, and for a
 // Woodbury instance Q and U_r.  An instance still short of its target after the nf
 // iterations stays active and continues on the per-step kernels.
-template <class T, int EPL>
+template <class T, bool LARGEK>
 __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs<T> a,
                                                                   const Bufs<T> w, int nf,
                                                                   int df) {
@@ -532,7 +678,6 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
   cx<T>* const Om = reinterpret_cast<cx<T>*>(sm + F.oOm);
   cx<T>* const Q = reinterpret_cast<cx<T>*>(sm + F.oQ);
   cx<T>* const Bm = reinterpret_cast<cx<T>*>(sm + F.oB);
-  cx<T>* const S = reinterpret_cast<cx<T>*>(sm + F.oS);
   cx<T>* const Gy = reinterpret_cast<cx<T>*>(sm + F.oGy);
   cx<T>* const Uh = reinterpret_cast<cx<T>*>(sm + F.oUh);
   T* const lam = reinterpret_cast<T*>(sm + F.oLam);
@@ -542,6 +687,9 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
   int* const perm = reinterpret_cast<int*>(sm + F.oPerm);
   int* const drop = reinterpret_cast<int*>(sm + F.oDrop);
   int* const flags = reinterpret_cast<int*>(sm + F.oFlags);
+  cx<T>* const buf0 = reinterpret_cast<cx<T>*>(sm + F.oBuf);
+  cx<T>* const buf1 = buf0 + (size_t)K * ((1 << kChunkLg) + 1);
+  const int lgcw = kChunkLg;
   const cx<T>* const D = w.D + (size_t)b * w.L.sD;
   const T dsc = w.dsc[b];
   int* const ctl = w.ctl + 8 * b;
@@ -565,22 +713,8 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
       if (2 * q + 1 < d) Om[i * df + 2 * q + 1] = box_muller(x.z, x.w, T(0));
     }
     __syncthreads();
-    // Y = 2^-e dG Omega (K x d, ld df): dG by 16-column chunks through S (K x 16)
-    for (int c0 = 0; c0 < K; c0 += 16) {
-      for (int e = tid; e < K * 16; e += kThreads) {
-        const int i = e >> 4, k = c0 + (e & 15);
-        S[e] = k < K ? D[(size_t)i * K + k] : cmk<T>(0, 0);
-      }
-      __syncthreads();
-      const int kn = min(16, K - c0);
-      for (int o = tid; o < K * d; o += kThreads) {
-        const int i = o / d, c = o - i * d;
-        cx<T> acc = c0 == 0 ? cmk<T>(0, 0) : Q[i * df + c];
-        for (int kk = 0; kk < kn; ++kk) cfma(acc, S[i * 16 + kk], Om[(c0 + kk) * df + c]);
-        Q[i * df + c] = c0 + 16 >= K ? cscale(acc, dsc) : acc;
-      }
-      __syncthreads();
-    }
+    // Y = 2^-e dG Omega (K x d, ld df), dG streamed once by column chunks
+    dr_product_n<T, fused_max_a<T>(), false>(D, K, Om, df, d, Q, df, dsc, lgcw, buf0, buf1);
     // Q = orth(Y): CholQR twice, numerically dependent columns dropped
     if (tid < d) drop[tid] = 0;
     __syncthreads();
@@ -589,43 +723,39 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
       __syncthreads();
       cholqr_pass_smem<T>(Q, df, K, d, Gy, df, drop, rs, cn, tol_rel);
     }
-    // B = 2^-e Q^H dG (d x K, ld K): dG by 16-row chunks through S (16 x K); the unrotated B
-    // (rows >= d zero) goes to the global buffer the Woodbury products read
-    for (int r0 = 0; r0 < K; r0 += 16) {
-      for (int e = tid; e < 16 * K; e += kThreads) {
-        const int i = r0 + e / K;
-        S[e] = i < K ? D[(size_t)i * K + (e - (e / K) * K)] : cmk<T>(0, 0);
-      }
-      __syncthreads();
-      const int in = min(16, K - r0);
-      for (int o = tid; o < d * K; o += kThreads) {
-        const int c = o / K, j = o - c * K;
-        cx<T> acc = r0 == 0 ? cmk<T>(0, 0) : Bm[o];
-        for (int ii = 0; ii < in; ++ii) cfma_jc(acc, Q[(r0 + ii) * df + c], S[ii * K + j]);
-        Bm[o] = r0 + 16 >= K ? cscale(acc, dsc) : acc;
-      }
-      __syncthreads();
-    }
+    // B = 2^-e Q^H dG (d x K, ld K).  dG is exactly Hermitian as stored (its lower triangle is
+    // the conjugate of the upper), so B = (2^-e dG Q)^H: the same row stream as the sketch.
+    // The unrotated B (rows >= d zero) goes to the global buffer the Woodbury step reads.
+    dr_product_n<T, fused_max_a<T>(), true>(D, K, Q, df, d, Bm, K, dsc, lgcw, buf0, buf1);
     {
       cx<T>* const Bg = w.Bm + (size_t)b * w.L.sBm;
       for (int o = tid; o < dmax * K; o += kThreads) Bg[o] = o < d * K ? Bm[o] : cmk<T>(0, 0);
     }
-    // svd(B): one-sided Jacobi on B's rows; U (d x d, ld df) starts as I
-    for (int e = tid; e < d * d; e += kThreads) {
-      const int i = e / d, j = e - i * d;
-      Uh[i * df + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
-    }
-    __syncthreads();
-    hestenes_jacobi<T, EPL>(Bm, K, Uh, df, d, tol2, sweeps, flags, red);
-    // sigma_hat^2 (squared row norms of the rotated B), sorted descending
-    for (int j0 = (tid >> 5) * 2; j0 < d; j0 += kThreads / 16) {   // warp-uniform loop
-      const int j = j0 + ((tid >> 4) & 1);
-      T v = 0;
-      if (j < d)
-        for (int k = tid & 15; k < K; k += 16) v += cabs2(Bm[j * K + k]);
+    // svd(B) as in the one-CTA engines: K <= 32, one-sided Jacobi on B's rows (the unrotated
+    // B is already in global memory for the Woodbury products), sigma_hat^2 the squared row
+    // norms; K > 32, two-sided Jacobi on E = B B^H (d x d, into Gy: Q^H Q is dead) on one warp,
+    // sigma_hat^2 E's rotated diagonal.  U_hat holds the left singular vectors.
+    if (!LARGEK) {
+      for (int e = tid; e < d * d; e += kThreads) {
+        const int i = e / d, j = e - i * d;
+        Uh[i * df + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
+      }
+      __syncthreads();
+      hestenes_jacobi<T, 4>(Bm, K, Uh, df, d, tol2, sweeps, flags, red);
+      for (int j0 = (tid >> 5) * 2; j0 < d; j0 += kThreads / 16) {   // warp-uniform loop
+        const int j = j0 + ((tid >> 4) & 1);
+        T v = 0;
+        if (j < d)
+          for (int k = tid & 15; k < K; k += 16) v += cabs2(Bm[j * K + k]);
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((tid & 15) == 0 && j < d) lam[j] = v;
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 15) == 0 && j < d) lam[j] = v;
+      }
+    } else {
+      mm<T, false, true, MM_SET>(d, d, K, Bm, K, Bm, K, Gy, df);
+      __syncthreads();
+      jacobi_eig<T>(Gy, df, Uh, df, d, tol2, sweeps);
+      if (tid < d) lam[tid] = fmax(Gy[tid * df + tid].re, T(0));
     }
     __syncthreads();
     if (tid < d) {
@@ -693,10 +823,10 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
 // with partial pivoting; a numerically singular pivot sends the instance to the direct
 // inverse (fallback branch).
 template <class T>
-__global__ void __launch_bounds__(256) capinv_kernel(const Bufs<T> w) {
+__global__ void __launch_bounds__(256) capinv_kernel(const Bufs<T> w, int gmask) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int b = blockIdx.x, tid = threadIdx.x, rcap = w.rcap;
-  if (!gate_ok(w.ctl, b, C_BRANCH, 1 << WBRZF_BRANCH_WOODBURY)) return;
+  if (!gate_ok(w.ctl, b, C_BRANCH, gmask)) return;
   const int n = w.ctl[8 * b + C_R], ld = 2 * n;
   cx<T>* A = reinterpret_cast<cx<T>*>(sm);
   cx<T>* col = A + (size_t)rcap * 2 * rcap;
@@ -764,11 +894,151 @@ __global__ void __launch_bounds__(256) capinv_kernel(const Bufs<T> w) {
   }
 }
 
+// X <- X - T W for X (K x K, global memory), T (K x r, ld ldt) and W (r x K, ld ldw) in shared
+// memory: thread t updates column j = t mod K of X on rows g, g + G, ... (g = t / K,
+// G = kThreads / K), holding W's column j in registers (r <= NR).
+template <class T, int NR>
+__device__ __forceinline__ void woodbury_update_cols(cx<T>* X, int K, int r, const cx<T>* Tm,
+                                                     int ldt, const cx<T>* W, int ldw) {
+  const int G = kThreads / K, t = threadIdx.x;
+  if (t >= G * K) return;
+  const int g = t / K, j = t - g * K;
+  cx<T> wc[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) wc[c] = c < r ? W[c * ldw + j] : cmk<T>(0, 0);
+#pragma unroll 2
+  for (int i = g; i < K; i += G) {
+    cx<T>* const xp = X + (size_t)i * K + j;
+    const cx<T> xv = *xp;
+    const cx<T>* const Ti = Tm + i * ldt;
+    cx<T> a0 = cmk<T>(0, 0), a1 = cmk<T>(0, 0);
+#pragma unroll
+    for (int c = 0; c < NR; c += 2) {
+      if (c < r) cfma(a0, Ti[c], wc[c]);
+      if (c + 1 < r) cfma(a1, Ti[c + 1], wc[c + 1]);
+    }
+    *xp = csub(xv, cadd(a0, a1));
+  }
+}
+
+// Woodbury update (Section III eq. 12) of one instance per CTA (K <= 128, rank r <= RF), in
+// place of the batched products around capinv_kernel:
+//   L = Q U_r (K x r) and R^H = nu U_r^H B (r x K) from Algorithm 1's factors (nu undoes dG's
+//     power-of-two scale), so that dG ~= L R^H;
+//   T = X L and Z = R^H X, each one stream of X through shared memory (dr_product /
+//     ad_product);
+//   C = I + R^H T (= I + R^H X L), and Gauss-Jordan with partial pivoting [C | Z] -> [I | C^-1 Z]
+//     on one warp (gauss_jordan_warp); a numerically singular C sends the instance to the
+//     direct inverse (branch FALLBACK);
+//   a second pass X <- X - T (C^-1 Z).
+// X is streamed from global memory three times (rows for T, columns for Z, columns for the
+// update); everything else stays in shared memory (layout of woodbury_fused_smem).  An
+// instance with r > RF is marked kWoodburyWide for the batched products.
+template <class T>
+__global__ void __launch_bounds__(256, 2) woodbury_fused_kernel(const StepArgs<T> a,
+                                                                const Bufs<T> w, int RF) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int singular;
+  const int b = blockIdx.x, tid = threadIdx.x, K = a.K, dmax = w.dmax, rcap = w.rcap;
+  if (!gate_ok(w.ctl, b, C_BRANCH, 1 << WBRZF_BRANCH_WOODBURY)) return;
+  int* const ctl = w.ctl + 8 * b;
+  const int r = ctl[C_R], d = ctl[C_D];
+  if (r > RF) {
+    if (tid == 0) ctl[C_BRANCH] = kWoodburyWide;
+    return;
+  }
+  const int ldz = RF + K;
+  cx<T>* const Lm = reinterpret_cast<cx<T>*>(sm);       // K x RF
+  cx<T>* const Rh = Lm + (size_t)K * RF;                  // RF x K
+  cx<T>* const Tm = Rh + (size_t)RF * K;                  // K x RF
+  cx<T>* const CZ = Tm + (size_t)K * RF;                  // RF x (RF + K): [C | Z]
+  cx<T>* const buf0 = CZ + (size_t)RF * ldz;               // two X chunks (stream_chunks)
+  cx<T>* const buf1 = buf0 + (size_t)K * ((1 << kChunkLg) + 1);
+  const int lgcw = kChunkLg;
+  const cx<T>* const Q = w.Q + (size_t)b * w.L.sOm;       // K x dmax
+  const cx<T>* const Ur = w.Ur + (size_t)b * w.L.sUr;     // dmax x rcap
+  const cx<T>* const Bg = w.Bm + (size_t)b * w.L.sBm;     // dmax x K (unrotated B)
+  const T nu = w.nu[b];
+  cx<T>* const X = a.Xs + (size_t)b * K * K;
+  // L = Q U_r, R^H = nu U_r^H B
+  for (int o = tid; o < K * r; o += 256) {
+    const int i = o / r, c = o - i * r;
+    cx<T> acc = cmk<T>(0, 0);
+    for (int k = 0; k < d; ++k) cfma(acc, Q[(size_t)i * dmax + k], Ur[(size_t)k * rcap + c]);
+    Lm[i * RF + c] = acc;
+  }
+  for (int o = tid; o < r * K; o += 256) {
+    const int c = o / K, j = o - c * K;
+    cx<T> acc = cmk<T>(0, 0);
+    for (int k = 0; k < d; ++k) cfma_jc(acc, Ur[(size_t)k * rcap + c], Bg[(size_t)k * K + j]);
+    Rh[c * K + j] = cscale(acc, nu);
+  }
+  __syncthreads();
+  if (a.trace != nullptr) {     // L (K x rcap) and R^H (rcap x K), zero beyond the rank
+    cx<T>* trl = reinterpret_cast<cx<T>*>(a.trace + (size_t)b * a.trace_stride +
+                                          align_up((size_t)dmax * sizeof(T), 16));
+    const size_t n = (size_t)K * rcap;
+    for (size_t e = tid; e < n; e += 256) {
+      const int i = (int)(e / rcap), c = (int)(e - (size_t)i * rcap);
+      trl[e] = c < r ? Lm[i * RF + c] : cmk<T>(0, 0);
+      const int cc = (int)(e / K), j = (int)(e - (size_t)cc * K);
+      trl[n + e] = cc < r ? Rh[cc * K + j] : cmk<T>(0, 0);
+    }
+  }
+  // T = X L (X streamed by column chunks), Z = R^H X (by row chunks) into [C | Z]
+  dr_product_n<T, kWoodburyMaxA, false>(X, K, Lm, RF, r, Tm, RF, T(1), lgcw, buf0, buf1);
+  ad_product_n<T, kWoodburyMaxA>(X, K, Rh, K, r, CZ + RF, ldz, lgcw, buf0, buf1);
+  // C = I + R^H T
+  for (int o = tid; o < r * r; o += 256) {
+    const int c = o / r, e = o - c * r;
+    cx<T> acc = cmk<T>(c == e ? T(1) : T(0), T(0));
+    for (int k = 0; k < K; ++k) cfma(acc, Rh[c * K + k], Tm[k * RF + e]);
+    CZ[c * ldz + e] = acc;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    T cmax = 0;
+    for (int o = tid; o < r * r; o += 32) {
+      const int c = o / r, e = o - c * r;
+      cmax = fmax(cmax, sqrt(cabs2(CZ[c * ldz + e])));
+    }
+    for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    const T tol = cmax * ((sizeof(T) == 4) ? T(1e-6) : T(1e-14));
+    const bool sg = gauss_jordan_warp<T>(CZ, ldz, r, RF, K, tol);
+    if (tid == 0) singular = sg ? 1 : 0;
+  }
+  __syncthreads();
+  if (singular) {
+    if (tid == 0) ctl[C_BRANCH] = WBRZF_BRANCH_FALLBACK;
+    return;
+  }
+  // X <- X - T (C^-1 Z): thread t updates column j = t mod K on rows g, g + G, ..., with the
+  // column of C^-1 Z in registers (r <= NR, NR the smallest bucket of 4, 8, 16, 24 >= r;
+  // woodbury_fused_cap keeps RF <= 24, and <= 16 in FP64)
+  if (r <= 4) woodbury_update_cols<T, 4>(X, K, r, Tm, RF, CZ + RF, ldz);
+  else if (r <= 8) woodbury_update_cols<T, 8>(X, K, r, Tm, RF, CZ + RF, ldz);
+  else if (r <= 16 || sizeof(T) == 8) woodbury_update_cols<T, 16>(X, K, r, Tm, RF, CZ + RF, ldz);
+  else woodbury_update_cols<T, (sizeof(T) == 4 ? 24 : 16)>(X, K, r, Tm, RF, CZ + RF, ldz);
+}
+
+// Condition of a CUDA-graph IF node: true when some instance's control word ctl[idx] is one of
+// the values in `mask` (the instances the guarded kernels would not skip).
+__global__ void any_selected_kernel(cudaGraphConditionalHandle h, const int* ctl, int batch,
+                                    int idx, int mask) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < batch; b += blockDim.x)
+    if ((mask >> ctl[8 * b + idx]) & 1) any = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
 // Trace of a Woodbury step: L (K x rcap) and R^H (rcap x K), zero beyond the rank
 template <class T>
-__global__ void trace_lr_kernel(const StepArgs<T> a, const Bufs<T> w) {
+__global__ void trace_lr_kernel(const StepArgs<T> a, const Bufs<T> w, int gmask) {
   const int b = blockIdx.y;
-  if (!gate_ok(w.ctl, b, C_BRANCH, 1 << WBRZF_BRANCH_WOODBURY)) return;
+  if (!gate_ok(w.ctl, b, C_BRANCH, gmask)) return;
   const size_t n = (size_t)a.K * w.rcap;
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
@@ -925,7 +1195,7 @@ __global__ void __launch_bounds__(256) sinr_final_kernel(const StepArgs<T> a, co
     int status = ctl[C_STATUS];
     if (!isfinite(s) || !isfinite(R)) status |= WBRZF_STATUS_NONFINITE;
     wbrzf_step_info inf;
-    inf.branch = ctl[C_BRANCH];
+    inf.branch = ctl[C_BRANCH] == kWoodburyWide ? WBRZF_BRANCH_WOODBURY : ctl[C_BRANCH];
     inf.r = ctl[C_R];
     inf.iters = ctl[C_ITERS];
     inf.d = ctl[C_D];
@@ -943,24 +1213,94 @@ template <class T>
 cudaError_t launch_arsvd_fused(const StepArgs<T>& a, const Bufs<T>& w, int nf, int df,
                                cudaStream_t s) {
   const int bytes = (int)fused_layout(a.K, df, sizeof(cx<T>), sizeof(T)).bytes;
-  cudaError_t e;
-  if (a.K <= 32) {
-    e = cudaFuncSetAttribute(arsvd_fused_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) arsvd_fused_kernel<T, 4><<<a.batch, kThreads, bytes, s>>>(a, w, nf, df);
-  } else if (a.K <= 64) {
-    e = cudaFuncSetAttribute(arsvd_fused_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) arsvd_fused_kernel<T, 8><<<a.batch, kThreads, bytes, s>>>(a, w, nf, df);
-  } else {
-    e = cudaFuncSetAttribute(arsvd_fused_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) arsvd_fused_kernel<T, 16><<<a.batch, kThreads, bytes, s>>>(a, w, nf, df);
-  }
+  const auto kern = a.K > 32 ? arsvd_fused_kernel<T, true> : arsvd_fused_kernel<T, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) kern<<<a.batch, kThreads, bytes, s>>>(a, w, nf, df);
   return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Shared memory of the fused Woodbury kernel at rank cap RF: L (K x RF), R^H (RF x K),
+// T (K x RF), [C | Z] (RF x (RF + K)), two chunk buffers of X (K x (2^kChunkLg + 1) each).
+inline size_t woodbury_fused_smem(int K, int RF, size_t cxb) {
+  return cxb * (3 * (size_t)K * RF + (size_t)RF * (RF + K) +
+                2 * (size_t)K * ((1 << kChunkLg) + 1));
+}
+// Largest rank cap RF <= rcap of the fused Woodbury kernel (0: not used, K > 128): its shared
+// memory within two CTAs per SM and each thread's share of T or Z within the stream
+// accumulators (RF <= kWoodburyMaxA kThreads / K).
+template <class T>
+int woodbury_fused_cap(int K, int rcap) {
+  if (K > 128) return 0;
+  const int top = sizeof(T) == 4 ? 24 : 16;        // woodbury_update_cols register buckets
+  for (int RF = rcap < top ? rcap : top; RF >= 1; --RF)
+    if (woodbury_fused_smem(K, RF, sizeof(cx<T>)) <= kFusedSmemCap &&
+        RF <= kWoodburyMaxA * (kThreads / K))
+      return RF;
+  return 0;
+}
+inline int woodbury_fused_cap(int K, int rcap, size_t cxb) {
+  return cxb == 8 ? woodbury_fused_cap<float>(K, rcap) : woodbury_fused_cap<double>(K, rcap);
+}
+
+template <class T>
+cudaError_t launch_woodbury_fused(const StepArgs<T>& a, const Bufs<T>& w, int RF,
+                                  cudaStream_t s) {
+  const int bytes = (int)woodbury_fused_smem(a.K, RF, sizeof(cx<T>));
+  cudaError_t e = cudaFuncSetAttribute(woodbury_fused_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  woodbury_fused_kernel<T><<<a.batch, 256, bytes, s>>>(a, w, RF);
+  return cudaGetLastError();
+}
+
+// Enqueue `body`, a block of launches whose kernels return at once for the instances that a
+// control word does not select, on stream s.  While s is being captured into a CUDA graph the
+// block becomes an IF node: any_selected_kernel sets its condition from the control words
+// (instance b counts when (mask >> ctl[8 b + idx]) & 1), so a replay skips the whole block
+// when no instance needs it; the node's body is recorded on body_stream, which must not be
+// capturing.  Enqueued eagerly (or without a body stream) the block is launched as is.  The
+// condition kernel is not counted in the handle's launches, so that a captured step counts
+// what an enqueued one does.
+template <class F>
+cudaError_t guarded(cudaStream_t s, cudaStream_t body_stream, const int* ctl, int batch, int idx,
+                    int mask, F&& body) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd);
+  if (e != cudaSuccess) return e;
+  if (st != cudaStreamCaptureStatusActive || body_stream == nullptr) return body(s);
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+    return e;
+  any_selected_kernel<<<1, 256, 0, s>>>(h, ctl, batch, idx, mask);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd)) != cudaSuccess)
+    return e;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeIf;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p)) != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(body_stream, p.conditional.phGraph_out[0], nullptr, nullptr,
+                                    0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t eb = body(body_stream);
+  cudaGraph_t out = nullptr;
+  e = cudaStreamEndCapture(body_stream, &out);
+  if (eb != cudaSuccess) return eb;
+  if (e != cudaSuccess) return e;
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                             cudaStreamSetCaptureDependencies);
 }
 
 // ---------------------------------------------------------------- the snapshot sequence
 template <class T>
-cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t s, int* launches,
-                        cudaEvent_t* ev) {
+cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t s,
+                        cudaStream_t sb, int* launches, cudaEvent_t* ev) {
   const int B = a.batch, K = a.K, N = a.N, dmax = a.dmax, rcap = a.rcap;
   const Bufs<T> w = make_bufs<T>(base, B, N, K, dmax, rcap);
   const BlockedLayout& L = w.L;
@@ -1015,7 +1355,9 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
       long long kk = a.k_init;
       for (int it = 0; it < a.i_max; ++it) {
         const int d = (int)(kk + a.p < K ? kk + a.p : K);
-        if (fused_layout(K, d, sizeof(cx<T>), sizeof(T)).bytes > kFusedSmemCap) break;
+        if (fused_layout(K, d, sizeof(cx<T>), sizeof(T)).bytes > kFusedSmemCap ||
+            d > fused_max_a<T>() * (kThreads / K))
+          break;
         nf = it + 1;
         df = d;
         if (kk < K) kk *= 2;
@@ -1029,80 +1371,103 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
     for (int it = it0; it < a.i_max; ++it) {
       const int d = (int)(k0 + a.p < K ? k0 + a.p : K);
       const int last = it == a.i_max - 1;
-      const int nq = (dmax + 1) / 2;
-      omega_kernel<T><<<dim3((K * nq + 255) / 256, B), 256, 0, s>>>(a, w, it, d);
-      WB_TRY(cudaGetLastError());
-      // Y = (2^-e dG) Omega: the power-of-two scale is exact, so applying it to the product
-      // gives the same values as scaling dG first
-      // (Omega's columns >= d are zero: those tiles of Y are zero without a reduction)
-      WB_TRY(gemm<T>(s, B, K, dmax, K, w.D, K, L.sD, 0, w.Om, dmax, L.sOm, 0, w.Q, dmax, L.sOm,
-                     one, w.dsc, zero, w.ctl, C_ACTIVE, 2, nullptr, Live{1 << 30, d, 1 << 30}));
-      for (int pass = 0; pass < 2; ++pass) {
-        WB_TRY(gemm<T>(s, B, d, d, K, w.Q, dmax, L.sOm, 1, w.Q, dmax, L.sOm, 0, w.Gy, dmax,
-                       L.sGy, one, nullptr, zero, w.ctl, C_ACTIVE, 2));
-        cholesky_kernel<T><<<B, 256, cs, s>>>(w, d, pass);
+      // one Algorithm 1 iteration for the instances still iterating (C_ACTIVE = 1)
+      e = guarded(s, sb, w.ctl, B, C_ACTIVE, 2, [&](cudaStream_t q) -> cudaError_t {
+        cudaError_t e;
+        const int nq = (dmax + 1) / 2;
+        omega_kernel<T><<<dim3((K * nq + 255) / 256, B), 256, 0, q>>>(a, w, it, d);
         WB_TRY(cudaGetLastError());
-        fwdsubst_kernel<T><<<dim3((K + 127) / 128, B), 128, 0, s>>>(a, w, d);
+        // Y = (2^-e dG) Omega: the power-of-two scale is exact, so applying it to the product
+        // gives the same values as scaling dG first
+        // (Omega's columns >= d are zero: those tiles of Y are zero without a reduction)
+        WB_TRY(gemm<T>(q, B, K, dmax, K, w.D, K, L.sD, 0, w.Om, dmax, L.sOm, 0, w.Q, dmax,
+                       L.sOm, one, w.dsc, zero, w.ctl, C_ACTIVE, 2, nullptr,
+                       Live{1 << 30, d, 1 << 30}));
+        for (int pass = 0; pass < 2; ++pass) {
+          WB_TRY(gemm<T>(q, B, d, d, K, w.Q, dmax, L.sOm, 1, w.Q, dmax, L.sOm, 0, w.Gy, dmax,
+                         L.sGy, one, nullptr, zero, w.ctl, C_ACTIVE, 2));
+          cholesky_kernel<T><<<B, 256, cs, q>>>(w, d, pass);
+          WB_TRY(cudaGetLastError());
+          fwdsubst_kernel<T><<<dim3((K + 127) / 128, B), 128, 0, q>>>(a, w, d);
+          WB_TRY(cudaGetLastError());
+        }
+        WB_TRY(gemm<T>(q, B, dmax, K, K, w.Q, dmax, L.sOm, 1, w.D, K, L.sD, 0, w.Bm, K, L.sBm,
+                       one, w.dsc, zero, w.ctl, C_ACTIVE, 2, nullptr, Live{d, 1 << 30, 1 << 30}));
+        WB_TRY(gemm<T>(q, B, d, d, K, w.Bm, K, L.sBm, 0, w.Bm, K, L.sBm, 1, w.E, dmax, L.sGy,
+                       one, nullptr, zero, w.ctl, C_ACTIVE, 2));
+        if (d > 32) jacobi_kernel<1024, T><<<B, 1024, js, q>>>(w, d);
+        else jacobi_kernel<256, T><<<B, 256, js, q>>>(w, d);
         WB_TRY(cudaGetLastError());
-      }
-      WB_TRY(gemm<T>(s, B, dmax, K, K, w.Q, dmax, L.sOm, 1, w.D, K, L.sD, 0, w.Bm, K, L.sBm,
-                     one, w.dsc, zero, w.ctl, C_ACTIVE, 2, nullptr, Live{d, 1 << 30, 1 << 30}));
-      WB_TRY(gemm<T>(s, B, d, d, K, w.Bm, K, L.sBm, 0, w.Bm, K, L.sBm, 1, w.E, dmax, L.sGy,
-                     one, nullptr, zero, w.ctl, C_ACTIVE, 2));
-      if (d > 32) jacobi_kernel<1024, T><<<B, 1024, js, s>>>(w, d);
-      else jacobi_kernel<256, T><<<B, 256, js, s>>>(w, d);
-      WB_TRY(cudaGetLastError());
-      rank_kernel<T><<<B, 256, 0, s>>>(a, w, it, d, last);
-      WB_TRY(cudaGetLastError());
+        rank_kernel<T><<<B, 256, 0, q>>>(a, w, it, d, last);
+        WB_TRY(cudaGetLastError());
+        return cudaSuccess;
+      });
+      if (e != cudaSuccess) return e;
       if (k0 < K) k0 *= 2;
     }
     if ((e = mark(2)) != cudaSuccess) return e;
-    const int g = 1 << WBRZF_BRANCH_WOODBURY;
-    // L = Q U_r, R^H = nu U_r^H B (nu undoes the scaling of dG), T = X L, Z = R^H X, C = Z L
-    // (U_r vanishes beyond rank r and sketch width d: live extents from the control words)
-    const Live all = live_none();
-    WB_TRY(gemm<T>(s, B, K, rcap, dmax, w.Q, dmax, L.sOm, 0, w.Ur, rcap, L.sUr, 0, w.Lm, rcap,
-                   L.sL, one, nullptr, zero, w.ctl, C_BRANCH, g, nullptr, all, -1, C_R, C_D));
-    WB_TRY(gemm<T>(s, B, rcap, K, dmax, w.Ur, rcap, L.sUr, 1, w.Bm, K, L.sBm, 0, w.Rh, K,
-                   L.sRh, one, w.nu, zero, w.ctl, C_BRANCH, g, nullptr, all, C_R, -1, C_D));
-    if (a.trace != nullptr) {
-      trace_lr_kernel<T><<<dim3((unsigned)((K * (size_t)rcap + 255) / 256), B), 256, 0, s>>>(a, w);
+    // Woodbury (eq. 12): one fused kernel per instance where the rank fits its shared memory
+    // (K <= 128), the batched products for the rest (marked kWoodburyWide) and for K > 128
+    const int RF = woodbury_fused_cap(K, rcap, sizeof(cx<T>));
+    if (RF > 0) WB_TRY(launch_woodbury_fused<T>(a, w, RF, s));
+    const int gw = RF > 0 ? (1 << kWoodburyWide) : (1 << WBRZF_BRANCH_WOODBURY);
+    e = guarded(s, sb, w.ctl, B, C_BRANCH, gw, [&](cudaStream_t q) -> cudaError_t {
+      cudaError_t e;
+      // L = Q U_r, R^H = nu U_r^H B (nu undoes the scaling of dG), T = X L, Z = R^H X,
+      // C = Z L (U_r vanishes beyond rank r and sketch width d: live extents from the control
+      // words)
+      const Live all = live_none();
+      WB_TRY(gemm<T>(q, B, K, rcap, dmax, w.Q, dmax, L.sOm, 0, w.Ur, rcap, L.sUr, 0, w.Lm, rcap,
+                     L.sL, one, nullptr, zero, w.ctl, C_BRANCH, gw, nullptr, all, -1, C_R, C_D));
+      WB_TRY(gemm<T>(q, B, rcap, K, dmax, w.Ur, rcap, L.sUr, 1, w.Bm, K, L.sBm, 0, w.Rh, K,
+                     L.sRh, one, w.nu, zero, w.ctl, C_BRANCH, gw, nullptr, all, C_R, -1, C_D));
+      if (a.trace != nullptr) {
+        trace_lr_kernel<T><<<dim3((unsigned)((K * (size_t)rcap + 255) / 256), B), 256, 0, q>>>(
+            a, w, gw);
+        WB_TRY(cudaGetLastError());
+      }
+      WB_TRY(gemm<T>(q, B, K, rcap, K, a.Xs, K, KK, 0, w.Lm, rcap, L.sL, 0, w.Tm, rcap, L.sL,
+                     one, nullptr, zero, w.ctl, C_BRANCH, gw, nullptr, all, -1, C_R, -1));
+      WB_TRY(gemm<T>(q, B, rcap, K, K, w.Rh, K, L.sRh, 0, a.Xs, K, KK, 0, w.Z, K, L.sRh, one,
+                     nullptr, zero, w.ctl, C_BRANCH, gw, nullptr, all, C_R, -1, -1));
+      WB_TRY(gemm<T>(q, B, rcap, rcap, K, w.Z, K, L.sRh, 0, w.Lm, rcap, L.sL, 0, w.Cm, rcap,
+                     L.sCm, one, nullptr, zero, w.ctl, C_BRANCH, gw, nullptr, all, C_R, C_R, -1));
+      capinv_kernel<T><<<B, 256, ps, q>>>(w, gw);
       WB_TRY(cudaGetLastError());
-    }
-    WB_TRY(gemm<T>(s, B, K, rcap, K, a.Xs, K, KK, 0, w.Lm, rcap, L.sL, 0, w.Tm, rcap, L.sL,
-                   one, nullptr, zero, w.ctl, C_BRANCH, g, nullptr, all, -1, C_R, -1));
-    WB_TRY(gemm<T>(s, B, rcap, K, K, w.Rh, K, L.sRh, 0, a.Xs, K, KK, 0, w.Z, K, L.sRh, one,
-                   nullptr, zero, w.ctl, C_BRANCH, g, nullptr, all, C_R, -1, -1));
-    WB_TRY(gemm<T>(s, B, rcap, rcap, K, w.Z, K, L.sRh, 0, w.Lm, rcap, L.sL, 0, w.Cm, rcap,
-                   L.sCm, one, nullptr, zero, w.ctl, C_BRANCH, g, nullptr, all, C_R, C_R, -1));
-    capinv_kernel<T><<<B, 256, ps, s>>>(w);
-    WB_TRY(cudaGetLastError());
-    WB_TRY(gemm<T>(s, B, rcap, K, rcap, w.Cm, rcap, L.sCm, 0, w.Z, K, L.sRh, 0, w.CZ, K, L.sRh,
-                   one, nullptr, zero, w.ctl, C_BRANCH, g, nullptr, all, C_R, -1, C_R));
-    WB_TRY(gemm<T>(s, B, K, K, rcap, w.Tm, rcap, L.sL, 0, w.CZ, K, L.sRh, 0, a.Xs, K, KK,
-                   T(-1), nullptr, one, w.ctl, C_BRANCH, g, nullptr, all, -1, -1, C_R));
+      WB_TRY(gemm<T>(q, B, rcap, K, rcap, w.Cm, rcap, L.sCm, 0, w.Z, K, L.sRh, 0, w.CZ, K,
+                     L.sRh, one, nullptr, zero, w.ctl, C_BRANCH, gw, nullptr, all, C_R, -1, C_R));
+      WB_TRY(gemm<T>(q, B, K, K, rcap, w.Tm, rcap, L.sL, 0, w.CZ, K, L.sRh, 0, a.Xs, K, KK,
+                     T(-1), nullptr, one, w.ctl, C_BRANCH, gw, nullptr, all, -1, -1, C_R));
+      return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
   }
   if (a.mode != MODE_UPDATE && (e = mark(2)) != cudaSuccess) return e;
   if ((e = mark(3)) != cudaSuccess) return e;
   // direct inverse by block exchange steps (instances whose branch asks for it)
-  copy_gx_kernel<T><<<dim3((unsigned)((KK + 255) / 256), B), 256, 0, s>>>(a, w);
-  WB_TRY(cudaGetLastError());
-  const int nb = (K + 31) / 32;
-  for (int p = 0; p < nb; ++p) {
-    const int bs = (K - 32 * p) < 32 ? (K - 32 * p) : 32;
-    panel_kernel<T><<<dim3((K * 32 + 255) / 256, B), 256, 0, s>>>(a, w, p, bs);
+  e = guarded(s, sb, w.ctl, B, C_BRANCH, kDirectMask, [&](cudaStream_t q) -> cudaError_t {
+    cudaError_t e;
+    copy_gx_kernel<T><<<dim3((unsigned)((KK + 255) / 256), B), 256, 0, q>>>(a, w);
     WB_TRY(cudaGetLastError());
-    blockinv_kernel<T><<<B, 256, 0, s>>>(w, bs);
-    WB_TRY(cudaGetLastError());
-    WB_TRY(gemm<T>(s, B, K, bs, bs, w.PC, 32, L.sPC, 0, w.Pb, 32, L.sPb, 0, w.PU, 32, L.sPC,
-                   one, nullptr, zero, w.ctl, C_BRANCH, kDirectMask));
-    WB_TRY(gemm<T>(s, B, bs, K, bs, w.Pb, 32, L.sPb, 0, w.PR, K, L.sPR, 0, w.PV, K, L.sPR, one,
-                   nullptr, zero, w.ctl, C_BRANCH, kDirectMask));
-    WB_TRY(gemm<T>(s, B, K, K, bs, w.PU, 32, L.sPC, 0, w.PR, K, L.sPR, 0, a.Xs, K, KK, T(-1),
-                   nullptr, one, w.ctl, C_BRANCH, kDirectMask));
-    fixup_kernel<T><<<dim3((K * 32 + 255) / 256, B), 256, 0, s>>>(a, w, p, bs);
-    WB_TRY(cudaGetLastError());
-  }
+    const int nb = (K + 31) / 32;
+    for (int p = 0; p < nb; ++p) {
+      const int bs = (K - 32 * p) < 32 ? (K - 32 * p) : 32;
+      panel_kernel<T><<<dim3((K * 32 + 255) / 256, B), 256, 0, q>>>(a, w, p, bs);
+      WB_TRY(cudaGetLastError());
+      blockinv_kernel<T><<<B, 256, 0, q>>>(w, bs);
+      WB_TRY(cudaGetLastError());
+      WB_TRY(gemm<T>(q, B, K, bs, bs, w.PC, 32, L.sPC, 0, w.Pb, 32, L.sPb, 0, w.PU, 32, L.sPC,
+                     one, nullptr, zero, w.ctl, C_BRANCH, kDirectMask));
+      WB_TRY(gemm<T>(q, B, bs, K, bs, w.Pb, 32, L.sPb, 0, w.PR, K, L.sPR, 0, w.PV, K, L.sPR,
+                     one, nullptr, zero, w.ctl, C_BRANCH, kDirectMask));
+      WB_TRY(gemm<T>(q, B, K, K, bs, w.PU, 32, L.sPC, 0, w.PR, K, L.sPR, 0, a.Xs, K, KK, T(-1),
+                     nullptr, one, w.ctl, C_BRANCH, kDirectMask));
+      fixup_kernel<T><<<dim3((K * 32 + 255) / 256, B), 256, 0, q>>>(a, w, p, bs);
+      WB_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
   if ((e = mark(4)) != cudaSuccess) return e;
   if (a.refine) {
     // one Newton step for G^-1 with the FP32-faithful G: X <- X (2 I - G X); it squares the
@@ -1145,11 +1510,11 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
 
 namespace wbk {
 cudaError_t run_blocked_f32(const StepArgs<float>& a, unsigned char* base, cudaStream_t s,
-                            int* launches, cudaEvent_t* ev) {
-  return run_blocked<float>(a, base, s, launches, ev);
+                            cudaStream_t sb, int* launches, cudaEvent_t* ev) {
+  return run_blocked<float>(a, base, s, sb, launches, ev);
 }
 cudaError_t run_blocked_f64(const StepArgs<double>& a, unsigned char* base, cudaStream_t s,
-                            int* launches, cudaEvent_t* ev) {
-  return run_blocked<double>(a, base, s, launches, ev);
+                            cudaStream_t sb, int* launches, cudaEvent_t* ev) {
+  return run_blocked<double>(a, base, s, sb, launches, ev);
 }
 }  // namespace wbk

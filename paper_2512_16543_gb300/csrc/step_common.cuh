@@ -243,10 +243,11 @@ __host__ __device__ inline BlockedSmem blocked_smem(int dmax, int rcap, size_t c
 }
 
 // Shared memory of the blocked engine's fused Algorithm 1 kernel (K <= 128, sketch width up
-// to df): Omega and Q (K x df), B (df x K), a 16 x K staging block of dG, the d x d Gram /
-// eigenvector blocks, and the small per-column arrays.
+// to df): Omega and Q (K x df), B (df x K), the d x d Gram / eigenvector blocks, the small
+// per-column arrays, and two K x (kChunkCols + 1) buffers through which dG is streamed.
+constexpr int kChunkLg = 3;                 // dG / X streamed in chunks of 8 columns or rows
 struct FusedLayout {
-  size_t oOm, oQ, oB, oS, oGy, oUh, oLam, oRs, oCn, oRed, oPerm, oDrop, oFlags, bytes;
+  size_t oOm, oQ, oB, oGy, oUh, oLam, oRs, oCn, oRed, oPerm, oDrop, oFlags, oBuf, bytes;
 };
 __host__ __device__ inline FusedLayout fused_layout(int K, int df, size_t cxb, size_t tb) {
   FusedLayout F;
@@ -255,7 +256,6 @@ __host__ __device__ inline FusedLayout fused_layout(int K, int df, size_t cxb, s
   F.oOm = take((size_t)K * df * cxb);
   F.oQ = take((size_t)K * df * cxb);
   F.oB = take((size_t)df * K * cxb);
-  F.oS = take((size_t)16 * K * cxb);
   F.oGy = take((size_t)df * df * cxb);
   F.oUh = take((size_t)df * df * cxb);
   F.oLam = take((size_t)df * tb);
@@ -265,6 +265,7 @@ __host__ __device__ inline FusedLayout fused_layout(int K, int df, size_t cxb, s
   F.oPerm = take((size_t)df * sizeof(int));
   F.oDrop = take((size_t)df * sizeof(int));
   F.oFlags = take(8 * sizeof(int));
+  F.oBuf = take(2 * (size_t)K * ((1 << kChunkLg) + 1) * cxb);
   F.bytes = o;
   return F;
 }
@@ -280,14 +281,16 @@ __host__ __device__ inline size_t trace_record_bytes(int K, int dmax, int rcap, 
 cudaError_t launch_step_f32(const StepArgs<float>& a, size_t smem, cudaStream_t s);
 cudaError_t launch_step_f64(const StepArgs<double>& a, size_t smem, cudaStream_t s);
 // Blocked engine (any K): a fixed sequence of batched kernels on `stream`; `base` is the
-// blocked scratch (blocked_layout) of the workspace (blocked.cu).
+// blocked scratch (blocked_layout) of the workspace (blocked.cu).  sb: a second stream of the
+// caller (not capturing), on which the bodies of CUDA-graph IF nodes are recorded when `s` is
+// being captured (NULL: no IF nodes).
 // *launches receives the number of kernels enqueued.  ev: NULL, or six events recorded on the
 // stream at the stage boundaries (start, after the Gram matrix and dG, after Algorithm 1,
 // after the Woodbury update, after the direct inverse, end).
 cudaError_t run_blocked_f32(const StepArgs<float>& a, unsigned char* base, cudaStream_t s,
-                            int* launches, cudaEvent_t* ev);
+                            cudaStream_t sb, int* launches, cudaEvent_t* ev);
 cudaError_t run_blocked_f64(const StepArgs<double>& a, unsigned char* base, cudaStream_t s,
-                            int* launches, cudaEvent_t* ev);
+                            cudaStream_t sb, int* launches, cudaEvent_t* ev);
 // Tensor-core products of the blocked engine (complex64, tc_gemm.cu): the Gram matrix into
 // D (upper triangle, instance stride sD) and W = s H^H X; P, T, XB are the operand buffers of
 // the blocked layout; a timeout ORs WBRZF_STATUS_TIMEOUT into stat[stat_stride * b];

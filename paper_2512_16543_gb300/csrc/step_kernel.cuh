@@ -357,6 +357,185 @@ __device__ void jacobi_round(cx<T>* E, cx<T>* U, int dmax, int d, int rnd, int* 
   __syncthreads();
 }
 
+// Pair k of round rnd of the round-robin ordering of dd indices (dm1 = dd - 1): index 0 is
+// fixed, indices 1 .. dm1 sit on a circle that turns by one place per round; pair 0 is
+// (0, x_0) and pair k (x_k, x_{dm1-k}) with x_j = 1 + (j + rnd) mod dm1.  Every dm1 rounds
+// visit every pair once.
+__device__ __forceinline__ void rr_pair(int k, int rnd, int dm1, int& p, int& q) {
+  if (k == 0) { p = 0; q = 1 + rnd; }
+  else {
+    int a1 = k + rnd, a2 = dm1 - k + rnd;
+    if (a1 >= dm1) a1 -= dm1;
+    if (a2 >= dm1) a2 -= dm1;
+    p = 1 + a1;
+    q = 1 + a2;
+  }
+}
+
+// Circle positions of pair k in round rnd (see rr_pair): x = (k + rnd) mod dm1 and
+// y = (dm1 - k + rnd) mod dm1; pair k is (0, 1 + x) for k = 0, else (1 + x, 1 + y).  Both
+// advance by one (mod dm1) per round, so they are kept in registers and stepped.
+struct RrPos {
+  int x, y;
+  __device__ __forceinline__ void init(int k, int dm1) {
+    x = k % dm1;
+    y = (dm1 - k) % dm1;
+  }
+  __device__ __forceinline__ void step(int dm1) {
+    x = x + 1 == dm1 ? 0 : x + 1;
+    y = y + 1 == dm1 ? 0 : y + 1;
+  }
+  __device__ __forceinline__ void pair(int k, int& p, int& q) const {
+    p = k == 0 ? 0 : 1 + x;
+    q = k == 0 ? 1 + x : 1 + y;
+  }
+};
+
+// Apply pair l's column rotation and pair k's row rotation to block (k, l) of E and the column
+// rotation to rows 2k, 2k + 1 of U (one lane's share of a Jacobi round; see jacobi_eig_warp).
+// The rotations (c, s, f) are in lane k / lane l and are read by shuffles, so every lane of the
+// warp must call this; `own` says whether the calling lane has a block.
+template <class T>
+__device__ __forceinline__ void jacobi_block(cx<T>* E, int ldE, cx<T>* U, int ldU, int d,
+                                             bool own, int k, int l, int rp, int rq, int cp,
+                                             int cq, T c, T sn, cx<T> f) {
+  cx<T> a00, a01, a10, a11;
+  {   // column rotation (pair l): col_p <- c col_p - s f col_q;  col_q <- s col_p + c f col_q,
+      // on U's rows 2k, 2k + 1 first, then on E's block
+    const T cl = __shfl_sync(0xffffffffu, c, l), sl = __shfl_sync(0xffffffffu, sn, l);
+    const cx<T> fl = cmk<T>(__shfl_sync(0xffffffffu, f.re, l),
+                            __shfl_sync(0xffffffffu, f.im, l));
+    if (own) {
+      if (cp < d && cq < d) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int u = 2 * k + h;
+          if (u < d) {
+            const cx<T> b0 = U[u * ldU + cp], b1 = cmul(fl, U[u * ldU + cq]);
+            U[u * ldU + cp] = csub(cscale(b0, cl), cscale(b1, sl));
+            U[u * ldU + cq] = cadd(cscale(b0, sl), cscale(b1, cl));
+          }
+        }
+      }
+      a00 = (rp < d && cp < d) ? E[rp * ldE + cp] : cmk<T>(0, 0);
+      a01 = (rp < d && cq < d) ? E[rp * ldE + cq] : cmk<T>(0, 0);
+      a10 = (rq < d && cp < d) ? E[rq * ldE + cp] : cmk<T>(0, 0);
+      a11 = (rq < d && cq < d) ? E[rq * ldE + cq] : cmk<T>(0, 0);
+      const cx<T> q0 = cmul(fl, a01), q1 = cmul(fl, a11);
+      const cx<T> n00 = csub(cscale(a00, cl), cscale(q0, sl));
+      const cx<T> n01 = cadd(cscale(a00, sl), cscale(q0, cl));
+      const cx<T> n10 = csub(cscale(a10, cl), cscale(q1, sl));
+      const cx<T> n11 = cadd(cscale(a10, sl), cscale(q1, cl));
+      a00 = n00; a01 = n01; a10 = n10; a11 = n11;
+    }
+  }
+  {   // row rotation (pair k): row_p <- c row_p - s conj(f) row_q;  row_q <- s row_p + c conj(f) row_q
+    const T ck = __shfl_sync(0xffffffffu, c, k), sk = __shfl_sync(0xffffffffu, sn, k);
+    const cx<T> fc = cmk<T>(__shfl_sync(0xffffffffu, f.re, k),
+                            -__shfl_sync(0xffffffffu, f.im, k));
+    if (own) {
+      const cx<T> q0 = cmul(fc, a10), q1 = cmul(fc, a11);
+      if (rp < d && cp < d) E[rp * ldE + cp] = csub(cscale(a00, ck), cscale(q0, sk));
+      if (rq < d && cp < d) E[rq * ldE + cp] = cadd(cscale(a00, sk), cscale(q0, ck));
+      if (rp < d && cq < d) E[rp * ldE + cq] = csub(cscale(a01, ck), cscale(q1, sk));
+      if (rq < d && cq < d) E[rq * ldE + cq] = cadd(cscale(a01, sk), cscale(q1, ck));
+    }
+  }
+}
+
+// Cyclic two-sided Jacobi eigendecomposition E = U Lambda U^H of the Hermitian d x d matrix E
+// (ld ldE, shared memory; d <= 64) by one warp, U (ld ldU) accumulated from I.  Each round
+// rotates the P = ceil(d / 2) disjoint pairs of the round-robin ordering at once (an odd d
+// gets a zero padding index, which never rotates): lane k < P takes pair k's rotation
+// (jacobi_rotation) from E_pp, E_qq, E_pq and keeps it in registers; then lane l owns the
+// blocks l, l + 32, ... of the P x P grid of 2 x 2 blocks -- block (k, l) is rows (p_k, q_k)
+// and columns (p_l, q_l) of E, and rows (2k, 2k + 1), columns (p_l, q_l) of U -- reads the two
+// rotations it needs by shuffles and applies E <- J_k^H E J_l and U <- U J_l to it.  Blocks
+// are disjoint, so a round needs one __syncwarp.  A pair with |E_pq|^2 <= tol2 tr(E)^2 is left
+// alone (tr(E) does not change under the rotations).  Each sweep (dm1 rounds, every pair
+// once) starts with a check of all pairs, and the rotations stop when none is above the
+// threshold -- every pair is then at most tol2^(1/2) tr(E) off the diagonal -- or after
+// max_sweeps sweeps.  The pair indices are stepped in registers (RrPos), without divisions.
+// On exit E's diagonal holds the eigenvalues and U's columns the eigenvectors.  Called by the
+// 32 lanes of one warp.
+template <class T>
+__device__ __noinline__ void jacobi_eig_warp(cx<T>* E, int ldE, cx<T>* U, int ldU, int d,
+                                             T tol2, int max_sweeps) {
+  const int lane = threadIdx.x & 31;
+  const int dd = d + (d & 1), P = dd >> 1, dm1 = dd - 1;
+  const int nbl = (P * P + 31) >> 5;
+  for (int i = 0; i < d; ++i)
+    for (int j = lane; j < d; j += 32) U[i * ldU + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
+  T tr = 0;                                  // every lane sums the diagonal in one order
+  for (int j = 0; j < d; ++j) tr += E[j * ldE + j].re;
+  const T thr = tol2 * tr * tr;
+  // this lane's block in the first slot (all of them for d <= 10) is stepped in registers;
+  // later slots are placed per round
+  const bool own0 = lane < P * P;
+  const int k0 = own0 ? lane / P : 0, l0 = own0 ? lane - k0 * P : 0;
+  RrPos me, rk0, cl0;
+  me.init(lane < P ? lane : 0, dm1);
+  rk0.init(k0, dm1);
+  cl0.init(l0, dm1);
+  __syncwarp();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // convergence check: the largest |E_pq|^2 over p < q (lane i: rows i, i + 32)
+    T mx = 0;
+    for (int i = lane; i < d; i += 32)
+      for (int j = i + 1; j < d; ++j) mx = fmax(mx, cabs2(E[i * ldE + j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (!(mx > thr)) break;
+    for (int rnd = 0; rnd < dm1; ++rnd) {
+      T c = 1, sn = 0;
+      cx<T> f = cmk<T>(1, 0);
+      bool act = false;
+      if (lane < P) {
+        int p, q;
+        me.pair(lane, p, q);
+        if (p < d && q < d) {
+          const cx<T> epq = E[p * ldE + q];
+          act = cabs2(epq) > thr &&
+                jacobi_rotation<T>(epq, E[p * ldE + p].re, E[q * ldE + q].re, c, sn, f);
+        }
+        if (!act) { c = 1; sn = 0; f = cmk<T>(1, 0); }
+      }
+      if (__ballot_sync(0xffffffffu, act) != 0u) {     // uniform
+        int rp, rq, cp, cq;
+        rk0.pair(k0, rp, rq);
+        cl0.pair(l0, cp, cq);
+        jacobi_block<T>(E, ldE, U, ldU, d, own0, k0, l0, rp, rq, cp, cq, c, sn, f);
+        for (int slot = 1; slot < nbl; ++slot) {
+          const int bi = lane + 32 * slot;
+          const bool own = bi < P * P;
+          const int k = own ? bi / P : 0, l = own ? bi - k * P : 0;
+          RrPos rk, cl;
+          rk.init(k + rnd, dm1);
+          cl.init(l + rnd, dm1);
+          rk.y = (dm1 - k + rnd) % dm1;
+          cl.y = (dm1 - l + rnd) % dm1;
+          rk.pair(k, rp, rq);
+          cl.pair(l, cp, cq);
+          jacobi_block<T>(E, ldE, U, ldU, d, own, k, l, rp, rq, cp, cq, c, sn, f);
+        }
+        __syncwarp();
+      }
+      me.step(dm1);
+      rk0.step(dm1);
+      cl0.step(dm1);
+    }
+  }
+}
+
+// Eigendecomposition of E (d x d Hermitian) on warp 0 (jacobi_eig_warp).  Must be reached by
+// all threads of the CTA; ends with a CTA barrier.
+template <class T>
+__device__ __forceinline__ void jacobi_eig(cx<T>* E, int ldE, cx<T>* U, int ldU, int d, T tol2,
+                                           int max_sweeps) {
+  if (threadIdx.x < 32) jacobi_eig_warp<T>(E, ldE, U, ldU, d, tol2, max_sweeps);
+  __syncthreads();
+}
+
 // One-sided (Hestenes) cyclic Jacobi on the rows of B (d x K, ld K; K <= 8 EPL, d <= 64) by
 // the kThreads threads of a CTA.  Each round rotates the disjoint pairs of the round-robin
 // ordering at once, pair k on the eight lanes 8k .. 8k + 7: lane l holds columns l + 8 e
@@ -474,6 +653,57 @@ __device__ void hestenes_jacobi(cx<T>* Bm, int K, cx<T>* U, int dmax, int d, T t
     else if (++quiet >= dm1) break;
   }
   __syncthreads();
+}
+
+// ------------------------------------------------------------------ small pivoted solve
+// Gauss-Jordan elimination with partial pivoting [C | Z] -> [I | C^{-1} Z] by one warp, for
+// C (n x n) in columns 0 .. n-1 and Z (n x nz) in columns zc .. zc + nz - 1 of the row-major
+// block CZ (ld ldcz, shared memory).  Column c's pivot is the largest |C_ic| over i >= c (the
+// first on ties); a pivot at most piv_tol, or not finite, marks the system singular.  Each
+// lane owns whole columns, so one pivot step needs no barrier between reading column c and
+// updating: column c itself (and every finished column of C, which would hold the identity)
+// is not written.  Returns the singular flag, the same in every lane; called by the 32 lanes
+// of one warp.
+template <class T>
+__device__ bool gauss_jordan_warp(cx<T>* CZ, int ldcz, int n, int zc, int nz, T piv_tol) {
+  const int lane = threadIdx.x & 31;
+  const int ncol = n + nz;
+  bool singular = false;
+  for (int c = 0; c < n; ++c) {
+    T v = T(-1);
+    int pr = n;
+    for (int i = c + lane; i < n; i += 32) {
+      const T x = cabs2(CZ[i * ldcz + c]);
+      if (x > v) { v = x; pr = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int op = __shfl_xor_sync(0xffffffffu, pr, o);
+      if (ov > v || (ov == v && op < pr)) { v = ov; pr = op; }
+    }
+    if (!(sqrt(v) > piv_tol) || !isfinite(v)) singular = true;
+    if (pr >= n) pr = c;                       // no usable entry: keep the row (singular)
+    if (pr != c) {
+      for (int j = c + lane; j < ncol; j += 32) {
+        const int col = j < n ? j : zc + (j - n);
+        const cx<T> t0 = CZ[c * ldcz + col];
+        CZ[c * ldcz + col] = CZ[pr * ldcz + col];
+        CZ[pr * ldcz + col] = t0;
+      }
+      __syncwarp();
+    }
+    const cx<T> ip = crecip(CZ[c * ldcz + c]);
+    for (int j = c + 1 + lane; j < ncol; j += 32) {
+      const int col = j < n ? j : zc + (j - n);
+      const cx<T> rcj = cmul(CZ[c * ldcz + col], ip);
+      for (int i = 0; i < n; ++i)
+        if (i != c) CZ[i * ldcz + col] = csub(CZ[i * ldcz + col], cmul(CZ[i * ldcz + c], rcj));
+      CZ[c * ldcz + col] = rcj;
+    }
+    __syncwarp();
+  }
+  return singular;
 }
 
 // ------------------------------------------------------------------ CholQR steps, d <= DM
@@ -620,8 +850,9 @@ __device__ void cholqr_pass_smem(cx<T>* Q, int ldq, int K, int d, cx<T>* Gy, int
 // Given G_t in w.G (Hermitian, alpha on the diagonal), run the perturbation, the low-rank
 // step, the Woodbury update or direct inverse, the state write-back, the power scale and the
 // SINR / sum-rate.  Leaves X in w.X and returns the precoder scale s.
-// JEPL: columns of B per lane in the Jacobi step (K <= 8 JEPL).
-template <class T, int JEPL>
+// LARGEK: the instantiation for K > 32 (svd(B) by the two-sided Jacobi on E = B B^H); the
+// other one serves K <= 32 (one-sided Jacobi on B's rows).
+template <class T, bool LARGEK>
 __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
   // On entry for MODE_UPDATE, w.D holds G_{t-1} and w.X holds X_{t-1}: the kernels copy them
   // from the resident state with cp.async (prefetch_state) while the Gram matrix is formed.
@@ -734,34 +965,45 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       // 3d. projection B = Q^H dG  (d x K)
       mm<T, true, false, MM_SET>(d, K, K, Q, dmax, D, K, Bm, K);
       __syncthreads();
-      // 3e. svd(B): one-sided Jacobi on B's rows.  B becomes U^H B with orthogonal rows, its
-      // squared row norms are sigma_hat^2 and U's columns the left singular vectors.
-      // Converged when no pair has |b_p b_q^H|^2 above tol2 tr(B B^H)^2: FP32 1e-8 (each
-      // off-diagonal entry of E = B B^H then at most 1e-4 of its trace, which leaves the
-      // eigenvalues -- the energy rule's input -- exact to second order, about 1e-8 relative
-      // to their gaps, and turns the singular vectors by about 1e-4; the Woodbury correction
-      // is ||dG|| / ||G|| ~ 1e-5 of X, so that moves X by about 1e-9 relative, far below its
-      // FP32 rounding); FP64 1e-28.
-      for (int e = tid; e < d * d; e += kThreads) {
-        const int i = e / d, j = e - i * d;
-        Uh[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
-      }
-      __syncthreads();
+      // 3e. svd(B).  Converged when no pair of rows of B has |b_p b_q^H|^2 above tol2
+      // tr(B B^H)^2: FP32 1e-8 (each off-diagonal entry of E = B B^H then at most 1e-4 of its
+      // trace, which leaves the eigenvalues -- the energy rule's input -- exact to second
+      // order, about 1e-8 relative to their gaps, and turns the singular vectors by about
+      // 1e-4; the Woodbury correction is ||dG|| / ||G|| ~ 1e-5 of X, so that moves X by about
+      // 1e-9 relative, far below its FP32 rounding); FP64 1e-28.
+      //   K <= 32: one-sided Jacobi on B's rows (short rows: one 8-lane group per pair).  B
+      //     becomes U^H B with orthogonal rows, whose squared norms are sigma_hat^2.
+      //   K > 32: two-sided Jacobi on E = B B^H (d x d, into Gy: Y^H Y is dead) on one warp,
+      //     whose cost does not grow with K; sigma_hat^2 is E's rotated diagonal.
+      // Either way U_hat (in Uh) holds the left singular vectors of B, and R^H = U_r^H B is
+      // formed from the unrotated B below when B was not rotated.
       {
         const T tol2 = (sizeof(T) == 4) ? T(1e-8) : T(1e-28);
         const int sweeps = (sizeof(T) == 4) ? 12 : 20;
-        if (JEPL == 4 || K <= 32) hestenes_jacobi<T, 4>(Bm, K, Uh, dmax, d, tol2, sweeps, misc + 6, red);
-        else hestenes_jacobi<T, JEPL>(Bm, K, Uh, dmax, d, tol2, sweeps, misc + 6, red);
-      }
-      // 3f. sigma_hat^2 (squared row norms of the rotated B) sorted descending
-      for (int j0 = (tid >> 5) * 2; j0 < d; j0 += kThreads / 16) {   // warp-uniform loop
-        const int j = j0 + ((tid >> 4) & 1);
-        T v = 0;
-        if (j < d)
-          for (int k = tid & 15; k < K; k += 16) v += cabs2(Bm[j * K + k]);
+        if (!LARGEK) {
+          for (int e = tid; e < d * d; e += kThreads) {
+            const int i = e / d, j = e - i * d;
+            Uh[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
+          }
+          __syncthreads();
+          hestenes_jacobi<T, 4>(Bm, K, Uh, dmax, d, tol2, sweeps, misc + 6, red);
+          // 3f. sigma_hat^2 (squared row norms of the rotated B) sorted descending
+          for (int j0 = (tid >> 5) * 2; j0 < d; j0 += kThreads / 16) {   // warp-uniform loop
+            const int j = j0 + ((tid >> 4) & 1);
+            T v = 0;
+            if (j < d)
+              for (int k = tid & 15; k < K; k += 16) v += cabs2(Bm[j * K + k]);
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((tid & 15) == 0 && j < d) lam[j] = v;
+            for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((tid & 15) == 0 && j < d) lam[j] = v;
+          }
+        } else {
+          mm<T, false, true, MM_SET>(d, d, K, Bm, K, Bm, K, Gy, dmax);
+          __syncthreads();
+          jacobi_eig<T>(Gy, dmax, Uh, dmax, d, tol2, sweeps);
+          // 3f. sigma_hat^2 (the diagonal of the rotated E) sorted descending
+          if (tid < d) lam[tid] = fmax(Gy[tid * dmax + tid].re, T(0));
+        }
       }
       __syncthreads();
       if (tid < d) {
@@ -813,10 +1055,16 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       Lm[i * rcap + c] = acc;
     }
     const T up = pow2(dg_exp, T(0));         // undo the scaling of dG: dG = L (up R^H)
-    // R^H = U_r^H B: the leading rows of the rotated B (which holds U^H B)
+    // R^H = U_r^H B (r x K) = Sigma_r V_r^H: the leading rows of the rotated B (K <= 32, where
+    // B holds U^H B), else the product with the unrotated B
     for (int idx = tid; idx < r * K; idx += kThreads) {
       const int c = idx / K, j = idx - c * K;
-      Rh[c * K + j] = cscale(Bm[perm[c] * K + j], up);
+      const int pc = perm[c];
+      cx<T> acc = cmk<T>(0, 0);
+      if (!LARGEK) acc = Bm[pc * K + j];
+      else
+        for (int k = 0; k < d; ++k) cfma_jc(acc, Uh[k * dmax + pc], Bm[k * K + j]);
+      Rh[c * K + j] = cscale(acc, up);
     }
     __syncthreads();
     if (a.trace != nullptr) {
@@ -844,63 +1092,20 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       CZ[c * ldcz + e] = acc;
     }
     __syncthreads();
-    // Gauss-Jordan with partial pivoting on [C | Z] -> [I | C^{-1} Z]
-    T cmax = 0;
-    for (int idx = tid; idx < r * r; idx += kThreads) {
-      const int c = idx / r, e = idx - c * r;
-      cmax = fmax(cmax, sqrt(cabs2(CZ[c * ldcz + e])));
-    }
-    {
-      // block max via sum of a one-hot trick is awkward; use shared slot with atomic-free pass
+    // Gauss-Jordan with partial pivoting on [C | Z] -> [I | C^{-1} Z] on warp 0; a pivot at
+    // most 1e-6 (FP32) / 1e-14 (FP64) of max |C_ij| marks C numerically singular
+    if (tid < 32) {
+      T cmax = 0;
+      for (int idx = tid; idx < r * r; idx += 32) {
+        const int c = idx / r, e = idx - c * r;
+        cmax = fmax(cmax, sqrt(cabs2(CZ[c * ldcz + e])));
+      }
       for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-      if ((tid & 31) == 0) red[tid >> 5] = cmax;
-      __syncthreads();
-      if (tid == 0) {
-        T m = 0;
-        for (int w = 0; w < kThreads / 32; ++w) m = fmax(m, red[w]);
-        red[33] = m;
-        misc[1] = 0;
-      }
-      __syncthreads();
-      cmax = red[33];
+      const T piv_tol = cmax * ((sizeof(T) == 4) ? T(1e-6) : T(1e-14));
+      const bool singular = gauss_jordan_warp<T>(CZ, ldcz, r, rcap, K, piv_tol);
+      if (tid == 0) misc[1] = singular ? 1 : 0;
     }
-    const T piv_tol = cmax * ((sizeof(T) == 4) ? T(1e-6) : T(1e-14));
-    for (int c = 0; c < r; ++c) {
-      if (tid == 0) {
-        int pr = c;
-        T best = -1;
-        for (int i = c; i < r; ++i) {
-          const T v = cabs2(CZ[i * ldcz + c]);
-          if (v > best) { best = v; pr = i; }
-        }
-        misc[2] = pr;
-        if (!(sqrt(best) > piv_tol) || !isfinite(best)) misc[1] = 1;
-      }
-      __syncthreads();
-      const int pr = misc[2];
-      if (pr != c) {
-        for (int j = tid; j < ldcz; j += kThreads) {
-          const cx<T> t0 = CZ[c * ldcz + j];
-          CZ[c * ldcz + j] = CZ[pr * ldcz + j];
-          CZ[pr * ldcz + j] = t0;
-        }
-        __syncthreads();
-      }
-      const cx<T> ipiv = crecip(CZ[c * ldcz + c]);
-      if (tid < r) tmp[tid] = CZ[tid * ldcz + c];    // column c before elimination
-      __syncthreads();
-      for (int j = tid; j < ldcz; j += kThreads) CZ[c * ldcz + j] = cmul(CZ[c * ldcz + j], ipiv);
-      __syncthreads();
-      for (int e = tid; e < r * ldcz; e += kThreads) {
-        const int i = e / ldcz, j = e - i * ldcz;
-        if (i != c) {
-          cx<T> v = CZ[e];
-          v = csub(v, cmul(tmp[i], CZ[c * ldcz + j]));
-          CZ[e] = v;
-        }
-      }
-      __syncthreads();
-    }
+    __syncthreads();
     if (misc[1]) {
       branch = WBRZF_BRANCH_FALLBACK;
     } else {
@@ -1077,7 +1282,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
 // ------------------------------------------------------------------ the SIMT kernel
 // General path: any K <= kMaxK, complex64 or complex128, the Gram matrix and the precoder
 // computed with FP32 / FP64 fused multiply-adds from H staged by cp.async.
-template <class T>
+template <class T, bool LARGEK>
 __global__ void __launch_bounds__(kThreads, 2) wbrzf_step_kernel(const StepArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
@@ -1145,8 +1350,7 @@ __global__ void __launch_bounds__(kThreads, 2) wbrzf_step_kernel(const StepArgs<
     __syncthreads();
   }
 
-  static_assert(8 * 8 >= kMaxK, "Jacobi columns per lane");
-  const T s = core_phases<T, 8>(a, w, b);
+  const T s = core_phases<T, LARGEK>(a, w, b);
   cx<T>* const X = w.X;
 
   // ---------------------------------------------------------------- 7. precoder W = s H^H X

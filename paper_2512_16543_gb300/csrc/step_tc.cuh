@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 4) wbrzf_step_tc_kernel(const StepAr
   cp_async_wait<0>();
   __syncthreads();
   const Work<float> w = carve_work<float>(uni, K, a.dmax, a.rcap, G, X, Dm);
-  const float s = core_phases<float, 4>(a, w, b);   // K <= 32
+  const float s = core_phases<float, false>(a, w, b);   // K <= 32
   __syncthreads();
 
   // ------------------------------------------------------------ 7. W = s H^H X on tensor cores

@@ -180,6 +180,8 @@ struct wbrzf {
   bool in_group;         // stepped by a wbrzf_group (its stream belongs to the group)
   int gemm_bf16;         // wbrzf_set_precision_mode: BF16 precoder product
   int refine;            // wbrzf_set_precision_mode: Newton refinement steps (0 or 1)
+  cudaStream_t cstream;  // blocked engine: records the bodies of CUDA-graph IF nodes while a
+                         // step is captured (its own captures only; never runs work)
 };
 
 namespace {
@@ -251,9 +253,11 @@ wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode,
     int nl = 0;
     cudaEvent_t* ev = h->timing ? h->ev : nullptr;
     if (h->prec == WBRZF_C128)
-      e = run_blocked_f64(make_args<double>(h, H, W, mode, active), base, h->stream, &nl, ev);
+      e = run_blocked_f64(make_args<double>(h, H, W, mode, active), base, h->stream, h->cstream,
+                          &nl, ev);
     else
-      e = run_blocked_f32(make_args<float>(h, H, W, mode, active), base, h->stream, &nl, ev);
+      e = run_blocked_f32(make_args<float>(h, H, W, mode, active), base, h->stream, h->cstream,
+                          &nl, ev);
     if (e != cudaSuccess) return cuda_fail(e);
     h->last_engine =
         h->engine == WBRZF_ENGINE_BLOCKED_FMA ? WBRZF_ENGINE_BLOCKED_FMA : WBRZF_ENGINE_BLOCKED;
@@ -461,6 +465,7 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   h->in_group = false;
   h->gemm_bf16 = 0;
   h->refine = 0;
+  h->cstream = nullptr;
   {
     const size_t tc = tc_smem_bytes(K, r.dmax, r.rcap);
     h->smem_tc = (simt_ok && prec == WBRZF_C64 && K <= 32 && tc <= 227 * 1024) ? tc : 0;
@@ -492,8 +497,13 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
     e = cudaMemcpyAsync(h->ws + wl.oIds, ids, batch * sizeof(uint32_t), cudaMemcpyHostToDevice,
                         h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && blocked_ok) e = cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking);
   free(host);
-  if (e != cudaSuccess) { delete h; return cuda_fail(e); }
+  if (e != cudaSuccess) {
+    if (h->cstream) cudaStreamDestroy(h->cstream);
+    delete h;
+    return cuda_fail(e);
+  }
   *out = h;
   return WBRZF_OK;
 }
@@ -738,6 +748,7 @@ void wbrzf_destroy(wbrzf* h) {
   if (h->timing)
     for (int i = 0; i < 6; ++i) cudaEventDestroy(h->ev[i]);
   wbrzf_set_graph(h, 0);
+  if (h->cstream) cudaStreamDestroy(h->cstream);
   delete h;
 }
 

@@ -57,6 +57,43 @@ def test_graph_replay_gives_the_enqueued_bits(engine, prec):
     g.close()
 
 
+def test_graph_replay_with_conditional_blocks_at_k128():
+    """The blocked engine at K = 128 (N = 256) under CUDA-graph replay, where Algorithm 1's
+    iterations beyond the fused kernel's sketch widths, the batched Woodbury products and the
+    direct inverse are IF nodes of the graph, skipped when no instance needs them: eta = 0.99
+    makes some instances iterate past the fused widths, and the periodic re-inversion (every 3
+    snapshots) switches the direct inverse on and off.  Replay gives the enqueued bits."""
+    sc = channel.LeoScenario(n_x=16, n_y=16, K=128, disc_radius=100e3)
+    B, T = 4, 8
+    Hs = channel.trajectory(channel.draw_trajectories(sc, B, seed=128), T,
+                            dtype=torch.complex64).cuda()
+    rule = binding.RankRule(eta=0.99, k_init=2, p=8, r_max=64, reinverse_period=3, seed=5)
+    a = _handle(sc, B, "c64", rule, "blocked")
+    g = _handle(sc, B, "c64", rule, "blocked")
+    g.set_graph(True)
+    Hbuf = torch.empty_like(Hs[0])
+    Wa = torch.empty(B, sc.N, sc.K, dtype=torch.complex64, device="cuda")
+    Wg = torch.empty_like(Wa)
+    iters = set()
+    for t in range(T):
+        Hbuf.copy_(Hs[t])
+        if t == 0:
+            a.full_inverse(Hbuf, Wa)
+            g.full_inverse(Hbuf, Wg)
+        else:
+            a.update(Hbuf, Wa)
+            g.update(Hbuf, Wg)
+        torch.cuda.synchronize()
+        assert torch.equal(Wa, Wg), t
+        assert torch.equal(a.state()[1], g.state()[1]), t
+        info = a.step_info()
+        assert info == g.step_info()
+        iters |= {i["iters"] for i in info}
+    assert max(iters) >= 3           # iterations beyond the fused widths (d <= 24) were taken
+    a.close()
+    g.close()
+
+
 def _classes():
     return [(channel.LeoScenario(n_x=8, n_y=8, K=8), 3, "simt"),
             (channel.scenario_batched_256x32(), 4, "tensor"),
