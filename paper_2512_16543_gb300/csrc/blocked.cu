@@ -518,6 +518,14 @@ __global__ void __launch_bounds__(256) rank_kernel(const StepArgs<T> a, const Bu
   }
 }
 
+// Ask L2 for n bytes from p (128-byte lines, spread over the CTA's threads) so that a later
+// stream of them does not wait on DRAM; no data moves into the CTA.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t n) {
+  const char* c = static_cast<const char*>(p);
+  for (size_t o = (size_t)threadIdx.x * 128; o < n; o += (size_t)kThreads * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+}
+
 // Stream a K x K matrix D (global memory, row-major) through two shared-memory buffers with
 // cp.async double buffering: chunk ch is loaded while chunk ch - 1 is used.  COLS: chunks of
 // CW columns, buf[i * (CW + 1) + kk] = D[i][c0 + kk] (rows padded by one entry against bank
@@ -698,6 +706,7 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
   const T tol_rel = (sizeof(T) == 4) ? T(1e-4) : T(1e-12);
   const T tol2 = (sizeof(T) == 4) ? T(1e-8) : T(1e-28);
   const int sweeps = (sizeof(T) == 4) ? 12 : 20;
+  prefetch_l2(D, (size_t)K * K * sizeof(cx<T>));      // dG, streamed after Omega is drawn
   long long k0 = a.k_init;
   for (int it = 0; it < nf; ++it) {
     const int d = (int)(k0 + a.p < K ? k0 + a.p : K);
@@ -721,6 +730,13 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
     for (int pass = 0; pass < 2; ++pass) {
       mm<T, true, false, MM_SET>(d, d, K, Q, df, Q, df, Gy, df);      // Q^H Q
       __syncthreads();
+      if (d <= kCqRegs) {   // Cholesky from registers on warp 0, one row of Q per thread
+        if (tid < 32) cholesky_regs<T, kCqRegs>(Gy, df, d, drop, rs, tol_rel);
+        __syncthreads();
+        fwd_subst_regs<T, kCqRegs>(Q, df, d, K, Gy, rs);
+        __syncthreads();
+        continue;
+      }
       cholqr_pass_smem<T>(Q, df, K, d, Gy, df, drop, rs, cn, tol_rel);
     }
     // B = 2^-e Q^H dG (d x K, ld K).  dG is exactly Hermitian as stored (its lower triangle is
@@ -948,18 +964,21 @@ __global__ void __launch_bounds__(256, 2) woodbury_fused_kernel(const StepArgs<T
     return;
   }
   const int ldz = RF + K;
-  cx<T>* const Lm = reinterpret_cast<cx<T>*>(sm);       // K x RF
+  // the two X chunk buffers first (an operand of the streamed products at the very start of
+  // the dynamic shared memory was measured to read about three times slower there)
+  cx<T>* const buf0 = reinterpret_cast<cx<T>*>(sm);
+  cx<T>* const buf1 = buf0 + (size_t)K * ((1 << kChunkLg) + 1);
+  const int lgcw = kChunkLg;
+  cx<T>* const Lm = buf1 + (size_t)K * ((1 << kChunkLg) + 1);   // K x RF
   cx<T>* const Rh = Lm + (size_t)K * RF;                  // RF x K
   cx<T>* const Tm = Rh + (size_t)RF * K;                  // K x RF
   cx<T>* const CZ = Tm + (size_t)K * RF;                  // RF x (RF + K): [C | Z]
-  cx<T>* const buf0 = CZ + (size_t)RF * ldz;               // two X chunks (stream_chunks)
-  cx<T>* const buf1 = buf0 + (size_t)K * ((1 << kChunkLg) + 1);
-  const int lgcw = kChunkLg;
   const cx<T>* const Q = w.Q + (size_t)b * w.L.sOm;       // K x dmax
   const cx<T>* const Ur = w.Ur + (size_t)b * w.L.sUr;     // dmax x rcap
   const cx<T>* const Bg = w.Bm + (size_t)b * w.L.sBm;     // dmax x K (unrotated B)
   const T nu = w.nu[b];
   cx<T>* const X = a.Xs + (size_t)b * K * K;
+  prefetch_l2(X, (size_t)K * K * sizeof(cx<T>));      // streamed three times below
   // L = Q U_r, R^H = nu U_r^H B
   for (int o = tid; o < K * r; o += 256) {
     const int i = o / r, c = o - i * r;
@@ -1219,8 +1238,8 @@ cudaError_t launch_arsvd_fused(const StepArgs<T>& a, const Bufs<T>& w, int nf, i
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// Shared memory of the fused Woodbury kernel at rank cap RF: L (K x RF), R^H (RF x K),
-// T (K x RF), [C | Z] (RF x (RF + K)), two chunk buffers of X (K x (2^kChunkLg + 1) each).
+// Shared memory of the fused Woodbury kernel at rank cap RF: two chunk buffers of X
+// (K x (2^kChunkLg + 1) each), L (K x RF), R^H (RF x K), T (K x RF), [C | Z] (RF x (RF + K)).
 inline size_t woodbury_fused_smem(int K, int RF, size_t cxb) {
   return cxb * (3 * (size_t)K * RF + (size_t)RF * (RF + K) +
                 2 * (size_t)K * ((1 << kChunkLg) + 1));
