@@ -16,6 +16,9 @@ written step by step from the paper so that a reader can check it against the eq
   philox    -- the Philox-4x32-10 counter-based generator (Salmon et al., SC'11) and the
                Box-Muller map that draw Algorithm 1's Gaussian test matrices.
   cost      -- the operation-count models of Tables I, II and IV.
+  hybrid    -- hybrid beamforming of Section II (eq. 4 and eq. 5): the DFT codebook,
+               best-power beams, the digital RZF precoder on H_eff = A F_RF, and the
+               sum-rate of eq. 15 through the beams.
 
 Parity status: every function is pinned by the CPU tests in ``tests/test_oracle_*.py``
 against closed forms, brute force, invariants or published vectors; none is "parity
