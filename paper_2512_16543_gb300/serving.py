@@ -7,7 +7,11 @@ state and carries that state's next channel H_t.  The server
 
   * admits states by HBM footprint: a state is given a slot only while the bytes of all
     admitted states (their share of the class workspace plus their input and output rows)
-    stay within the budget; requests of states that were not admitted are rejected;
+    stay within the budget.  A state that does not fit either is turned away (its requests
+    are rejected) or, with admit(..., wait=True), joins a first-come admission queue: its
+    requests are held, and it is admitted -- its held requests then join its class's
+    pending work -- as soon as retire() frees a slot and the bytes it needs; its requests'
+    latency includes that wait;
   * batches continuously: whenever a class has pending requests and fewer than `depth`
     launches in flight, it gathers the pending requests (at most one per state) into the
     class's input rows and launches one masked step for exactly those states -- requests
@@ -90,6 +94,9 @@ class BeamServer:
         self.used_bytes = 0
         self.rejected = 0
         self.completed: list[Request] = []
+        self.waiting: collections.deque = collections.deque()   # (state, class, alpha, sigma2)
+        self.held: dict[int, list] = {}        # waiting state -> its requests, in order
+        self.admitted_after_wait = 0
         for spec in classes:
             N, K, cap = spec[:3]
             crule = spec[3] if len(spec) > 3 else self.rule
@@ -119,34 +126,57 @@ class BeamServer:
             self.classes.append(c)
 
     # ------------------------------------------------------------------ admission
-    def admit(self, state: int, cls: int, alpha: float, sigma2: float) -> bool:
-        """Give `state` a slot of class `cls` if a slot and the HBM budget allow it."""
+    def _fits(self, c: _Class) -> bool:
+        return bool(c.free) and (self.budget is None or
+                                 self.used_bytes + c.per_state_bytes <= self.budget)
+
+    def _place(self, state: int, cls: int, alpha: float, sigma2: float) -> None:
         c = self.classes[cls]
-        if state in self.class_of:
-            raise ValueError(f"state {state} is already admitted")
-        if not c.free or (self.budget is not None and
-                          self.used_bytes + c.per_state_bytes > self.budget):
-            return False
         slot = c.free.pop()
         c.slot_of[state] = slot
         self.class_of[state] = cls
         self.used_bytes += c.per_state_bytes
         c.handle.set_instance_params(slot, alpha, sigma2, instance_id=state)
-        return True
+
+    def admit(self, state: int, cls: int, alpha: float, sigma2: float,
+              wait: bool = False) -> bool:
+        """Give `state` a slot of class `cls` if a slot and the HBM budget allow it; returns
+        True when it is admitted now.  With wait=True a state that does not fit joins the
+        admission queue instead of being turned away (see retire)."""
+        if state in self.class_of or state in self.held:
+            raise ValueError(f"state {state} is already admitted or waiting")
+        if not self.waiting and self._fits(self.classes[cls]):
+            self._place(state, cls, alpha, sigma2)
+            return True
+        if wait:
+            self.waiting.append((state, cls, alpha, sigma2))
+            self.held[state] = []
+        return False
 
     def retire(self, state: int) -> None:
-        """Free a state's slot (after its requests have completed)."""
+        """Free a state's slot (after its requests have completed), then admit waiting states
+        in arrival order while the head of the queue fits."""
         cls = self.class_of.pop(state)
         c = self.classes[cls]
         slot = c.slot_of.pop(state)
         c.initialised.discard(state)
         c.free.append(slot)
         self.used_bytes -= c.per_state_bytes
+        while self.waiting and self._fits(self.classes[self.waiting[0][1]]):
+            st, ci, alpha, sigma2 = self.waiting.popleft()
+            self._place(st, ci, alpha, sigma2)
+            self.classes[ci].pending.extend(self.held.pop(st))
+            self.admitted_after_wait += 1
 
     # ------------------------------------------------------------------ requests
     def submit(self, req: Request) -> bool:
+        """Queue a request; False (counted in `rejected`) for a state that is neither admitted
+        nor waiting for admission."""
         cls = self.class_of.get(req.state)
         if cls is None:
+            if req.state in self.held:           # waiting for memory: held until admitted
+                self.held[req.state].append(req)
+                return True
             self.rejected += 1
             return False
         self.classes[cls].pending.append(req)
@@ -206,6 +236,8 @@ class BeamServer:
         return ndone
 
     def drain(self) -> None:
+        """Run until every admitted state's requests are done (held requests of states still
+        waiting for memory stay held)."""
         while any(c.pending or c.inflight for c in self.classes):
             self.pump()
 

@@ -1,4 +1,5 @@
-"""Continuous-batching server: results alone and in the mix, admission by HBM footprint."""
+"""Continuous-batching server: results alone and in the mix, admission by HBM footprint,
+states waiting for memory admitted as retires free it."""
 import numpy as np
 import pytest
 import torch
@@ -93,3 +94,49 @@ def test_admission_respects_the_hbm_budget():
     assert srv.admit(4, 0, sc.alpha, sc.sigma2)
     assert srv.used_bytes <= 3 * per + per // 2
     srv.close()
+
+
+def test_a_state_waiting_for_memory_is_served_after_a_retire():
+    """Budget for two states: a third state's admission waits (not rejected), its requests
+    are held while the first two are served, and after a retire frees memory it is admitted
+    and served; its results equal the same state served alone, and its latency includes the
+    wait."""
+    rule = binding.RankRule(eta=0.9, k_init=2, p=4, r_max=16, reinverse_period=5, seed=3)
+    probe = serving.BeamServer([(256, 32, 4)], rule)
+    per = probe.classes[0].per_state_bytes
+    probe.close()
+    states = _states(3, 4, seed=910)[:3]           # three states of the (256, 32) class
+    srv = serving.BeamServer([(256, 32, 4)], rule, budget_bytes=2 * per + per // 2,
+                             keep_results=True)
+    got = [srv.admit(sid, 0, states[sid][1].alpha, states[sid][1].sigma2, wait=True)
+           for sid in range(3)]
+    assert got == [True, True, False] and srv.waiting and srv.rejected == 0
+    reqs = []
+    for t in range(3):
+        for sid in range(3):
+            r = serving.Request(sid, states[sid][2][t], arrival=0.0)
+            assert srv.submit(r)                     # held, not rejected, for state 2
+            reqs.append(r)
+    srv.drain()
+    assert all(r.done is not None for r in reqs if r.state != 2)
+    assert all(r.done is None for r in reqs if r.state == 2)
+    srv.retire(0)
+    assert srv.admitted_after_wait == 1 and not srv.waiting
+    assert srv.used_bytes <= 2 * per + per // 2
+    srv.drain()
+    srv.close()
+    mine = [r for r in reqs if r.state == 2]
+    assert all(r.done is not None for r in mine)
+    assert min(r.done for r in mine) > max(r.done for r in reqs if r.state == 0)
+    alone = serving.BeamServer([(256, 32, 4)], rule, keep_results=True)
+    assert alone.admit(2, 0, states[2][1].alpha, states[2][1].sigma2)
+    ref = []
+    for t in range(3):
+        r = serving.Request(2, states[2][2][t])
+        alone.submit(r)
+        ref.append(r)
+        alone.drain()
+    alone.close()
+    for a, m in zip(ref, mine):
+        assert torch.equal(a.W, m.W)
+        assert a.sum_rate == m.sum_rate
