@@ -54,8 +54,11 @@ def true_sum_rate(Ht: torch.Tensor, F: torch.Tensor, W: torch.Tensor, p_t: float
 
 def run(batch: int = 100, steps: int = 2400, etas=(0.9, 0.8, 0.65), seed: int = 2025,
         device="cuda", precision: str = "c64", snr_db: float = 10.0,
-        reinverse_period: int = 0) -> dict:
-    """reinverse_period: 0 = Algorithm 2 as printed (a direct inverse only on the rank test)."""
+        reinverse_period: int = 0, per_snapshot: bool = False) -> dict:
+    """reinverse_period: 0 = Algorithm 2 as printed (a direct inverse only on the rank test).
+    per_snapshot: also return "sum_rates", per method (in the table's order) the sum-rate of
+    every snapshot and run, a [steps, batch] nested list (snapshot 0 is the initial direct
+    inverse), with "t0", the time index of snapshot 0."""
     sc = channel.scenario_paper_hybrid(snr_db=snr_db)
     K = sc.K
     cb = channel.dft_codebook(sc, device=device)
@@ -108,4 +111,6 @@ def run(batch: int = 100, steps: int = 2400, etas=(0.9, 0.8, 0.65), seed: int = 
         table.append(row)
     return {"K": K, "N": sc.N, "N_RF": K, "updates_per_run": steps - 1, "runs": batch,
             "update_period_ms": sc.dt * 1e3, "precision": precision, "snr_db": snr_db,
-            "reinverse_period": reinverse_period, "table": table}
+            "reinverse_period": reinverse_period, "table": table,
+            **({"t0": t0, "sum_rates": [torch.stack(r).cpu().tolist() for r in rates]}
+               if per_snapshot else {})}

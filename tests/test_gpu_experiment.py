@@ -17,3 +17,40 @@ def test_paper_style_sweep_trends():
         assert -1.0 < row["sr_degradation_pct"] < 15.0
         q = list(row["ecdf_quantiles"].values())
         assert q == sorted(q)
+
+
+def test_per_snapshot_sum_rates_match_the_hybrid_oracle():
+    """Conventional RZF in the hybrid study against the FP64 oracle of Section II eq. 4-5 and
+    eq. 15, snapshot by snapshot: best-power DFT beams from the steering vectors, the RZF
+    precoder on H_eff = A F_RF scaled to ||F_RF F_BB||_F^2 = P_t, the sum-rate on the Rician
+    channel through the beams.  The study runs in complex128, so the sum-rates agree to 1e-9.
+    The library picks beams from complex64 products: a user whose two best beams are within
+    1e-4 in power is a tie (either pick is right), and such snapshots are skipped.  The
+    WB-arSVD rows start from the same direct inverse, so their snapshot 0 agrees too."""
+    import numpy as np
+
+    from oracle import hybrid
+    from paper_2512_16543_gb300 import channel
+
+    B, steps, seed = 2, 12, 11
+    res = experiment.run(batch=B, steps=steps, etas=(0.9,), seed=seed, precision="c128",
+                         per_snapshot=True)
+    sc = channel.scenario_paper_hybrid()
+    params = channel.draw_beam_users(sc, B, seed)
+    F = hybrid.dft_codebook(sc.n_x, sc.n_y)
+    compared = 0
+    for s in range(steps):
+        t = res["t0"] + s
+        A = channel.steering_at(params, t).numpy()
+        H = channel.channel_at(params, t).numpy()
+        for b in range(B):
+            pw = np.sort(np.abs(A[b].conj() @ F) ** 2, axis=1)
+            if np.any(pw[:, -1] - pw[:, -2] < 1e-4 * pw[:, -1]):
+                continue
+            o = hybrid.hybrid_rzf(A[b], H[b], sc.n_x, sc.n_y, sc.alpha, sc.p_t, sc.sigma2, F=F)
+            got = res["sum_rates"][0][s][b]
+            assert abs(got - o["sum_rate"]) <= 1e-9 * o["sum_rate"], (s, b, got, o["sum_rate"])
+            if s == 0:
+                assert abs(res["sum_rates"][1][0][b] - o["sum_rate"]) <= 1e-9 * o["sum_rate"]
+            compared += 1
+    assert compared >= 0.75 * B * steps
