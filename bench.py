@@ -479,6 +479,53 @@ def main_uneven(args):
     for h in hs:
         h.close()
 
+    # ---- each class alone, both methods on their autotuned engines, steps replayed from a
+    # CUDA graph (the blocked engine's optional blocks are IF nodes), L2 flushed between steps
+    def class_alone(ci, method, engine, eta):
+        c = pop[ci]
+        h = binding.WBRZF(c.batch, c.scenario.N, c.scenario.K, c.alpha, c.sigma2,
+                          p_t=c.scenario.p_t, rule=binding.RankRule(**uneven_rule_kw(
+                              c.scenario.K, eta)), method=method, device=dev,
+                          workspace_for="blocked")
+        h.set_instance_ids([int(i) for i in c.index])
+        h.set_engine(engine)
+        h.set_graph(True)
+        Hin, Wc = Hb[ci], Ws[ci]
+        Hin.copy_(Hs[ci][0])
+        h.full_inverse(Hin, Wc)
+        for t in range(1, 1 + W_):
+            Hin.copy_(Hs[ci][t])
+            h.update(Hin, Wc)
+        ms_c = []
+        for k in range(K_):
+            Hin.copy_(Hs[ci][1 + W_ + k])
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda._sleep(50000)        # keeps the GPU busy while the host submits
+            e0.record(stream)
+            h.update(Hin, Wc)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_c.append(e0.elapsed_time(e1))
+        info = h.step_info()
+        h.close()
+        return statistics.median(ms_c), {
+            "mean_r": statistics.mean(i["r"] for i in info),
+            "mean_iters": statistics.mean(i["iters"] for i in info)}
+
+    per_class = []
+    for ci, c in enumerate(pop):
+        t_wb, st = class_alone(ci, "wb", engines[ci], chosen)
+        t_full, _ = class_alone(ci, "full", fengines[ci], 0.9)
+        per_class.append({"N": c.scenario.N, "K": c.scenario.K, "batch": c.batch,
+                          "wb_engine": engines[ci], "full_engine": fengines[ci],
+                          "wb_last_step": st,
+                          "wb_ms": t_wb, "full_ms": t_full,
+                          "wb_updates_per_s": c.batch / (t_wb / 1e3),
+                          "full_updates_per_s": c.batch / (t_full / 1e3),
+                          "wb_over_full": t_full / t_wb})
+
     # ---- second run: BF16 precoder products plus one Newton refinement of X per snapshot
     # (blocked engine for every class), error against FP64 as above
     hs = []
@@ -563,6 +610,7 @@ def main_uneven(args):
                                  "p99_ms": float(np.percentile(ms_full, 99)),
                                  "engines": fengines},
             "wb_over_full": value / value_full,
+            "per_class_alone": per_class,
             "error_vs_fp64": {"max_W_relerr": worst_w, "max_sum_rate_gap_bits": worst_rate,
                               "sample": "2 instances per class x 4 snapshots, against the "
                                         "library's complex128 path on the same inputs"},
@@ -745,6 +793,10 @@ def main_single(args):
                 Hin.copy_(Hs[t])                        # outside the events
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
+                # a short device-side delay ahead of the first event: the host enqueues the
+                # whole step while the GPU waits, so the events time the step's device work
+                # and not the host's submission latency
+                torch.cuda._sleep(100000)
                 e0.record(stream)
                 h.update(Hin, Wout)
                 e1.record(stream)
