@@ -10,7 +10,7 @@ import torch
 
 from gpu_harness import relerr, run_oracle
 from paper_2512_16543_gb300 import binding, channel
-from test_gpu_parity import tf32_w_bound
+from test_gpu_parity import tf32_w_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -152,7 +152,8 @@ def test_group_autotune_chooses_an_accepted_engine_and_keeps_parity():
             Hb = Hs[i][:, b].cpu().numpy().astype(np.complex128)
             ref = run_oracle(Hb, sc.alpha, sc.sigma2, sc.p_t, rule, instance=b)
             for t in range(1, 4):
-                tol = max(2e-3, 2 * tf32_w_bound(Hb[t], ref[t].X)) if tf32 else 1e-4
+                tol = (tf32_w_tol(Hb[t], ref[t].X, ref[t].W, sc.p_t, x_tol=1e-4) if tf32
+                       else 1e-4)
                 assert relerr(outs[t - 1][i][b], ref[t].W) < tol, (i, b, t, chosen[i])
     grp.close()
     for h in members:

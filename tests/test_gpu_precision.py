@@ -1,8 +1,11 @@
 """Precision modes of the blocked engine: BF16 precoder product, one Newton refinement of X.
 
-BF16 operands carry a unit roundoff of 2^-9, four times TF32's, so W is held to 8e-3 or to
-twice the entrywise bound 2 u || |H^H| |X| || / ||H^H X|| with u = 2^-9 (tf32_w_bound x 4);
-X is untouched by that mode (its Gram matrix stays FP32-faithful) and keeps 1e-4.  The Newton
+BF16 operands carry a unit roundoff of 2^-9, four times TF32's.  W is held, snapshot by
+snapshot, to the tolerance computed from the data as for TF32 (tf32_w_tol with BF16
+rounding: the X error, three times the exact error of the rounded operands' product, FP32
+accumulation), and to 8e-3 overall (the largest error measured against FP64 on the uneven
+workload is 7.5e-3).  X is untouched by that mode (its Gram matrix stays FP32-faithful) and
+keeps 1e-4.  The Newton
 step X <- X (2 I - G X) squares the residual I - G X: with it the residual stays at the square
 of one snapshot's truncation residual (about (5e-5)^2 in FP64 at eta = 0.65) or at FP32
 rounding (1e-4 entrywise at K = 32), while without it the truncation error accumulates from
@@ -15,7 +18,7 @@ import torch
 from gpu_harness import relerr, run_gpu, run_oracle
 from oracle import rzf
 from paper_2512_16543_gb300 import binding, channel
-from test_gpu_parity import _traj, tf32_w_bound
+from test_gpu_parity import _traj, bf16_round, tf32_w_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -48,7 +51,7 @@ def test_bf16_precoder_product_against_the_oracle():
         for t in range(8):
             W, _, X, info = gpu[t]
             assert relerr(X[b], ref[t].X) < 1e-4
-            tol = max(8e-3, 2 * 4 * tf32_w_bound(Hb[t], ref[t].X))
+            tol = min(8e-3, tf32_w_tol(Hb[t], X[b], ref[t].W, sc.p_t, rnd=bf16_round))
             e = relerr(W[b], ref[t].W)
             assert e < tol, (t, b, e, tol)
             assert e > 1e-5            # the BF16 product is really in use

@@ -6,7 +6,7 @@ import torch
 
 from gpu_harness import relerr, run_oracle
 from paper_2512_16543_gb300 import binding, channel, serving
-from test_gpu_parity import tf32_w_bound
+from test_gpu_parity import tf32_w_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -72,7 +72,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
     Hn = Hs[:6].cpu().numpy().astype(np.complex128)
     ref = run_oracle(Hn, sc.alpha, sc.sigma2, sc.p_t, rule, instance=1)
     for t, r in enumerate(mine):
-        tol = max(2e-3, 2 * tf32_w_bound(Hn[t], ref[t].X))
+        tol = tf32_w_tol(Hn[t], ref[t].X, ref[t].W, sc.p_t, x_tol=1e-4)
         assert relerr(r.W.cpu().numpy(), ref[t].W) < tol
         assert abs(r.sum_rate - ref[t].sum_rate) < 1e-3
 
