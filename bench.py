@@ -526,51 +526,62 @@ def main_uneven(args):
                           "full_updates_per_s": c.batch / (t_full / 1e3),
                           "wb_over_full": t_full / t_wb})
 
-    # ---- second run: BF16 precoder products plus one Newton refinement of X per snapshot
-    # (blocked engine for every class), error against FP64 as above
-    hs = []
-    for c in pop:
-        h = binding.WBRZF(c.batch, c.scenario.N, c.scenario.K, c.alpha, c.sigma2,
-                          p_t=c.scenario.p_t, rule=binding.RankRule(**uneven_rule_kw(
-                              c.scenario.K, chosen)), device=dev, workspace_for="blocked")
-        h.set_instance_ids([int(i) for i in c.index])
-        h.set_engine("blocked")
-        h.set_precision_mode(True, 1)
-        hs.append(h)
-    grp = binding.WBRZFGroup(hs)
-    grp.set_graph(True)
-    ms_bf, _, _ = timed(grp, hs)
-    bf_w, bf_rate = 0.0, 0.0
-    for ci, c in enumerate(pop):
-        K = c.scenario.K
-        rk = uneven_rule_kw(K, chosen)
-        for j in range(min(2, c.batch)):
-            pair = []
-            for prec in ("c64", "c128"):
-                h = binding.WBRZF(1, c.scenario.N, K, [c.alpha[j]], [c.sigma2[j]],
-                                  p_t=c.scenario.p_t, rule=binding.RankRule(**rk),
-                                  precision=prec, device=dev, workspace_for="blocked")
-                h.set_instance_ids([int(c.index[j])])
-                if prec == "c64":
-                    h.set_engine("blocked")
-                    h.set_precision_mode(True, 1)
-                pair.append(h)
-            for t in range(4):
-                Hd = Hs[ci][t, j:j + 1].contiguous()
-                outs = []
-                for h, dt in zip(pair, (torch.complex64, torch.complex128)):
-                    Hx = Hd.to(dt)
-                    W = h.full_inverse(Hx) if t == 0 else h.update(Hx)
-                    outs.append((W[0].to(torch.complex128), float(h.sum_rate()[1][0])))
-                (W32, r32), (W64, r64) = outs
-                bf_w = max(bf_w, float((W32 - W64).norm() / W64.norm()))
-                bf_rate = max(bf_rate, abs(r32 - r64))
-            for h in pair:
-                h.close()
-    bf16_refine = {"value": world * count * K_ / barrier_max(sum(ms_bf) / 1e3, world),
-                   "unit": "updates/s", "ms_per_step": statistics.mean(ms_bf),
-                   "engine": "blocked (all classes)",
-                   "error_vs_fp64": {"max_W_relerr": bf_w, "max_sum_rate_gap_bits": bf_rate}}
+    # ---- precision modes, each a run of the whole group on the blocked engine (every class),
+    # error against FP64 on the same sample as above:
+    #   bf16_refine: BF16 precoder products plus one Newton refinement of X per snapshot;
+    #   fp64_small_solves: the eigensolver of Algorithm 1, the capacitance inverse and every
+    #     direct inverse in FP64 (the products as in the headline run)
+    def mode_run(configure):
+        hs_m = []
+        for c in pop:
+            h = binding.WBRZF(c.batch, c.scenario.N, c.scenario.K, c.alpha, c.sigma2,
+                              p_t=c.scenario.p_t, rule=binding.RankRule(**uneven_rule_kw(
+                                  c.scenario.K, chosen)), device=dev, workspace_for="blocked")
+            h.set_instance_ids([int(i) for i in c.index])
+            h.set_engine("blocked")
+            configure(h)
+            hs_m.append(h)
+        grp_m = binding.WBRZFGroup(hs_m)
+        grp_m.set_graph(True)
+        ms_m, _, _ = timed(grp_m, hs_m)
+        grp_m.close()
+        for h in hs_m:
+            h.close()
+        m_w, m_rate = 0.0, 0.0
+        for ci, c in enumerate(pop):
+            K = c.scenario.K
+            rk = uneven_rule_kw(K, chosen)
+            for j in range(min(2, c.batch)):
+                pair = []
+                for prec in ("c64", "c128"):
+                    h = binding.WBRZF(1, c.scenario.N, K, [c.alpha[j]], [c.sigma2[j]],
+                                      p_t=c.scenario.p_t, rule=binding.RankRule(**rk),
+                                      precision=prec, device=dev, workspace_for="blocked")
+                    h.set_instance_ids([int(c.index[j])])
+                    if prec == "c64":
+                        h.set_engine("blocked")
+                        configure(h)
+                    pair.append(h)
+                for t in range(4):
+                    Hd = Hs[ci][t, j:j + 1].contiguous()
+                    outs = []
+                    for h, dt in zip(pair, (torch.complex64, torch.complex128)):
+                        Hx = Hd.to(dt)
+                        W = h.full_inverse(Hx) if t == 0 else h.update(Hx)
+                        outs.append((W[0].to(torch.complex128), float(h.sum_rate()[1][0])))
+                    (W32, r32), (W64, r64) = outs
+                    m_w = max(m_w, float((W32 - W64).norm() / W64.norm()))
+                    m_rate = max(m_rate, abs(r32 - r64))
+                for h in pair:
+                    h.close()
+        return {"value": world * count * K_ / barrier_max(sum(ms_m) / 1e3, world),
+                "unit": "updates/s", "ms_per_step": statistics.mean(ms_m),
+                "engine": "blocked (all classes)",
+                "error_vs_fp64": {"max_W_relerr": m_w, "max_sum_rate_gap_bits": m_rate}}
+
+    bf16_refine = mode_run(lambda h: h.set_precision_mode(True, 1))
+    fp64_small = mode_run(lambda h: h.set_fp64_small_solves(True))
+    fp32_blocked = mode_run(lambda h: None)
 
     tot_wb = barrier_max(sum(ms_wb) / 1e3, world)
     tot_full = barrier_max(sum(ms_full) / 1e3, world)
@@ -614,14 +625,13 @@ def main_uneven(args):
             "error_vs_fp64": {"max_W_relerr": worst_w, "max_sum_rate_gap_bits": worst_rate,
                               "sample": "2 instances per class x 4 snapshots, against the "
                                         "library's complex128 path on the same inputs"},
-            "precision_modes": {"tf32": "the headline run above", "bf16_refine": bf16_refine},
+            "precision_modes": {"tf32": "the headline run above", "bf16_refine": bf16_refine,
+                                "fp64_small_solves": fp64_small,
+                                "blocked_default": fp32_blocked},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": None,
             "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
-    grp.close()
-    for h in hs:
-        h.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

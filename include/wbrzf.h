@@ -293,6 +293,26 @@ void wbrzf_destroy(wbrzf* h);
 wbrzf_status wbrzf_set_precision_mode(wbrzf* h, int bf16_products, int refine_steps);
 
 /*
+ * FP64 small solves (complex64 handles on the blocked engine; a step on another engine with
+ * the mode set returns WBRZF_ERR_UNSUPPORTED).  With enable != 0 the three solves whose
+ * conditioning the method relies on run in FP64, the large products staying as they are:
+ *   - the small SVD of B in Algorithm 1 (Section IV-A): the eigendecomposition of
+ *     E = B B^H (formed by FP32 products) to FP64 convergence -- FP32 Jacobi rotations
+ *     finished by FP64 ones -- with sigma_hat^2 and the energy rule (eq. 14) in FP64;
+ *   - the r x r capacitance system of the Woodbury update (Section III eq. 12): C = I + R^H X L
+ *     (formed by FP32 products) is inverted by FP64 Gauss-Jordan with partial pivoting;
+ *   - every direct inverse of G_t (initialisation, the periodic re-inversion and the rank /
+ *     fallback branches of Algorithm 2): an FP64 Cholesky factorisation, triangular inverse and
+ *     product, rounded to complex64 once.
+ * G_t, X and the precoder stay complex64.  FP64 arithmetic runs at about 1/68 of the FP32
+ * rate on this GPU, so the mode costs time; it is off by default.
+ * Returns WBRZF_ERR_UNSUPPORTED for complex128 handles (already FP64 throughout) and where
+ * the FP64 blocks do not fit in shared memory (K > 160, or a rank rule whose largest sketch
+ * width or rank does not fit); the setting then stays as it was.
+ */
+wbrzf_status wbrzf_set_fp64_small_solves(wbrzf* h, int enable);
+
+/*
  * CUDA-graph replay (not part of the paper's method).  With enable != 0 the next step is
  * captured into a CUDA graph on a stream the handle owns and replayed, fork/joined with the
  * handle's stream by events, for every later step with the same kind (full inverse or

@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_uint32)]
     L.wbrzf_set_precision_mode.restype = i32
     L.wbrzf_set_precision_mode.argtypes = [vp, i32, i32]
+    L.wbrzf_set_fp64_small_solves.restype = i32
+    L.wbrzf_set_fp64_small_solves.argtypes = [vp, i32]
     L.wbrzf_set_graph.restype = i32
     L.wbrzf_set_graph.argtypes = [vp, i32]
     L.wbrzf_group_create.restype = i32
@@ -255,6 +257,12 @@ class WBRZF:
         """Blocked engine: BF16 precoder product and / or one Newton refinement of X."""
         _check(lib().wbrzf_set_precision_mode(self._h, int(bf16_products), int(refine)),
                "wbrzf_set_precision_mode")
+
+    def set_fp64_small_solves(self, enable: bool = True) -> None:
+        """Blocked engine, complex64: the eigensolver of Algorithm 1, the capacitance inverse
+        and every direct inverse of G in FP64."""
+        _check(lib().wbrzf_set_fp64_small_solves(self._h, int(enable)),
+               "wbrzf_set_fp64_small_solves")
 
     def set_graph(self, enable: bool = True) -> None:
         """Replay steps from a CUDA graph while H, W and the mask stay the same tensors."""
@@ -477,9 +485,14 @@ class WBRZFGroup:
         _check(lib().wbrzf_group_update(self._g, Ha, Wa), "wbrzf_group_update")
 
     def set_precision_mode(self, bf16_products: bool = False, refine: int = 0) -> None:
-        """Blocked engine: BF16 precoder product and / or one Newton refinement of X."""
-        _check(lib().wbrzf_set_precision_mode(self._h, int(bf16_products), int(refine)),
-               "wbrzf_set_precision_mode")
+        """Every member: BF16 precoder product and / or one Newton refinement of X."""
+        for h in self.handles:
+            h.set_precision_mode(bf16_products, refine)
+
+    def set_fp64_small_solves(self, enable: bool = True) -> None:
+        """Every member: FP64 eigensolver, capacitance inverse and direct inverses."""
+        for h in self.handles:
+            h.set_fp64_small_solves(enable)
 
     def set_graph(self, enable: bool = True) -> None:
         _check(lib().wbrzf_group_set_graph(self._g, int(enable)), "wbrzf_group_set_graph")

@@ -17,6 +17,8 @@
 // Data-dependent control never returns to the host: every kernel reads per-instance control
 // words (low-rank step still iterating, branch) and instances that are not selected return at
 // once, so one snapshot is always the same launch sequence.
+#include <type_traits>
+
 #include "step_kernel.cuh"
 
 static_assert(sizeof(wbrzf_step_info) == 32 && offsetof(wbrzf_step_info, status) == 28,
@@ -32,10 +34,16 @@ constexpr int kDirectMask = (1 << WBRZF_BRANCH_INIT) | (1 << WBRZF_BRANCH_PERIOD
 
 constexpr int kPending = 15;   // branch code while the low-rank step has not decided
 constexpr int kInactive = 14;  // branch code of an instance that sits this step out
-constexpr int kWoodburyWide = 13;
+constexpr int kWoodburyWide = 13;    // rank above the fused Woodbury kernel's cap
 // Stream accumulators per thread (dr_product / ad_product) of the fused Woodbury step and of the
 // fused Algorithm 1 kernel; each bounds the columns a stream covers to MAXA kThreads / K.
 constexpr int kWoodburyMaxA = 12;
+constexpr int kWoodburyFusedTop = 24;      // largest rank of the fused Woodbury kernel (FP32)
+// Sketch width from which the fused kernel's eigensolver runs on the whole CTA instead of one
+// warp
+constexpr int kJacobiCtaMin = 12;
+// Sketch widths up to this take the register CholQR in the fused kernel as well
+constexpr int kCqRegsWide = 16;
 template <class T> constexpr int fused_max_a() { return sizeof(T) == 4 ? 12 : 6; }  // Woodbury step whose rank exceeds the fused kernel's cap:
                                    // the batched products take it (reported as Woodbury)
 constexpr int kLiveMask = ~(1 << kInactive);
@@ -418,33 +426,34 @@ __device__ T block_sum_n(T v, T* red) {
 // Cyclic Jacobi eigendecomposition of E (d x d Hermitian, ld dmax): eigenvalues to lam,
 // eigenvectors (columns) to Uh, one CTA of NT threads per instance; each round is
 // jacobi_round (all pairs' rotations, then every 2 x 2 block of J^H E J and U J: two barriers).
-template <int NT, class T>
+// S: the real type of the rotations (float or double for FP32 buffers, double for FP64).
+template <int NT, class T, class S>
 __global__ void __launch_bounds__(NT) jacobi_kernel(const Bufs<T> w, int d) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int b = blockIdx.x, tid = threadIdx.x, dmax = w.dmax;
   if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
-  cx<T>* E = reinterpret_cast<cx<T>*>(sm);
-  cx<T>* U = E + (size_t)dmax * dmax;
-  cx<T>* ph = U + (size_t)dmax * dmax;
-  T* rc = reinterpret_cast<T*>(ph + dmax);
-  T* rs = rc + dmax;
-  T* red = rs + dmax;
+  cx<S>* E = reinterpret_cast<cx<S>*>(sm);
+  cx<S>* U = E + (size_t)dmax * dmax;
+  cx<S>* ph = U + (size_t)dmax * dmax;
+  S* rc = reinterpret_cast<S*>(ph + dmax);
+  S* rs = rc + dmax;
+  S* red = rs + dmax;
   int* pp = reinterpret_cast<int*>(red + 40);
   int* pq = pp + dmax;
   const cx<T>* Eg = w.E + (size_t)b * w.L.sGy;
   for (int e = tid; e < d * d; e += NT) {
     const int i = e / d, j = e - i * d;
-    E[i * dmax + j] = Eg[i * dmax + j];
-    U[i * dmax + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
+    E[i * dmax + j] = ccast<S>(Eg[i * dmax + j]);
+    U[i * dmax + j] = cmk<S>(i == j ? S(1) : S(0), S(0));
   }
   __syncthreads();
   const int dm1 = d + (d & 1) - 1;
-  const T eps = (sizeof(T) == 4) ? T(1e-8) : T(1e-26);
-  for (int sweep = 0; sweep < ((sizeof(T) == 4) ? 12 : 20); ++sweep) {
-    T off = 0, tot = 0;
+  const S eps = (sizeof(S) == 4) ? S(1e-8) : S(1e-26);
+  for (int sweep = 0; sweep < ((sizeof(S) == 4) ? 12 : 20); ++sweep) {
+    S off = 0, tot = 0;
     for (int e = tid; e < d * d; e += NT) {
       const int i = e / d, j = e - i * d;
-      const T v = cabs2(E[i * dmax + j]);
+      const S v = cabs2(E[i * dmax + j]);
       tot += v;
       if (i != j) off += v;
     }
@@ -452,14 +461,15 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const Bufs<T> w, int d) {
     tot = block_sum_n<NT>(tot, red);
     if (!(off > eps * tot)) break;
     for (int rnd = 0; rnd < dm1; ++rnd)
-      jacobi_round<T, NT>(E, U, dmax, d, rnd, pp, pq, rc, rs, ph);
+      jacobi_round<S, NT>(E, U, dmax, d, rnd, pp, pq, rc, rs, ph);
   }
   cx<T>* Ug = w.Uh + (size_t)b * w.L.sGy;
   for (int e = tid; e < d * d; e += NT) {
     const int i = e / d, j = e - i * d;
-    Ug[i * dmax + j] = U[i * dmax + j];
+    Ug[i * dmax + j] = ccast<T>(U[i * dmax + j]);
   }
-  for (int j = tid; j < d; j += NT) w.lam[(size_t)b * dmax + j] = fmax(E[j * dmax + j].re, T(0));
+  for (int j = tid; j < d; j += NT)
+    w.lam[(size_t)b * dmax + j] = (T)fmax(E[j * dmax + j].re, S(0));
 }
 
 // Energy rule (eq. 14) and Algorithm 1's loop control; on exit the branch of Algorithm 2 and,
@@ -642,28 +652,79 @@ __device__ __forceinline__ void ad_product(const cx<T>* __restrict__ D, int K, c
 
 // dr_product / ad_product with the accumulator count fixed at compile time to the smallest of
 // 2, 4, 6, 8, 12 that covers ceil(n / G) (n the columns / rows covered, G = kThreads / K), so
-// that no thread issues work for accumulators it does not use.  MAXA bounds the largest.
+// that no thread issues work for accumulators it does not use.  MAXA bounds the largest; wider
+// products run as several of at most MAXA G columns / rows each, D streamed once per part.
 template <class T, int MAXA, bool CONJT>
 __device__ __forceinline__ void dr_product_n(const cx<T>* __restrict__ D, int K, const cx<T>* R,
                                              int ldr, int nc, cx<T>* P, int ldp, T scale,
                                              int lg, cx<T>* buf0, cx<T>* buf1) {
-  const int G = kThreads / K, na = (nc + G - 1) / G;
-  if (na <= 2) dr_product<T, 2, CONJT>(D, K, R, ldr, nc, P, ldp, scale, lg, buf0, buf1);
-  else if (na <= 4) dr_product<T, 4, CONJT>(D, K, R, ldr, nc, P, ldp, scale, lg, buf0, buf1);
-  else if (na <= 6 || MAXA <= 6) dr_product<T, (MAXA < 6 ? MAXA : 6), CONJT>(D, K, R, ldr, nc, P, ldp, scale, lg, buf0, buf1);
-  else if (na <= 8) dr_product<T, (MAXA < 8 ? MAXA : 8), CONJT>(D, K, R, ldr, nc, P, ldp, scale, lg, buf0, buf1);
-  else dr_product<T, MAXA, CONJT>(D, K, R, ldr, nc, P, ldp, scale, lg, buf0, buf1);
+  const int G = kThreads / K, span = MAXA * G;
+  for (int c0 = 0; c0 < nc; c0 += span) {
+    const int n = nc - c0 < span ? nc - c0 : span, na = (n + G - 1) / G;
+    const cx<T>* const Rc = R + c0;
+    cx<T>* const Pc = CONJT ? P + (size_t)c0 * ldp : P + c0;
+    if (na <= 2) dr_product<T, 2, CONJT>(D, K, Rc, ldr, n, Pc, ldp, scale, lg, buf0, buf1);
+    else if (na <= 4) dr_product<T, 4, CONJT>(D, K, Rc, ldr, n, Pc, ldp, scale, lg, buf0, buf1);
+    else if (na <= 6 || MAXA <= 6) dr_product<T, (MAXA < 6 ? MAXA : 6), CONJT>(D, K, Rc, ldr, n, Pc, ldp, scale, lg, buf0, buf1);
+    else if (na <= 8) dr_product<T, (MAXA < 8 ? MAXA : 8), CONJT>(D, K, Rc, ldr, n, Pc, ldp, scale, lg, buf0, buf1);
+    else dr_product<T, MAXA, CONJT>(D, K, Rc, ldr, n, Pc, ldp, scale, lg, buf0, buf1);
+  }
 }
 template <class T, int MAXA>
 __device__ __forceinline__ void ad_product_n(const cx<T>* __restrict__ D, int K, const cx<T>* A,
                                              int lda, int nr, cx<T>* Z, int ldz, int lg,
                                              cx<T>* buf0, cx<T>* buf1) {
-  const int G = kThreads / K, na = (nr + G - 1) / G;
-  if (na <= 2) ad_product<T, 2>(D, K, A, lda, nr, Z, ldz, lg, buf0, buf1);
-  else if (na <= 4) ad_product<T, 4>(D, K, A, lda, nr, Z, ldz, lg, buf0, buf1);
-  else if (na <= 6 || MAXA <= 6) ad_product<T, (MAXA < 6 ? MAXA : 6)>(D, K, A, lda, nr, Z, ldz, lg, buf0, buf1);
-  else if (na <= 8) ad_product<T, (MAXA < 8 ? MAXA : 8)>(D, K, A, lda, nr, Z, ldz, lg, buf0, buf1);
-  else ad_product<T, MAXA>(D, K, A, lda, nr, Z, ldz, lg, buf0, buf1);
+  const int G = kThreads / K, span = MAXA * G;
+  for (int r0 = 0; r0 < nr; r0 += span) {
+    const int n = nr - r0 < span ? nr - r0 : span, na = (n + G - 1) / G;
+    const cx<T>* const Ar = A + (size_t)r0 * lda;
+    cx<T>* const Zr = Z + (size_t)r0 * ldz;
+    if (na <= 2) ad_product<T, 2>(D, K, Ar, lda, n, Zr, ldz, lg, buf0, buf1);
+    else if (na <= 4) ad_product<T, 4>(D, K, Ar, lda, n, Zr, ldz, lg, buf0, buf1);
+    else if (na <= 6 || MAXA <= 6) ad_product<T, (MAXA < 6 ? MAXA : 6)>(D, K, Ar, lda, n, Zr, ldz, lg, buf0, buf1);
+    else if (na <= 8) ad_product<T, (MAXA < 8 ? MAXA : 8)>(D, K, Ar, lda, n, Zr, ldz, lg, buf0, buf1);
+    else ad_product<T, MAXA>(D, K, Ar, lda, n, Zr, ldz, lg, buf0, buf1);
+  }
+}
+
+// Cyclic two-sided Jacobi eigendecomposition E = U Lambda U^H of the Hermitian d x d matrix E
+// (ld ld, shared memory) by all kThreads threads of the CTA, U (ld ld) accumulated from I:
+// each round is jacobi_round (the disjoint pairs' rotations, then every 2 x 2 block of
+// J^H E J and U's columns, two barriers).  Each sweep starts with the largest |E_pq|^2
+// (p < q) against tol2 tr(E)^2 -- the test of the one-warp solver -- and the sweeps stop when
+// it passes or after max_sweeps.  Scratch: pp, pq (ints), rc, rs (reals), ph (complex), at
+// least ceil(d / 2) each; red: 33 reals.  For sketch widths at which the one-warp solver's
+// serial rounds dominate.  Called by all threads; ends with a barrier.
+template <class T>
+__device__ void jacobi_eig_cta(cx<T>* E, cx<T>* U, int ld, int d, T tol2, int max_sweeps,
+                               int* pp, int* pq, T* rc, T* rs, cx<T>* ph, T* red) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < d * d; e += kThreads) {
+    const int i = e / d, j = e - i * d;
+    U[i * ld + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
+  }
+  T tr = 0;                                  // every thread sums the diagonal in one order
+  for (int j = 0; j < d; ++j) tr += E[j * ld + j].re;
+  const T thr = tol2 * tr * tr;
+  const int dm1 = d + (d & 1) - 1;
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    T mx = 0;
+    for (int e = tid; e < d * d; e += kThreads) {
+      const int i = e / d, j = e - i * d;
+      if (j > i) mx = fmax(mx, cabs2(E[i * ld + j]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    mx = 0;
+    for (int q = 0; q < kThreads / 32; ++q) mx = fmax(mx, red[q]);
+    __syncthreads();
+    if (!(mx > thr)) break;
+    for (int rnd = 0; rnd < dm1; ++rnd)
+      jacobi_round<T, kThreads>(E, U, ld, d, rnd, pp, pq, rc, rs, ph);
+  }
 }
 
 // Fused Algorithm 1 iterations (K <= 128, the leading nf iterations, whose sketch widths fit
@@ -675,14 +736,14 @@ __device__ __forceinline__ void ad_product_n(const cx<T>* __restrict__ D, int K,
 // for the Woodbury stage: the control words, perm, lam, the trace, the unrotated B, and for a
 // Woodbury instance Q and U_r.  An instance still short of its target after the nf
 // iterations stays active and continues on the per-step kernels.
-template <class T, bool LARGEK>
+template <class T, bool LARGEK, bool S64>
 __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs<T> a,
-                                                                  const Bufs<T> w, int nf,
-                                                                  int df) {
+                                                                  const Bufs<T> w, int it0,
+                                                                  int nf, int df) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int b = blockIdx.x, tid = threadIdx.x, K = a.K, dmax = w.dmax, rcap = w.rcap;
   if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
-  const FusedLayout F = fused_layout(K, df, sizeof(cx<T>), sizeof(T));
+  const FusedLayout F = fused_layout(K, df, sizeof(cx<T>), sizeof(T), S64);
   cx<T>* const Om = reinterpret_cast<cx<T>*>(sm + F.oOm);
   cx<T>* const Q = reinterpret_cast<cx<T>*>(sm + F.oQ);
   cx<T>* const Bm = reinterpret_cast<cx<T>*>(sm + F.oB);
@@ -695,6 +756,14 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
   int* const perm = reinterpret_cast<int*>(sm + F.oPerm);
   int* const drop = reinterpret_cast<int*>(sm + F.oDrop);
   int* const flags = reinterpret_cast<int*>(sm + F.oFlags);
+  cx<double>* const E64 = reinterpret_cast<cx<double>*>(sm + F.oE64);    // S64 only
+  cx<double>* const U64 = reinterpret_cast<cx<double>*>(sm + F.oU64);
+  double* const lam64 = reinterpret_cast<double*>(sm + F.oLam64);
+  // sigma_hat_j^2 as the energy rule reads it
+  auto lamv = [&](int j) -> double {
+    if constexpr (S64) return lam64[j];
+    else return (double)lam[j];
+  };
   cx<T>* const buf0 = reinterpret_cast<cx<T>*>(sm + F.oBuf);
   cx<T>* const buf1 = buf0 + (size_t)K * ((1 << kChunkLg) + 1);
   const int lgcw = kChunkLg;
@@ -708,7 +777,9 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
   const int sweeps = (sizeof(T) == 4) ? 12 : 20;
   prefetch_l2(D, (size_t)K * K * sizeof(cx<T>));      // dG, streamed after Omega is drawn
   long long k0 = a.k_init;
-  for (int it = 0; it < nf; ++it) {
+  for (int it = 0; it < it0; ++it)
+    if (k0 < K) k0 *= 2;
+  for (int it = it0; it < it0 + nf; ++it) {
     const int d = (int)(k0 + a.p < K ? k0 + a.p : K);
     const bool last = it == a.i_max - 1;
     // Omega: entry (i, j) from counter (i, j/2, t, 16 id + it)
@@ -737,6 +808,13 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
         __syncthreads();
         continue;
       }
+      if (d <= kCqRegsWide) {
+        if (tid < 32) cholesky_regs<T, kCqRegsWide>(Gy, df, d, drop, rs, tol_rel);
+        __syncthreads();
+        fwd_subst_regs<T, kCqRegsWide>(Q, df, d, K, Gy, rs);
+        __syncthreads();
+        continue;
+      }
       cholqr_pass_smem<T>(Q, df, K, d, Gy, df, drop, rs, cn, tol_rel);
     }
     // B = 2^-e Q^H dG (d x K, ld K).  dG is exactly Hermitian as stored (its lower triangle is
@@ -747,11 +825,73 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
       cx<T>* const Bg = w.Bm + (size_t)b * w.L.sBm;
       for (int o = tid; o < dmax * K; o += kThreads) Bg[o] = o < d * K ? Bm[o] : cmk<T>(0, 0);
     }
+    // The d values sigma_hat_j^2 sum to tr(B B^H) = ||B||_F^2 (the rotations keep the trace).
+    // When that falls short of the energy target by more than the rotations' rounding, no
+    // r <= d meets eq. 14 and this iteration fails (k0 doubles) without the eigensolver.
+    if (!last) {
+      T part = 0;
+      for (int o = tid; o < d * K; o += kThreads) part += cabs2(Bm[o]);
+      const T trE = block_sum(part, red);
+      if ((double)trE < w.et[b] * (1.0 - 1e-4)) {
+        if (tid == 0) ctl[C_K0] *= 2;
+        if (k0 < K) k0 *= 2;
+        continue;
+      }
+    }
     // svd(B) as in the one-CTA engines: K <= 32, one-sided Jacobi on B's rows (the unrotated
     // B is already in global memory for the Woodbury products), sigma_hat^2 the squared row
     // norms; K > 32, two-sided Jacobi on E = B B^H (d x d, into Gy: Q^H Q is dead) on one warp,
     // sigma_hat^2 E's rotated diagonal.  U_hat holds the left singular vectors.
-    if (!LARGEK) {
+    // S64 (any K): the eigendecomposition of E = B B^H (formed by FP32 products) to FP64
+    // convergence.  FP64 runs at about 1/68 of the FP32 rate here, so the bulk of the rotations
+    // is done in FP32 and finished in FP64:
+    //   the FP32 Jacobi gives U_1 (unitary to FP32 rounding);
+    //   one Newton-Schulz step in FP64, U = U_1 S with S = (3 I - U_1^H U_1) / 2, makes it
+    //     unitary to FP64 rounding (the deviation is squared), so that
+    //   E' = U^H E U (FP64) is a similarity of E, nearly diagonal, which the FP64 Jacobi
+    //     diagonalises (V) in a sweep or two;
+    //   U_hat = U V, rounded to FP32 for the products; sigma_hat^2 (E''s diagonal) stays FP64.
+    // Blocks: E64 (E, then E'), U64 (U_1, then W = E U, then U_hat), T64 (S, then V) and GU
+    // (the FP32 Gy and Uh blocks, contiguous, as one FP64 block: U).
+    if constexpr (S64) {
+      cx<double>* const T64 = reinterpret_cast<cx<double>*>(sm + F.oT64);
+      cx<double>* const GU = reinterpret_cast<cx<double>*>(Gy);
+      mm<T, false, true, MM_SET>(d, d, K, Bm, K, Bm, K, Gy, df);
+      __syncthreads();
+      for (int e = tid; e < d * d; e += kThreads) {
+        const int i = e / d, j = e - i * d;
+        E64[i * df + j] = ccast<double>(Gy[i * df + j]);
+      }
+      __syncthreads();
+      jacobi_eig<T>(Gy, df, Uh, df, d, tol2, sweeps);          // U_1 in Uh
+      for (int e = tid; e < d * d; e += kThreads) {
+        const int i = e / d, j = e - i * d;
+        U64[i * df + j] = ccast<double>(Uh[i * df + j]);
+      }
+      __syncthreads();
+      mm<double, true, false, MM_SET>(d, d, d, U64, df, U64, df, T64, df);   // U_1^H U_1
+      __syncthreads();
+      for (int e = tid; e < d * d; e += kThreads) {                          // S
+        const int i = e / d, j = e - i * d;
+        const cx<double> m = T64[i * df + j];
+        T64[i * df + j] = cmk<double>((i == j ? 1.5 : 0.0) - 0.5 * m.re, -0.5 * m.im);
+      }
+      __syncthreads();
+      mm<double, false, false, MM_SET>(d, d, d, U64, df, T64, df, GU, df);   // U = U_1 S
+      __syncthreads();
+      mm<double, false, false, MM_SET>(d, d, d, E64, df, GU, df, U64, df);   // W = E U
+      __syncthreads();
+      mm<double, true, false, MM_SET>(d, d, d, GU, df, U64, df, E64, df);    // E' = U^H W
+      __syncthreads();
+      jacobi_eig<double>(E64, df, T64, df, d, 1e-28, 20);                     // V in T64
+      if (tid < d) lam64[tid] = fmax(E64[tid * df + tid].re, 0.0);
+      mm<double, false, false, MM_SET>(d, d, d, GU, df, T64, df, U64, df);   // U_hat = U V
+      __syncthreads();
+      for (int e = tid; e < d * d; e += kThreads) {
+        const int i = e / d, j = e - i * d;
+        Uh[i * df + j] = ccast<T>(U64[i * df + j]);
+      }
+    } else if (!LARGEK) {
       for (int e = tid; e < d * d; e += kThreads) {
         const int i = e / d, j = e - i * d;
         Uh[i * df + j] = cmk<T>(i == j ? T(1) : T(0), T(0));
@@ -770,14 +910,17 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
     } else {
       mm<T, false, true, MM_SET>(d, d, K, Bm, K, Bm, K, Gy, df);
       __syncthreads();
-      jacobi_eig<T>(Gy, df, Uh, df, d, tol2, sweeps);
+      if (d >= kJacobiCtaMin)      // (perm, drop, cn, rs and Omega are scratch here)
+        jacobi_eig_cta<T>(Gy, Uh, df, d, tol2, sweeps, perm, drop, cn, rs, Om, red);
+      else
+        jacobi_eig<T>(Gy, df, Uh, df, d, tol2, sweeps);
       if (tid < d) lam[tid] = fmax(Gy[tid * df + tid].re, T(0));
     }
     __syncthreads();
     if (tid < d) {
-      const T v = lam[tid];
+      const double v = lamv(tid);
       int rk = 0;
-      for (int i = 0; i < d; ++i) rk += (lam[i] > v || (lam[i] == v && i < tid)) ? 1 : 0;
+      for (int i = 0; i < d; ++i) rk += (lamv(i) > v || (lamv(i) == v && i < tid)) ? 1 : 0;
       perm[rk] = tid;
     }
     __syncthreads();
@@ -786,7 +929,7 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
       double cum = 0.0;
       int rf = 0;
       for (int j = 0; j < d; ++j) {
-        cum += (double)lam[perm[j]];
+        cum += lamv(perm[j]);
         if (cum >= w.et[b]) { rf = j + 1; break; }
       }
       int rw = -1;
@@ -802,14 +945,14 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
         if (a.trace != nullptr) {
           T* tr = reinterpret_cast<T*>(a.trace + (size_t)b * a.trace_stride);
           const int e2 = 2 * ctl[C_EXP];
-          for (int j = 0; j < dmax; ++j) tr[j] = (j < d) ? (T)ldexp((double)lam[perm[j]], e2) : T(0);
+          for (int j = 0; j < dmax; ++j) tr[j] = (j < d) ? (T)ldexp(lamv(perm[j]), e2) : T(0);
         }
       } else {
         ctl[C_K0] *= 2;
       }
       for (int j = 0; j < d; ++j) {
         w.perm[(size_t)b * dmax + j] = perm[j];
-        w.lam[(size_t)b * dmax + j] = lam[j];
+        w.lam[(size_t)b * dmax + j] = (T)lamv(j);
       }
       flags[4] = rw;
       flags[5] = (rf > 0 || last) ? 1 : 0;
@@ -838,26 +981,27 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
 // the rest of the rcap x rcap buffer becomes zero, as T and Z vanish there) by Gauss-Jordan
 // with partial pivoting; a numerically singular pivot sends the instance to the direct
 // inverse (fallback branch).
-template <class T>
+// S: the real type of the elimination (T, or double for FP32 buffers).
+template <class T, class S>
 __global__ void __launch_bounds__(256) capinv_kernel(const Bufs<T> w, int gmask) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int b = blockIdx.x, tid = threadIdx.x, rcap = w.rcap;
   if (!gate_ok(w.ctl, b, C_BRANCH, gmask)) return;
   const int n = w.ctl[8 * b + C_R], ld = 2 * n;
-  cx<T>* A = reinterpret_cast<cx<T>*>(sm);
-  cx<T>* col = A + (size_t)rcap * 2 * rcap;
-  T* red = reinterpret_cast<T*>(col + rcap);
+  cx<S>* A = reinterpret_cast<cx<S>*>(sm);
+  cx<S>* col = A + (size_t)rcap * 2 * rcap;
+  S* red = reinterpret_cast<S*>(col + rcap);
   __shared__ int piv_row, singular;
   cx<T>* Cm = w.Cm + (size_t)b * w.L.sCm;
-  T cmax = 0;
+  S cmax = 0;
   for (int e = tid; e < n * ld; e += 256) {
     const int i = e / ld, j = e - i * ld;
-    cx<T> v;
+    cx<S> v;
     if (j < n) {
-      v = cadd(Cm[i * rcap + j], cmk<T>(i == j ? T(1) : T(0), T(0)));
+      v = cadd(ccast<S>(Cm[i * rcap + j]), cmk<S>(i == j ? S(1) : S(0), S(0)));
       cmax = fmax(cmax, sqrt(cabs2(v)));
     } else {
-      v = cmk<T>((j - n) == i ? T(1) : T(0), T(0));
+      v = cmk<S>((j - n) == i ? S(1) : S(0), S(0));
     }
     A[e] = v;
   }
@@ -867,13 +1011,13 @@ __global__ void __launch_bounds__(256) capinv_kernel(const Bufs<T> w, int gmask)
   __syncthreads();
   cmax = 0;
   for (int q = 0; q < 8; ++q) cmax = fmax(cmax, red[q]);
-  const T tol = cmax * ((sizeof(T) == 4) ? T(1e-6) : T(1e-14));
+  const S tol = cmax * ((sizeof(S) == 4) ? S(1e-6) : S(1e-14));
   for (int c = 0; c < n; ++c) {
     if (tid == 0) {
       int pr = c;
-      T best = -1;
+      S best = -1;
       for (int i = c; i < n; ++i) {
-        const T v = cabs2(A[i * ld + c]);
+        const S v = cabs2(A[i * ld + c]);
         if (v > best) { best = v; pr = i; }
       }
       piv_row = pr;
@@ -883,13 +1027,13 @@ __global__ void __launch_bounds__(256) capinv_kernel(const Bufs<T> w, int gmask)
     const int pr = piv_row;
     if (pr != c) {
       for (int j = tid; j < ld; j += 256) {
-        const cx<T> t0 = A[c * ld + j];
+        const cx<S> t0 = A[c * ld + j];
         A[c * ld + j] = A[pr * ld + j];
         A[pr * ld + j] = t0;
       }
       __syncthreads();
     }
-    const cx<T> ip = crecip(A[c * ld + c]);
+    const cx<S> ip = crecip(A[c * ld + c]);
     for (int i = tid; i < n; i += 256) col[i] = A[i * ld + c];
     __syncthreads();
     for (int j = tid; j < ld; j += 256) A[c * ld + j] = cmul(A[c * ld + j], ip);
@@ -906,7 +1050,7 @@ __global__ void __launch_bounds__(256) capinv_kernel(const Bufs<T> w, int gmask)
   }
   for (int e = tid; e < rcap * rcap; e += 256) {
     const int i = e / rcap, j = e - i * rcap;
-    Cm[e] = (i < n && j < n) ? A[i * ld + n + j] : cmk<T>(0, 0);
+    Cm[e] = (i < n && j < n) ? ccast<T>(A[i * ld + n + j]) : cmk<T>(0, 0);
   }
 }
 
@@ -948,19 +1092,26 @@ __device__ __forceinline__ void woodbury_update_cols(cx<T>* X, int K, int r, con
 //     direct inverse (branch FALLBACK);
 //   a second pass X <- X - T (C^-1 Z).
 // X is streamed from global memory three times (rows for T, columns for Z, columns for the
-// update); everything else stays in shared memory (layout of woodbury_fused_smem).  An
-// instance with r > RF is marked kWoodburyWide for the batched products.
-template <class T>
+// update); everything else stays in shared memory (layout of woodbury_fused_smem).  The
+// kernel takes the instances whose branch is in gmask; one with r > RF is marked wide_mark
+// for a launch with a larger cap or for the batched products.  Above kWoodburyFusedTop, T and
+// Z stream X once per part of at most kWoodburyMaxA kThreads / K columns, and the update
+// once per part of kWoodburyFusedTop columns.
+// S64: C (formed by FP32 products) is inverted in FP64 -- Gauss-Jordan on [C | I] over the
+// L and R^H blocks, dead by then (RF <= K / 2 makes them large enough) -- and C^-1 Z is
+// formed in FP32 from the rounded inverse.
+template <class T, bool S64>
 __global__ void __launch_bounds__(256, 2) woodbury_fused_kernel(const StepArgs<T> a,
-                                                                const Bufs<T> w, int RF) {
+                                                                const Bufs<T> w, int RF,
+                                                                int gmask, int wide_mark) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int singular;
   const int b = blockIdx.x, tid = threadIdx.x, K = a.K, dmax = w.dmax, rcap = w.rcap;
-  if (!gate_ok(w.ctl, b, C_BRANCH, 1 << WBRZF_BRANCH_WOODBURY)) return;
+  if (!gate_ok(w.ctl, b, C_BRANCH, gmask)) return;
   int* const ctl = w.ctl + 8 * b;
   const int r = ctl[C_R], d = ctl[C_D];
   if (r > RF) {
-    if (tid == 0) ctl[C_BRANCH] = kWoodburyWide;
+    if (tid == 0) ctl[C_BRANCH] = wide_mark;
     return;
   }
   const int ldz = RF + K;
@@ -1015,6 +1166,47 @@ __global__ void __launch_bounds__(256, 2) woodbury_fused_kernel(const StepArgs<T
     CZ[c * ldz + e] = acc;
   }
   __syncthreads();
+  if constexpr (S64) {
+    cx<double>* const A64 = reinterpret_cast<cx<double>*>(Lm);   // r x 2r, ld 2r
+    const int l64 = 2 * r;
+    if (tid < 32) {
+      double cmax = 0;
+      for (int o = tid; o < r * r; o += 32) {
+        const int c = o / r, e = o - c * r;
+        const cx<double> v = cmk<double>((double)CZ[c * ldz + e].re, (double)CZ[c * ldz + e].im);
+        A64[c * l64 + e] = v;
+        A64[c * l64 + r + e] = cmk<double>(c == e ? 1.0 : 0.0, 0.0);
+        cmax = fmax(cmax, sqrt(cabs2(v)));
+      }
+      for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+      __syncwarp();
+      const bool sg = gauss_jordan_warp<double>(A64, l64, r, r, r, cmax * 1e-14);
+      if (tid == 0) singular = sg ? 1 : 0;
+    }
+    __syncthreads();
+    if (singular) {
+      if (tid == 0) ctl[C_BRANCH] = WBRZF_BRANCH_FALLBACK;
+      return;
+    }
+    // Z <- C^-1 Z in place: thread j < K owns column j (r <= RF <= kWoodburyFusedTop)
+    if (tid < K) {
+      cx<T> z[kWoodburyFusedTop];
+#pragma unroll
+      for (int c = 0; c < kWoodburyFusedTop; ++c)
+        z[c] = c < r ? CZ[c * ldz + RF + tid] : cmk<T>(0, 0);
+      for (int i = 0; i < r; ++i) {
+        cx<T> acc = cmk<T>(0, 0);
+#pragma unroll
+        for (int c = 0; c < kWoodburyFusedTop; ++c)
+          if (c < r) {
+            const cx<double> ci = A64[i * l64 + r + c];
+            cfma(acc, cmk<T>((T)ci.re, (T)ci.im), z[c]);
+          }
+        CZ[i * ldz + RF + tid] = acc;
+      }
+    }
+    __syncthreads();
+  } else {
   if (tid < 32) {
     T cmax = 0;
     for (int o = tid; o < r * r; o += 32) {
@@ -1031,13 +1223,21 @@ __global__ void __launch_bounds__(256, 2) woodbury_fused_kernel(const StepArgs<T
     if (tid == 0) ctl[C_BRANCH] = WBRZF_BRANCH_FALLBACK;
     return;
   }
+  }
   // X <- X - T (C^-1 Z): thread t updates column j = t mod K on rows g, g + G, ..., with the
-  // column of C^-1 Z in registers (r <= NR, NR the smallest bucket of 4, 8, 16, 24 >= r;
-  // woodbury_fused_cap keeps RF <= 24, and <= 16 in FP64)
-  if (r <= 4) woodbury_update_cols<T, 4>(X, K, r, Tm, RF, CZ + RF, ldz);
-  else if (r <= 8) woodbury_update_cols<T, 8>(X, K, r, Tm, RF, CZ + RF, ldz);
-  else if (r <= 16 || sizeof(T) == 8) woodbury_update_cols<T, 16>(X, K, r, Tm, RF, CZ + RF, ldz);
-  else woodbury_update_cols<T, (sizeof(T) == 4 ? 24 : 16)>(X, K, r, Tm, RF, CZ + RF, ldz);
+  // column of C^-1 Z in registers (NR the smallest bucket of 4, 8, 16, 24 >= the part's
+  // width; 16 at most in FP64), one pass over X per part of at most that many columns (each
+  // thread keeps its own entries of X, so the parts need no barrier between them)
+  constexpr int top = sizeof(T) == 4 ? kWoodburyFusedTop : 16;
+  for (int c0 = 0; c0 < r; c0 += top) {
+    const int n = r - c0 < top ? r - c0 : top;
+    const cx<T>* const Tc = Tm + c0;
+    const cx<T>* const Wc = CZ + (size_t)c0 * ldz + RF;
+    if (n <= 4) woodbury_update_cols<T, 4>(X, K, n, Tc, RF, Wc, ldz);
+    else if (n <= 8) woodbury_update_cols<T, 8>(X, K, n, Tc, RF, Wc, ldz);
+    else if (n <= 16 || sizeof(T) == 8) woodbury_update_cols<T, 16>(X, K, n, Tc, RF, Wc, ldz);
+    else woodbury_update_cols<T, top>(X, K, n, Tc, RF, Wc, ldz);
+  }
 }
 
 // Condition of a CUDA-graph IF node: true when some instance's control word ctl[idx] is one of
@@ -1074,6 +1274,92 @@ __global__ void copy_gx_kernel(const StepArgs<T> a, const Bufs<T> w) {
   const size_t KK = (size_t)a.K * a.K;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < KK) a.Xs[(size_t)b * KK + idx] = a.Gs[(size_t)b * KK + idx];
+}
+
+// Direct inverse X = G^-1 in FP64 (the small-solve FP64 mode, K <= kInv64MaxK), one CTA per
+// instance, on G's upper triangle packed row by row in shared memory (row i holds columns
+// i .. K-1):
+//   Cholesky G = R^H R (R upper, right-looking: row j scaled by 1 / sqrt(G_jj), then the
+//     trailing triangle G_ik -= conj(R_ji) R_jk);
+//   R <- R^-1 row by row from the bottom: (R^-1)_ij = (delta_ij - sum_{i<k<=j} R_ik (R^-1)_kj)
+//     / R_ii, with row i of R staged first;
+//   X = R^-1 R^-H row by row from the top: X_ij = sum_{k>=j} (R^-1)_ik conj((R^-1)_jk), j >= i
+//     (row i, staged first, is read from its copy while it is overwritten; later rows read
+//     rows >= their own);
+// then X (Hermitian) is written in full, rounded to T.  A pivot that is not positive and
+// finite (G not numerically positive definite) marks the instance NOT_PD and its X NaN.
+constexpr int kInv64MaxK = 160;
+inline size_t inv64_smem(int K) {
+  return ((size_t)K * (K + 1) / 2 + (size_t)K) * sizeof(cx<double>);
+}
+template <class T>
+__global__ void __launch_bounds__(256) inverse64_kernel(const StepArgs<T> a, const Bufs<T> w) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int b = blockIdx.x, tid = threadIdx.x, K = a.K;
+  if (!gate_ok(w.ctl, b, C_BRANCH, kDirectMask)) return;
+  cx<double>* const P = reinterpret_cast<cx<double>*>(sm);
+  cx<double>* const row = P + (size_t)K * (K + 1) / 2;
+  __shared__ int bad;
+  auto at = [K](int i, int j) { return i * K - (i * (i - 1)) / 2 + (j - i); };   // j >= i
+  const cx<T>* const G = a.Gs + (size_t)b * K * K;
+  cx<T>* const X = a.Xs + (size_t)b * K * K;
+  for (int e = tid; e < K * K; e += 256) {
+    const int i = e / K, j = e - i * K;
+    if (j >= i) P[at(i, j)] = ccast<double>(G[e]);
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  // threads (g, c): column c = t mod K (K <= 256), rows g, g + NG, ...
+  const int NG = 256 / K, g = tid / K, c = tid - g * K;
+  for (int j = 0; j < K; ++j) {
+    const double piv = P[at(j, j)].re;
+    if (!(piv > 0.0) || !isfinite(piv)) {           // the same value in every thread
+      if (tid == 0) bad = 1;
+      break;
+    }
+    const double rinv = 1.0 / sqrt(piv);
+    __syncthreads();
+    for (int k = j + tid; k < K; k += 256) P[at(j, k)] = cscale(P[at(j, k)], rinv);
+    __syncthreads();
+    if (g < NG && c > j) {
+      const cx<double> rjc = P[at(j, c)];
+      for (int i = j + 1 + g; i <= c; i += NG) cfma_jc(P[at(i, c)], cscale(P[at(j, i)], -1.0), rjc);
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad) {
+    const T nan = (T)NAN;
+    for (int e = tid; e < K * K; e += 256) X[e] = cmk<T>(nan, nan);
+    if (tid == 0) atomicOr(&w.ctl[8 * b + C_STATUS], WBRZF_STATUS_NOT_PD);
+    return;
+  }
+  for (int i = K - 1; i >= 0; --i) {
+    for (int k = i + tid; k < K; k += 256) row[k] = P[at(i, k)];
+    __syncthreads();
+    for (int j = i + tid; j < K; j += 256) {
+      cx<double> acc = cmk<double>(j == i ? 1.0 : 0.0, 0.0);
+      for (int k = i + 1; k <= j; ++k) acc = csub(acc, cmul(row[k], P[at(k, j)]));
+      P[at(i, j)] = cscale(acc, 1.0 / row[i].re);
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < K; ++i) {
+    for (int k = i + tid; k < K; k += 256) row[k] = P[at(i, k)];
+    __syncthreads();
+    for (int j = i + tid; j < K; j += 256) {     // row i itself is read from its copy
+      const cx<double>* const rj = j == i ? row : P + at(j, j) - j;
+      cx<double> acc = cmk<double>(0.0, 0.0);
+      for (int k = j; k < K; ++k) cfma(acc, row[k], cconj(rj[k]));
+      P[at(i, j)] = acc;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < K * K; e += 256) {
+    const int i = e / K, j = e - i * K;
+    const cx<double> v = j >= i ? P[at(i, j)] : cconj(P[at(j, i)]);
+    X[e] = i == j ? cmk<T>((T)v.re, T(0)) : ccast<T>(v);
+  }
 }
 
 // Pivot block P = [32p, 32p + bs): PC = X[:, P], PR = X[P, :], Pb = X[P, P]
@@ -1229,12 +1515,15 @@ __global__ void __launch_bounds__(256) sinr_final_kernel(const StepArgs<T> a, co
 }
 
 template <class T>
-cudaError_t launch_arsvd_fused(const StepArgs<T>& a, const Bufs<T>& w, int nf, int df,
+cudaError_t launch_arsvd_fused(const StepArgs<T>& a, const Bufs<T>& w, int it0, int nf, int df,
                                cudaStream_t s) {
-  const int bytes = (int)fused_layout(a.K, df, sizeof(cx<T>), sizeof(T)).bytes;
-  const auto kern = a.K > 32 ? arsvd_fused_kernel<T, true> : arsvd_fused_kernel<T, false>;
+  const bool s64 = sizeof(T) == 4 && a.small64;
+  const int bytes = (int)fused_layout(a.K, df, sizeof(cx<T>), sizeof(T), s64).bytes;
+  const auto kern = s64 ? arsvd_fused_kernel<T, true, (sizeof(T) == 4)>
+                        : (a.K > 32 ? arsvd_fused_kernel<T, true, false>
+                                    : arsvd_fused_kernel<T, false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) kern<<<a.batch, kThreads, bytes, s>>>(a, w, nf, df);
+  if (e == cudaSuccess) kern<<<a.batch, kThreads, bytes, s>>>(a, w, it0, nf, df);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -1246,29 +1535,27 @@ inline size_t woodbury_fused_smem(int K, int RF, size_t cxb) {
 }
 // Largest rank cap RF <= rcap of the fused Woodbury kernel (0: not used, K > 128): its shared
 // memory within two CTAs per SM and each thread's share of T or Z within the stream
-// accumulators (RF <= kWoodburyMaxA kThreads / K).
+// accumulators (RF <= kWoodburyMaxA kThreads / K); with the FP64 capacitance inverse also
+// RF <= K / 2 (its [C | I] block lives over L and R^H).
+// top: the largest cap considered; cap: the shared-memory budget.
 template <class T>
-int woodbury_fused_cap(int K, int rcap) {
+int woodbury_fused_cap(int K, int rcap, bool s64, int top, size_t cap) {
   if (K > 128) return 0;
-  const int top = sizeof(T) == 4 ? 24 : 16;        // woodbury_update_cols register buckets
   for (int RF = rcap < top ? rcap : top; RF >= 1; --RF)
-    if (woodbury_fused_smem(K, RF, sizeof(cx<T>)) <= kFusedSmemCap &&
-        RF <= kWoodburyMaxA * (kThreads / K))
+    if (woodbury_fused_smem(K, RF, sizeof(cx<T>)) <= cap && (!s64 || 2 * RF <= K))
       return RF;
   return 0;
 }
-inline int woodbury_fused_cap(int K, int rcap, size_t cxb) {
-  return cxb == 8 ? woodbury_fused_cap<float>(K, rcap) : woodbury_fused_cap<double>(K, rcap);
-}
 
 template <class T>
-cudaError_t launch_woodbury_fused(const StepArgs<T>& a, const Bufs<T>& w, int RF,
-                                  cudaStream_t s) {
+cudaError_t launch_woodbury_fused(const StepArgs<T>& a, const Bufs<T>& w, int RF, int gmask,
+                                  int wide_mark, cudaStream_t s) {
   const int bytes = (int)woodbury_fused_smem(a.K, RF, sizeof(cx<T>));
-  cudaError_t e = cudaFuncSetAttribute(woodbury_fused_kernel<T>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const auto kern = (sizeof(T) == 4 && a.small64) ? woodbury_fused_kernel<T, (sizeof(T) == 4)>
+                                                  : woodbury_fused_kernel<T, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  woodbury_fused_kernel<T><<<a.batch, 256, bytes, s>>>(a, w, RF);
+  kern<<<a.batch, 256, bytes, s>>>(a, w, RF, gmask, wide_mark);
   return cudaGetLastError();
 }
 
@@ -1328,17 +1615,28 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
   int nl = 0;
   *launches = 0;
 #define WB_TRY(x) do { e = (x); if (e != cudaSuccess) return e; ++nl; } while (0)
+  // small64 (complex64 only): the eigensolver, the capacitance inverse and the direct inverse
+  // in FP64 (their shared-memory blocks at FP64 sizes)
+  const bool s64 = sizeof(T) == 4 && a.small64;
+  using S = std::conditional_t<sizeof(T) == 4, double, T>;
   const BlockedSmem sm = blocked_smem(dmax, rcap, sizeof(cx<T>), sizeof(T));
-  const size_t js = sm.jacobi, cs = sm.cholesky, ps = sm.capinv;
-  e = cudaFuncSetAttribute(jacobi_kernel<256, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)js);
+  const BlockedSmem sms = s64 ? blocked_smem(dmax, rcap, sizeof(cx<S>), sizeof(S)) : sm;
+  const size_t js = sms.jacobi, cs = sm.cholesky, ps = sms.capinv;
+  const auto jac256 = s64 ? jacobi_kernel<256, T, S> : jacobi_kernel<256, T, T>;
+  const auto jac1024 = s64 ? jacobi_kernel<1024, T, S> : jacobi_kernel<1024, T, T>;
+  const auto capinv = s64 ? capinv_kernel<T, S> : capinv_kernel<T, T>;
+  if (s64 && (K > kInv64MaxK || js > 227 * 1024 || ps > 227 * 1024))
+    return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(jac256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)js);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(jacobi_kernel<1024, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)js);
+    e = cudaFuncSetAttribute(jac1024, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)js);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(cholesky_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(capinv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+    e = cudaFuncSetAttribute(capinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+  if (e == cudaSuccess && s64)
+    e = cudaFuncSetAttribute(inverse64_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)inv64_smem(K));
   if (e != cudaSuccess) return e;
   const T one = T(1), zero = T(0);
   // stage boundaries for the optional timing events (ev[0..5])
@@ -1366,26 +1664,27 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
   if (a.mode == MODE_UPDATE) {
     long long k0 = a.k_init;
     int it0 = 0;
-    // the leading iterations whose sketch width fits the fused kernel's shared memory (two
-    // CTAs per SM) run in one launch; the rest, for instances still short of their target,
-    // on the per-step kernels below
-    int nf = 0, df = 0;
+    // Algorithm 1 on the fused kernel (K <= 128): the leading iterations whose sketch width
+    // fits its shared memory at two CTAs per SM in one launch; the rest, for the instances
+    // still short of their target, on the per-step kernels below.  (A second fused launch at
+    // one CTA per SM for the next widths was measured slower than the per-step kernels: its
+    // one-warp Jacobi at d = 40 takes millions of cycles.)
     if (K <= 128) {
-      long long kk = a.k_init;
+      int nf = 0, df = 0;
+      long long kk = k0;
       for (int it = 0; it < a.i_max; ++it) {
         const int d = (int)(kk + a.p < K ? kk + a.p : K);
-        if (fused_layout(K, d, sizeof(cx<T>), sizeof(T)).bytes > kFusedSmemCap ||
-            d > fused_max_a<T>() * (kThreads / K))
+        if (fused_layout(K, d, sizeof(cx<T>), sizeof(T), a.small64 != 0).bytes > kFusedSmemCap)
           break;
         nf = it + 1;
         df = d;
         if (kk < K) kk *= 2;
       }
-    }
-    if (nf > 0) {
-      WB_TRY(launch_arsvd_fused<T>(a, w, nf, df, s));
-      for (; it0 < nf; ++it0)
-        if (k0 < K) k0 *= 2;
+      if (nf > 0) {
+        WB_TRY(launch_arsvd_fused<T>(a, w, 0, nf, df, s));
+        for (int k = 0; k < nf; ++k, ++it0)
+          if (k0 < K) k0 *= 2;
+      }
     }
     for (int it = it0; it < a.i_max; ++it) {
       const int d = (int)(k0 + a.p < K ? k0 + a.p : K);
@@ -1414,8 +1713,8 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
                        one, w.dsc, zero, w.ctl, C_ACTIVE, 2, nullptr, Live{d, 1 << 30, 1 << 30}));
         WB_TRY(gemm<T>(q, B, d, d, K, w.Bm, K, L.sBm, 0, w.Bm, K, L.sBm, 1, w.E, dmax, L.sGy,
                        one, nullptr, zero, w.ctl, C_ACTIVE, 2));
-        if (d > 32) jacobi_kernel<1024, T><<<B, 1024, js, q>>>(w, d);
-        else jacobi_kernel<256, T><<<B, 256, js, q>>>(w, d);
+        if (d > 32) jac1024<<<B, 1024, js, q>>>(w, d);
+        else jac256<<<B, 256, js, q>>>(w, d);
         WB_TRY(cudaGetLastError());
         rank_kernel<T><<<B, 256, 0, q>>>(a, w, it, d, last);
         WB_TRY(cudaGetLastError());
@@ -1427,8 +1726,12 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
     if ((e = mark(2)) != cudaSuccess) return e;
     // Woodbury (eq. 12): one fused kernel per instance where the rank fits its shared memory
     // (K <= 128), the batched products for the rest (marked kWoodburyWide) and for K > 128
-    const int RF = woodbury_fused_cap(K, rcap, sizeof(cx<T>));
-    if (RF > 0) WB_TRY(launch_woodbury_fused<T>(a, w, RF, s));
+    // (ranks above the cap RF, whose one-warp Gauss-Jordan would be slower than the batched
+    // capacitance kernel, take the batched products)
+    const int top1 = sizeof(T) == 4 ? kWoodburyFusedTop : 16;
+    const int RF = woodbury_fused_cap<T>(K, rcap, s64, top1, kFusedSmemCap);
+    if (RF > 0)
+      WB_TRY(launch_woodbury_fused<T>(a, w, RF, 1 << WBRZF_BRANCH_WOODBURY, kWoodburyWide, s));
     const int gw = RF > 0 ? (1 << kWoodburyWide) : (1 << WBRZF_BRANCH_WOODBURY);
     e = guarded(s, sb, w.ctl, B, C_BRANCH, gw, [&](cudaStream_t q) -> cudaError_t {
       cudaError_t e;
@@ -1451,7 +1754,7 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
                      nullptr, zero, w.ctl, C_BRANCH, gw, nullptr, all, C_R, -1, -1));
       WB_TRY(gemm<T>(q, B, rcap, rcap, K, w.Z, K, L.sRh, 0, w.Lm, rcap, L.sL, 0, w.Cm, rcap,
                      L.sCm, one, nullptr, zero, w.ctl, C_BRANCH, gw, nullptr, all, C_R, C_R, -1));
-      capinv_kernel<T><<<B, 256, ps, q>>>(w, gw);
+      capinv<<<B, 256, ps, q>>>(w, gw);
       WB_TRY(cudaGetLastError());
       WB_TRY(gemm<T>(q, B, rcap, K, rcap, w.Cm, rcap, L.sCm, 0, w.Z, K, L.sRh, 0, w.CZ, K,
                      L.sRh, one, nullptr, zero, w.ctl, C_BRANCH, gw, nullptr, all, C_R, -1, C_R));
@@ -1466,6 +1769,11 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
   // direct inverse by block exchange steps (instances whose branch asks for it)
   e = guarded(s, sb, w.ctl, B, C_BRANCH, kDirectMask, [&](cudaStream_t q) -> cudaError_t {
     cudaError_t e;
+    if (s64) {
+      inverse64_kernel<T><<<B, 256, inv64_smem(K), q>>>(a, w);
+      WB_TRY(cudaGetLastError());
+      return cudaSuccess;
+    }
     copy_gx_kernel<T><<<dim3((unsigned)((KK + 255) / 256), B), 256, 0, q>>>(a, w);
     WB_TRY(cudaGetLastError());
     const int nb = (K + 31) / 32;
@@ -1528,6 +1836,10 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
 }  // namespace wbk
 
 namespace wbk {
+bool blocked_small64_ok(int K, int dmax, int rcap) {
+  const BlockedSmem s = blocked_smem(dmax, rcap, sizeof(cx<double>), sizeof(double));
+  return K <= kInv64MaxK && s.jacobi <= 227 * 1024 && s.capinv <= 227 * 1024;
+}
 cudaError_t run_blocked_f32(const StepArgs<float>& a, unsigned char* base, cudaStream_t s,
                             cudaStream_t sb, int* launches, cudaEvent_t* ev) {
   return run_blocked<float>(a, base, s, sb, launches, ev);

@@ -52,6 +52,8 @@ struct StepArgs {
   int tc_products;         // blocked engine, complex64: Gram and precoder on tensor cores
   int gemm_bf16;           // blocked engine, complex64: the precoder product in BF16
   int refine;              // blocked engine: one Newton step X <- X (2 I - G X) per snapshot
+  int small64;             // blocked engine, complex64: the eigensolver of B B^H, the
+                           // capacitance inverse and every direct inverse of G in FP64
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -247,9 +249,12 @@ __host__ __device__ inline BlockedSmem blocked_smem(int dmax, int rcap, size_t c
 // per-column arrays, and two K x (kChunkCols + 1) buffers through which dG is streamed.
 constexpr int kChunkLg = 3;                 // dG / X streamed in chunks of 8 columns or rows
 struct FusedLayout {
-  size_t oOm, oQ, oB, oGy, oUh, oLam, oRs, oCn, oRed, oPerm, oDrop, oFlags, oBuf, bytes;
+  size_t oOm, oQ, oB, oGy, oUh, oLam, oRs, oCn, oRed, oPerm, oDrop, oFlags, oBuf;
+  size_t oE64, oU64, oT64, oLam64; // FP64 eigensolver blocks (s64 only)
+  size_t bytes;
 };
-__host__ __device__ inline FusedLayout fused_layout(int K, int df, size_t cxb, size_t tb) {
+__host__ __device__ inline FusedLayout fused_layout(int K, int df, size_t cxb, size_t tb,
+                                                    bool s64 = false) {
   FusedLayout F;
   size_t o = 0;
   auto take = [&](size_t n) { const size_t at = o; o = align_up(o + n, 16); return at; };
@@ -268,6 +273,22 @@ __host__ __device__ inline FusedLayout fused_layout(int K, int df, size_t cxb, s
   F.oPerm = take((size_t)df * sizeof(int));
   F.oDrop = take((size_t)df * sizeof(int));
   F.oFlags = take(8 * sizeof(int));
+  // three d x d complex128 blocks and the eigenvalues of the FP64 eigensolver; the blocks
+  // overlay the chunk buffers and Omega (both dead while it runs) when they fit there
+  F.oE64 = F.oU64 = F.oT64 = F.oLam64 = 0;
+  if (s64) {
+    const size_t blk = align_up((size_t)df * df * 16, 16);
+    if (3 * blk <= F.oQ) {
+      F.oE64 = 0;
+      F.oU64 = blk;
+      F.oT64 = 2 * blk;
+    } else {
+      F.oE64 = take(blk);
+      F.oU64 = take(blk);
+      F.oT64 = take(blk);
+    }
+    F.oLam64 = take((size_t)df * 8);
+  }
   F.bytes = o;
   return F;
 }
@@ -293,6 +314,9 @@ cudaError_t run_blocked_f32(const StepArgs<float>& a, unsigned char* base, cudaS
                             cudaStream_t sb, int* launches, cudaEvent_t* ev);
 cudaError_t run_blocked_f64(const StepArgs<double>& a, unsigned char* base, cudaStream_t s,
                             cudaStream_t sb, int* launches, cudaEvent_t* ev);
+// The FP64 small-solve mode fits this (K, dmax, rcap): the FP64 direct inverse's packed
+// triangle, the batched eigensolver's and capacitance inverse's FP64 blocks in shared memory.
+bool blocked_small64_ok(int K, int dmax, int rcap);
 // Tensor-core products of the blocked engine (complex64, tc_gemm.cu): the Gram matrix into
 // D (upper triangle, instance stride sD) and W = s H^H X; P, T, XB are the operand buffers of
 // the blocked layout; a timeout ORs WBRZF_STATUS_TIMEOUT into stat[stat_stride * b];

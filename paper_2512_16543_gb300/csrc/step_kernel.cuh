@@ -27,6 +27,10 @@ namespace wbk {
 
 // ------------------------------------------------------------------ complex helpers
 template <class T> __device__ __forceinline__ cx<T> cmk(T r, T i) { cx<T> z; z.re = r; z.im = i; return z; }
+// The same complex number in another real type (rounded to nearest)
+template <class D, class S> __device__ __forceinline__ cx<D> ccast(cx<S> v) {
+  return cmk<D>((D)v.re, (D)v.im);
+}
 template <class T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return cmk(a.re + b.re, a.im + b.im); }
 template <class T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return cmk(a.re - b.re, a.im - b.im); }
 template <class T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
@@ -791,9 +795,9 @@ template <class T, int kNT = kThreads>
 __device__ void cholqr_pass_smem(cx<T>* Q, int ldq, int K, int d, cx<T>* Gy, int ldg,
                                  int* drop, T* rs, T* cn, T tol_rel) {
   const int tid = threadIdx.x;
-  if (tid < 32) {   // one warp factors the d x d Gram matrix; lane c owns column c
-    const int cl = tid;
-    if (cl < d) cn[cl] = Gy[cl * ldg + cl].re;
+  if (tid < 32) {   // one warp factors the d x d Gram matrix; lane l owns columns l, l + 32
+    const int lane = tid;
+    for (int c = lane; c < d; c += 32) cn[c] = Gy[c * ldg + c].re;
     __syncwarp();
     // right-looking Cholesky Gy = R^H R (R upper, stored in the upper triangle)
     for (int j = 0; j < d; ++j) {
@@ -801,25 +805,27 @@ __device__ void cholqr_pass_smem(cx<T>* Q, int ldq, int K, int d, cx<T>* Gy, int
       const bool dj = drop[j] || !(cn[j] > T(0)) || !(piv > tol_rel * cn[j]) || !isfinite(piv);
       const T rinv = dj ? T(0) : T(1) / sqrt(piv);
       __syncwarp();
-      if (cl == 0) { drop[j] = dj ? 1 : 0; rs[j] = rinv; }
-      if (cl >= j && cl < d) Gy[j * ldg + cl] = cscale(Gy[j * ldg + cl], rinv);
+      if (lane == 0) { drop[j] = dj ? 1 : 0; rs[j] = rinv; }
+      for (int c = lane; c < d; c += 32)
+        if (c >= j) Gy[j * ldg + c] = cscale(Gy[j * ldg + c], rinv);
       __syncwarp();
-      if (cl > j && cl < d) {
-        const cx<T> rjc = Gy[j * ldg + cl];
-        for (int ai = j + 1; ai <= cl; ai += 4) {     // independent rows, loads first
+      for (int c = lane; c < d; c += 32) {
+        if (c <= j) continue;
+        const cx<T> rjc = Gy[j * ldg + c];
+        for (int ai = j + 1; ai <= c; ai += 4) {     // independent rows, loads first
           cx<T> v[4], rr[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            if (ai + u <= cl) {
-              v[u] = Gy[(ai + u) * ldg + cl];
+            if (ai + u <= c) {
+              v[u] = Gy[(ai + u) * ldg + c];
               rr[u] = Gy[j * ldg + ai + u];
             }
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            if (ai + u <= cl) {
+            if (ai + u <= c) {
               cfma_jc(v[u], cscale(rr[u], T(-1)), rjc);
-              Gy[(ai + u) * ldg + cl] = v[u];
+              Gy[(ai + u) * ldg + c] = v[u];
             }
           }
         }

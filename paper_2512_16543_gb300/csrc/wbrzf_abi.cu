@@ -180,6 +180,7 @@ struct wbrzf {
   bool in_group;         // stepped by a wbrzf_group (its stream belongs to the group)
   int gemm_bf16;         // wbrzf_set_precision_mode: BF16 precoder product
   int refine;            // wbrzf_set_precision_mode: Newton refinement steps (0 or 1)
+  int small64;           // wbrzf_set_fp64_small_solves
   cudaStream_t cstream;  // blocked engine: records the bodies of CUDA-graph IF nodes while a
                          // step is captured (its own captures only; never runs work)
 };
@@ -223,6 +224,7 @@ StepArgs<T> make_args(const wbrzf* h, const void* H, void* W, int mode,
   a.tc_products = (h->prec == WBRZF_C64 && h->engine != WBRZF_ENGINE_BLOCKED_FMA) ? 1 : 0;
   a.gemm_bf16 = (a.tc_products && h->gemm_bf16) ? 1 : 0;
   a.refine = h->refine;
+  a.small64 = h->small64;
   return a;
 }
 
@@ -238,7 +240,7 @@ bool use_blocked(const wbrzf* h) {
 
 // The precision modes run on the blocked engine only.
 bool precision_mode_ok(const wbrzf* h) {
-  return (h->gemm_bf16 == 0 && h->refine == 0) || use_blocked(h);
+  return (h->gemm_bf16 == 0 && h->refine == 0 && h->small64 == 0) || use_blocked(h);
 }
 
 wbrzf_status run_step(wbrzf* h, const void* H, void* W, int mode,
@@ -464,6 +466,7 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   h->glast_engine = 0;
   h->in_group = false;
   h->gemm_bf16 = 0;
+  h->small64 = 0;
   h->refine = 0;
   h->cstream = nullptr;
   {
@@ -720,6 +723,15 @@ wbrzf_status wbrzf_set_precision_mode(wbrzf* h, int bf16_products, int refine_st
   if (bf16_products && h->prec != WBRZF_C64) return WBRZF_ERR_UNSUPPORTED;
   h->gemm_bf16 = bf16_products ? 1 : 0;
   h->refine = refine_steps;
+  invalidate_graph(h);
+  return WBRZF_OK;
+}
+
+wbrzf_status wbrzf_set_fp64_small_solves(wbrzf* h, int enable) {
+  if (!h) return WBRZF_ERR_INVALID_ARG;
+  if (enable && (h->prec != WBRZF_C64 || !blocked_small64_ok(h->K, h->rule.dmax, h->rule.rcap)))
+    return WBRZF_ERR_UNSUPPORTED;
+  h->small64 = enable ? 1 : 0;
   invalidate_graph(h);
   return WBRZF_OK;
 }

@@ -24,8 +24,10 @@ def oracle_rule(rule: binding.RankRule) -> om.RankRule:
 
 
 def run_gpu(Hs: torch.Tensor, alpha, sigma2, p_t, rule: binding.RankRule, *, precision="c64",
-            method="wb", ids=None, trace=False, keep_state=True, device="cuda", engine="auto"):
-    """Hs: [T, B, K, N] complex tensor (any device).  Returns a list of per-step dicts."""
+            method="wb", ids=None, trace=False, keep_state=True, device="cuda", engine="auto",
+            fp64_small=False):
+    """Hs: [T, B, K, N] complex tensor (any device).  Returns a list of per-step dicts.
+    fp64_small: the blocked engine's FP64 small-solve mode."""
     T, B, K, N = Hs.shape
     dt = torch.complex64 if precision == "c64" else torch.complex128
     h = binding.WBRZF(B, N, K, alpha, sigma2, p_t=p_t, rule=rule, method=method,
@@ -33,6 +35,8 @@ def run_gpu(Hs: torch.Tensor, alpha, sigma2, p_t, rule: binding.RankRule, *, pre
                       workspace_for="blocked" if engine.startswith("blocked") else "auto")
     if engine != "auto":
         h.set_engine(engine)
+    if fp64_small:
+        h.set_fp64_small_solves(True)
     if ids is not None:
         h.set_instance_ids(ids)
     if trace:

@@ -16,8 +16,10 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_harness import relerr, run_gpu, run_oracle
-from oracle import rzf
+import types
+
+from gpu_harness import energy_tie, oracle_rule, relerr, run_gpu, run_oracle
+from oracle import lowrank, philox, rzf
 from paper_2512_16543_gb300 import binding, channel
 from test_gpu_parity import _check, _traj
 
@@ -164,7 +166,14 @@ def test_large_array_against_oracle():
     (the leading 64 of 512 singular values hold about half its energy) and a sketch of
     d = 72 columns captures about a third of it, so eta = 0.25 is met at a rank in the 40s
     and the updates take the Woodbury branch, while at eta = 0.9 Algorithm 1 ends unmet at
-    r = d = 72 > r_max and every update is a direct inverse (branch RANK), as in the oracle."""
+    r = d = 72 > r_max and every update is a direct inverse (branch RANK), as in the oracle.
+
+    The rank of a Woodbury update is checked against the oracle's Algorithm 1 run on the dG
+    the GPU itself formed (G_t - G_{t-1} from its complex64 states, the same Philox test
+    matrices): equal, or an energy tie at 1e-3 of the target.  Against the oracle's own dG it
+    may differ by a few components: the FP32 Gram matrix's rounding (about sqrt(N) u of each
+    entry, 4e-6 here) is a sizeable fraction of dG (1.6e-5 of ||G|| per 10 ms step), and on a
+    flat spectrum that moves the cumulative energies by about as much as a component holds."""
     sc = channel.scenario_large_4096x512()
     Hs = _traj(sc, 1, 4, seed=7)
     H64 = Hs[:, 0].numpy().astype(np.complex64).astype(np.complex128)
@@ -178,10 +187,46 @@ def test_large_array_against_oracle():
             assert inf["status"] == 0
             assert inf["branch"] == ref[t].branch == (2 if t == 0 else branch)
             if branch == 1 and t > 0:
-                assert abs(inf["r"] - ref[t].r) <= 4, (inf["r"], ref[t].r)
+                dG = gpu[t]["G"][0].astype(np.complex128) - gpu[t - 1]["G"][0].astype(np.complex128)
+                rr = oracle_rule(rule).resolved(sc.K)
+                lr = lowrank.arsvd(dG, rr.eta, rr.k_init, rr.p, rr.i_max,
+                                   lambda it, d, t=t: philox.omega(sc.K, d, seed=rr.seed, step=t,
+                                                                   instance=0, it=it))
+                own = types.SimpleNamespace(sigma_hat=lr.sigma_hat, r=lr.k_est,
+                                            dA_fro2=float(np.sum(np.abs(dG) ** 2)))
+                assert inf["r"] == lr.k_est or energy_tie(own, 1e-3, eta, inf["r"]), (
+                    inf["r"], lr.k_est, ref[t].r)
             assert relerr(gpu[t]["X"][0], ref[t].X) < 1e-4
             assert relerr(gpu[t]["W"][0], ref[t].W) < 2e-3      # TF32 precoder product
             assert abs(gpu[t]["rate"][0] - ref[t].sum_rate) < 1e-3
         if branch == 4:                           # direct inverse: X G = I to FP32 level
             G = rzf.gram(H64[3], sc.alpha)
             assert np.max(np.abs(gpu[3]["X"][0] @ G - np.eye(sc.K))) < 1e-4
+
+
+@pytest.mark.parametrize("K,N,eta,engine,fp64", [(64, 128, 0.9, "simt", False),
+                                                 (64, 128, 0.9, "blocked", False),
+                                                 (64, 128, 0.97, "blocked", False),
+                                                 (65, 97, 0.95, "blocked", False),
+                                                 (128, 256, 0.8, "blocked", False),
+                                                 (128, 256, 0.85, "blocked", False),
+                                                 (64, 128, 0.9, "blocked", True),
+                                                 (65, 97, 0.95, "blocked", True)])
+def test_sketch_wider_than_a_warp(K, N, eta, engine, fp64):
+    """A wide user disc and a high eta drive Algorithm 1 to sketch widths d = 40, 64 and 72,
+    wider than the 32 lanes of the warp that factors CholQR's Gram matrix and rotates the
+    eigensolver's pairs, with Woodbury ranks 23 to 42 (above the fused Woodbury kernel's first
+    cap of 24, and at K = 128 around its second cap of 40): the one-CTA FMA engine, the blocked engine's fused kernels (both launches) and
+    its per-step kernels, in FP32 and with the FP64 small solves, against the oracle.  The
+    one-CTA engine's shared memory holds d = 40 at K = 64 with r_max = 32."""
+    sc = channel.LeoScenario(n_x=N, n_y=1, K=K, disc_radius=200e3)
+    Hs = _traj(sc, 2, 4, seed=7)
+    rule = binding.RankRule(eta=eta, k_init=2, p=8, r_max=32 if engine == "simt" else 48,
+                            reinverse_period=0, seed=4)
+    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64", engine=engine,
+                        fp64_small=fp64)
+    assert meta["engine"] == engine
+    assert _check(gpu, Hs, sc, rule, "c64", engine=engine) <= 2
+    infos = [g["info"][b] for g in gpu[1:] for b in range(2)]
+    assert max(i["d"] for i in infos) > 32
+    assert any(i["branch"] == 1 and i["r"] > (20 if engine == "simt" else 24) for i in infos)
