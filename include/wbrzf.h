@@ -313,6 +313,18 @@ wbrzf_status wbrzf_set_precision_mode(wbrzf* h, int bf16_products, int refine_st
 wbrzf_status wbrzf_set_fp64_small_solves(wbrzf* h, int enable);
 
 /*
+ * Launch shapes of the blocked engine (not part of the paper's method; no result depends on
+ * the tile cap, the eigensolver threshold changes results only within the eigensolver's
+ * tolerance).  tile_cap: the largest tile edge of the batched complex GEMMs, 64 (default) or
+ * 32 (more, smaller CTAs).  jacobi_cta_min (>= 2): the first sketch width at which the fused
+ * Algorithm 1 kernel's eigensolver of E = B B^H runs on the whole CTA instead of one warp
+ * (default 12; 65 or more keeps one warp).  wbrzf_group_autotune searches both.
+ * Returns WBRZF_ERR_INVALID_ARG for other values.
+ */
+wbrzf_status wbrzf_set_blocked_tuning(wbrzf* h, int tile_cap, int jacobi_cta_min);
+wbrzf_status wbrzf_get_blocked_tuning(const wbrzf* h, int* tile_cap, int* jacobi_cta_min);
+
+/*
  * CUDA-graph replay (not part of the paper's method).  With enable != 0 the next step is
  * captured into a CUDA graph on a stream the handle owns and replayed, fork/joined with the
  * handle's stream by events, for every later step with the same kind (full inverse or
@@ -336,9 +348,12 @@ wbrzf_status wbrzf_set_graph(wbrzf* h, int enable);
  * (all members, their fork and join) and replayed while H[] and W[] stay the same.
  *
  * wbrzf_group_autotune picks each member's engine by measurement: for every engine in
- * engine_mask (bit e = WBRZF_ENGINE_e) that the member accepts, a full inverse on H0[i] then
- * `reps` updates on H1[i] are run and the fastest update (CUDA events) wins.  It finishes
- * with a full inverse on H0[i] with the chosen engine (so the state is that of a fresh
+ * engine_mask (bit e = WBRZF_ENGINE_e) that the member accepts -- and for the blocked
+ * engines every launch shape of the grid {tile cap 64, 32} x {CTA eigensolver from sketch
+ * width 12, one-warp eigensolver} (wbrzf_set_blocked_tuning) -- a full inverse on H0[i] then
+ * `reps` updates on H1[i] are run and the fastest update (CUDA events) wins; the member keeps
+ * the winning engine and launch shape (wbrzf_get_blocked_tuning reads the latter).  It
+ * finishes with a full inverse on H0[i] with the choice (so the state is that of a fresh
  * full inverse), synchronises, and returns WBRZF_ERR_UNSUPPORTED if a member accepts none of
  * the engines.  wbrzf_group_engine returns member i's engine.
  */

@@ -101,6 +101,10 @@ def lib() -> ctypes.CDLL:
     L.wbrzf_set_precision_mode.argtypes = [vp, i32, i32]
     L.wbrzf_set_fp64_small_solves.restype = i32
     L.wbrzf_set_fp64_small_solves.argtypes = [vp, i32]
+    L.wbrzf_set_blocked_tuning.restype = i32
+    L.wbrzf_set_blocked_tuning.argtypes = [vp, i32, i32]
+    L.wbrzf_get_blocked_tuning.restype = i32
+    L.wbrzf_get_blocked_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.wbrzf_set_graph.restype = i32
     L.wbrzf_set_graph.argtypes = [vp, i32]
     L.wbrzf_group_create.restype = i32
@@ -263,6 +267,19 @@ class WBRZF:
         and every direct inverse of G in FP64."""
         _check(lib().wbrzf_set_fp64_small_solves(self._h, int(enable)),
                "wbrzf_set_fp64_small_solves")
+
+    def set_blocked_tuning(self, tile_cap: int = 64, jacobi_cta_min: int = 12) -> None:
+        """Blocked engine launch shapes: GEMM tile cap (64 or 32), first sketch width of the
+        CTA-wide eigensolver."""
+        _check(lib().wbrzf_set_blocked_tuning(self._h, int(tile_cap), int(jacobi_cta_min)),
+               "wbrzf_set_blocked_tuning")
+
+    @property
+    def blocked_tuning(self) -> tuple[int, int]:
+        cap, jmin = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().wbrzf_get_blocked_tuning(self._h, ctypes.byref(cap), ctypes.byref(jmin)),
+               "wbrzf_get_blocked_tuning")
+        return cap.value, jmin.value
 
     def set_graph(self, enable: bool = True) -> None:
         """Replay steps from a CUDA graph while H, W and the mask stay the same tensors."""

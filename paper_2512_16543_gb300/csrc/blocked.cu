@@ -39,9 +39,6 @@ constexpr int kWoodburyWide = 13;    // rank above the fused Woodbury kernel's c
 // fused Algorithm 1 kernel; each bounds the columns a stream covers to MAXA kThreads / K.
 constexpr int kWoodburyMaxA = 12;
 constexpr int kWoodburyFusedTop = 24;      // largest rank of the fused Woodbury kernel (FP32)
-// Sketch width from which the fused kernel's eigensolver runs on the whole CTA instead of one
-// warp
-constexpr int kJacobiCtaMin = 12;
 // Sketch widths up to this take the register CholQR in the fused kernel as well
 constexpr int kCqRegsWide = 16;
 template <class T> constexpr int fused_max_a() { return sizeof(T) == 4 ? 12 : 6; }  // Woodbury step whose rank exceeds the fused kernel's cap:
@@ -196,6 +193,10 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) cgemm_kernel(const GemmAr
   }
 }
 
+// The tile cap of the step being enqueued on this host thread (set by run_blocked from the
+// handle's tuning; the tile shape changes no result: each output's k-sum keeps its order).
+thread_local int t_tile_cap = 64;
+
 template <class T, int BM, int BN>
 cudaError_t launch_cgemm(const GemmArgs<T>& g, int batch, cudaStream_t s) {
   dim3 grid((g.n + BN - 1) / BN, (g.m + BM - 1) / BM, batch);
@@ -213,8 +214,9 @@ cudaError_t gemm(cudaStream_t s, int batch, int m, int n, int k, const cx<T>* A,
   GemmArgs<T> g{m, n, k, A, lda, sA, opA, B, ldb, sB, opB, C, ldc, sC, alpha, scale, beta,
                 ctl, gidx, gmask, dshift, live.m, live.n, live.k, lm, ln, lk};
   // tile widths from the extents known on the host (the control-word limits can only shrink
-  // them further)
-  const bool nm = (m < live.m ? m : live.m) <= 32, nn = (n < live.n ? n : live.n) <= 32;
+  // them further), at most the step's tile cap (t_tile_cap)
+  const bool nm = (m < live.m ? m : live.m) <= 32 || t_tile_cap <= 32;
+  const bool nn = (n < live.n ? n : live.n) <= 32 || t_tile_cap <= 32;
   if (nm && nn) return launch_cgemm<T, 32, 32>(g, batch, s);
   if (nm) return launch_cgemm<T, 32, 64>(g, batch, s);
   if (nn) return launch_cgemm<T, 64, 32>(g, batch, s);
@@ -405,30 +407,18 @@ __global__ void fwdsubst_kernel(const StepArgs<T> a, const Bufs<T> w, int d) {
   }
 }
 
-// Sum over a CTA of NT threads (NT a multiple of 32, at most 1024); red holds 33 values.
-template <int NT, class T>
-__device__ T block_sum_n(T v, T* red) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    T r = (l < NT / 32) ? red[l] : T(0);
-    r = warp_sum(r);
-    if (l == 0) red[32] = r;
-  }
-  __syncthreads();
-  const T out = red[32];
-  __syncthreads();
-  return out;
-}
-
 // Cyclic Jacobi eigendecomposition of E (d x d Hermitian, ld dmax): eigenvalues to lam,
 // eigenvectors (columns) to Uh, one CTA of NT threads per instance; each round is
 // jacobi_round (all pairs' rotations, then every 2 x 2 block of J^H E J and U J: two barriers).
 // S: the real type of the rotations (float or double for FP32 buffers, double for FP64).
+// skip_ok: the eigenvectors are not needed when the energy test fails (every iteration but
+// the last, or a last one whose fall-through rank d takes the direct inverse and no trace is
+// kept).  Then, when tr(E) = ||B||_F^2 -- the sum of all d eigenvalues -- is short of the
+// energy target by more than the rotations' rounding, no rank meets eq. 14: E's diagonal is
+// passed on as lam unrotated (it has the same sum, so rank_kernel's test fails the same way)
+// and U is not formed.
 template <int NT, class T, class S>
-__global__ void __launch_bounds__(NT) jacobi_kernel(const Bufs<T> w, int d) {
+__global__ void __launch_bounds__(NT) jacobi_kernel(const Bufs<T> w, int d, int skip_ok) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int b = blockIdx.x, tid = threadIdx.x, dmax = w.dmax;
   if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
@@ -447,21 +437,34 @@ __global__ void __launch_bounds__(NT) jacobi_kernel(const Bufs<T> w, int d) {
     U[i * dmax + j] = cmk<S>(i == j ? S(1) : S(0), S(0));
   }
   __syncthreads();
+  // sweeps stop when the largest |E_pq|^2 (p < q) is at most tol2 tr(E)^2, and pairs below
+  // that are not rotated (the test of the fused kernel's solvers)
   const int dm1 = d + (d & 1) - 1;
-  const S eps = (sizeof(S) == 4) ? S(1e-8) : S(1e-26);
+  const S tol2 = (sizeof(S) == 4) ? S(1e-8) : S(1e-28);
+  S tr = 0;
+  for (int j = 0; j < d; ++j) tr += E[j * dmax + j].re;
+  const S thr = tol2 * tr * tr;
+  if (skip_ok && (double)tr < w.et[b] * (1.0 - 1e-4)) {
+    for (int j = tid; j < d; j += NT)
+      w.lam[(size_t)b * dmax + j] = (T)fmax(E[j * dmax + j].re, S(0));
+    return;
+  }
   for (int sweep = 0; sweep < ((sizeof(S) == 4) ? 12 : 20); ++sweep) {
-    S off = 0, tot = 0;
+    S mx = 0;
     for (int e = tid; e < d * d; e += NT) {
       const int i = e / d, j = e - i * d;
-      const S v = cabs2(E[i * dmax + j]);
-      tot += v;
-      if (i != j) off += v;
+      if (j > i) mx = fmax(mx, cabs2(E[i * dmax + j]));
     }
-    off = block_sum_n<NT>(off, red);
-    tot = block_sum_n<NT>(tot, red);
-    if (!(off > eps * tot)) break;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    mx = 0;
+    for (int q = 0; q < NT / 32; ++q) mx = fmax(mx, red[q]);
+    __syncthreads();
+    if (!(mx > thr)) break;
     for (int rnd = 0; rnd < dm1; ++rnd)
-      jacobi_round<S, NT>(E, U, dmax, d, rnd, pp, pq, rc, rs, ph);
+      jacobi_round<S, NT>(E, U, dmax, d, rnd, pp, pq, rc, rs, ph, thr);
   }
   cx<T>* Ug = w.Uh + (size_t)b * w.L.sGy;
   for (int e = tid; e < d * d; e += NT) {
@@ -723,7 +726,7 @@ __device__ void jacobi_eig_cta(cx<T>* E, cx<T>* U, int ld, int d, T tol2, int ma
     __syncthreads();
     if (!(mx > thr)) break;
     for (int rnd = 0; rnd < dm1; ++rnd)
-      jacobi_round<T, kThreads>(E, U, ld, d, rnd, pp, pq, rc, rs, ph);
+      jacobi_round<T, kThreads>(E, U, ld, d, rnd, pp, pq, rc, rs, ph, thr);
   }
 }
 
@@ -910,7 +913,7 @@ __global__ void __launch_bounds__(kThreads, 2) arsvd_fused_kernel(const StepArgs
     } else {
       mm<T, false, true, MM_SET>(d, d, K, Bm, K, Bm, K, Gy, df);
       __syncthreads();
-      if (d >= kJacobiCtaMin)      // (perm, drop, cn, rs and Omega are scratch here)
+      if (d >= a.jacobi_cta_min)   // (perm, drop, cn, rs and Omega are scratch here)
         jacobi_eig_cta<T>(Gy, Uh, df, d, tol2, sweeps, perm, drop, cn, rs, Om, red);
       else
         jacobi_eig<T>(Gy, df, Uh, df, d, tol2, sweeps);
@@ -1610,6 +1613,7 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
   const int B = a.batch, K = a.K, N = a.N, dmax = a.dmax, rcap = a.rcap;
   const Bufs<T> w = make_bufs<T>(base, B, N, K, dmax, rcap);
   const BlockedLayout& L = w.L;
+  t_tile_cap = a.tile_cap;
   const size_t KK = (size_t)K * K;
   cudaError_t e;
   int nl = 0;
@@ -1713,8 +1717,10 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
                        one, w.dsc, zero, w.ctl, C_ACTIVE, 2, nullptr, Live{d, 1 << 30, 1 << 30}));
         WB_TRY(gemm<T>(q, B, d, d, K, w.Bm, K, L.sBm, 0, w.Bm, K, L.sBm, 1, w.E, dmax, L.sGy,
                        one, nullptr, zero, w.ctl, C_ACTIVE, 2));
-        if (d > 32) jac1024<<<B, 1024, js, q>>>(w, d);
-        else jac256<<<B, 256, js, q>>>(w, d);
+        const int skip_ok = !last || ((d > a.r_max || (double)d / K > a.switch_ratio) &&
+                                      a.trace == nullptr);
+        if (d > 32) jac1024<<<B, 1024, js, q>>>(w, d, skip_ok);
+        else jac256<<<B, 256, js, q>>>(w, d, skip_ok);
         WB_TRY(cudaGetLastError());
         rank_kernel<T><<<B, 256, 0, q>>>(a, w, it, d, last);
         WB_TRY(cudaGetLastError());

@@ -54,6 +54,10 @@ struct StepArgs {
   int refine;              // blocked engine: one Newton step X <- X (2 I - G X) per snapshot
   int small64;             // blocked engine, complex64: the eigensolver of B B^H, the
                            // capacitance inverse and every direct inverse of G in FP64
+  // blocked engine launch shapes (wbrzf_set_blocked_tuning): the largest tile edge of the
+  // batched complex GEMMs (64 or 32), and the sketch width from which the fused kernel's
+  // eigensolver runs on the whole CTA instead of one warp
+  int tile_cap, jacobi_cta_min;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -282,10 +282,12 @@ __device__ __forceinline__ bool jacobi_rotation<double>(cx<double> bpq, double e
 // (x_k, x_{dd-1-k}), dd = d rounded up to even) at once: phase 1 computes the rotations; as
 // the pairs are disjoint, every 2 x 2 block (rows of pair k, columns of pair l) of J^H E J
 // depends only on the same block of E and the two rotations, so phase 2 updates all blocks
-// and U's columns.  pp, pq, rc, rs, ph: npairs-entry scratch.  Ends with a barrier.
+// and U's columns.  pp, pq, rc, rs, ph: npairs-entry scratch.  A pair with |E_pq|^2 <= thr is
+// left alone (threshold Jacobi: the last sweeps then rotate few pairs and skip their blocks).
+// Ends with a barrier.
 template <class T, int NT>
 __device__ void jacobi_round(cx<T>* E, cx<T>* U, int dmax, int d, int rnd, int* pp, int* pq,
-                             T* rc, T* rs, cx<T>* ph) {
+                             T* rc, T* rs, cx<T>* ph, T thr) {
   const int tid = threadIdx.x;
   const int dd = d + (d & 1), npairs = dd >> 1, dm1 = dd - 1;
   for (int k = tid; k < npairs; k += NT) {
@@ -301,8 +303,9 @@ __device__ void jacobi_round(cx<T>* E, cx<T>* U, int dmax, int d, int rnd, int* 
     const int p1 = min(p0, q0), q1 = max(p0, q0);
     T c = 1, sn = 0;
     cx<T> f = cmk<T>(1, 0);
-    const bool act = q1 < d && jacobi_rotation<T>(E[p1 * dmax + q1], E[p1 * dmax + p1].re,
-                                                   E[q1 * dmax + q1].re, c, sn, f);
+    const bool act = q1 < d && cabs2(E[p1 * dmax + q1]) > thr &&
+                     jacobi_rotation<T>(E[p1 * dmax + q1], E[p1 * dmax + p1].re,
+                                        E[q1 * dmax + q1].re, c, sn, f);
     pp[k] = act ? p1 : -1 - p1;        // inactive: -1 - p (p is still a row / column)
     pq[k] = q1;
     rc[k] = c;

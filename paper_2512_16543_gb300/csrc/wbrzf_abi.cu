@@ -22,6 +22,13 @@ cudaError_t launch_wait_selftest(unsigned long long* out, cudaStream_t s);   // 
 
 namespace {
 
+// Default launch shapes of the blocked engine (wbrzf_set_blocked_tuning): 64-wide GEMM tiles
+// where the output is wider than 32, and the CTA-wide eigensolver from sketch width 12 (a
+// phase-clock probe of the fused kernel at K = 64 and 128 measured 12 and 16 equal and 24 and
+// the one-warp solver slower)
+constexpr int kDefaultTileCap = 64;
+constexpr int kDefaultJacobiCtaMin = 12;
+
 thread_local char g_cuda_err[256] = "";
 
 wbrzf_status cuda_fail(cudaError_t e) {
@@ -181,6 +188,8 @@ struct wbrzf {
   int gemm_bf16;         // wbrzf_set_precision_mode: BF16 precoder product
   int refine;            // wbrzf_set_precision_mode: Newton refinement steps (0 or 1)
   int small64;           // wbrzf_set_fp64_small_solves
+  int tile_cap;          // wbrzf_set_blocked_tuning: largest batched-GEMM tile edge (64, 32)
+  int jacobi_cta_min;    // wbrzf_set_blocked_tuning: first sketch width of the CTA eigensolver
   cudaStream_t cstream;  // blocked engine: records the bodies of CUDA-graph IF nodes while a
                          // step is captured (its own captures only; never runs work)
 };
@@ -225,6 +234,8 @@ StepArgs<T> make_args(const wbrzf* h, const void* H, void* W, int mode,
   a.gemm_bf16 = (a.tc_products && h->gemm_bf16) ? 1 : 0;
   a.refine = h->refine;
   a.small64 = h->small64;
+  a.tile_cap = h->tile_cap;
+  a.jacobi_cta_min = h->jacobi_cta_min;
   return a;
 }
 
@@ -468,6 +479,8 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   h->gemm_bf16 = 0;
   h->small64 = 0;
   h->refine = 0;
+  h->tile_cap = kDefaultTileCap;
+  h->jacobi_cta_min = kDefaultJacobiCtaMin;
   h->cstream = nullptr;
   {
     const size_t tc = tc_smem_bytes(K, r.dmax, r.rcap);
@@ -727,6 +740,21 @@ wbrzf_status wbrzf_set_precision_mode(wbrzf* h, int bf16_products, int refine_st
   return WBRZF_OK;
 }
 
+wbrzf_status wbrzf_set_blocked_tuning(wbrzf* h, int tile_cap, int jacobi_cta_min) {
+  if (!h || (tile_cap != 32 && tile_cap != 64) || jacobi_cta_min < 2) return WBRZF_ERR_INVALID_ARG;
+  h->tile_cap = tile_cap;
+  h->jacobi_cta_min = jacobi_cta_min;
+  invalidate_graph(h);
+  return WBRZF_OK;
+}
+
+wbrzf_status wbrzf_get_blocked_tuning(const wbrzf* h, int* tile_cap, int* jacobi_cta_min) {
+  if (!h || !tile_cap || !jacobi_cta_min) return WBRZF_ERR_INVALID_ARG;
+  *tile_cap = h->tile_cap;
+  *jacobi_cta_min = h->jacobi_cta_min;
+  return WBRZF_OK;
+}
+
 wbrzf_status wbrzf_set_fp64_small_solves(wbrzf* h, int enable) {
   if (!h) return WBRZF_ERR_INVALID_ARG;
   if (enable && (h->prec != WBRZF_C64 || !blocked_small64_ok(h->K, h->rule.dmax, h->rule.rcap)))
@@ -914,15 +942,24 @@ wbrzf_status wbrzf_group_autotune(wbrzf_group* g, const void* const* H0, const v
   if (!g || !H0 || !H1 || !W || reps < 1) return WBRZF_ERR_INVALID_ARG;
   static const int cand[] = {WBRZF_ENGINE_TENSOR, WBRZF_ENGINE_SIMT, WBRZF_ENGINE_BLOCKED,
                              WBRZF_ENGINE_BLOCKED_FMA};
+  // the blocked engines' launch shapes tried for each: (tile cap, first sketch width of the
+  // CTA-wide eigensolver); 65 keeps the one-warp eigensolver at every fused width
+  static const int tune[][2] = {{64, kDefaultJacobiCtaMin}, {32, kDefaultJacobiCtaMin},
+                                {64, 65}, {32, 65}};
   wbrzf_group_set_graph(g, g->graph);          // drops the captured step
   for (size_t i = 0; i < g->m.size(); ++i) {
     wbrzf* h = g->m[i];
-    const int own = h->engine;
-    int best = -1;
+    const int own = h->engine, own_cap = h->tile_cap, own_jmin = h->jacobi_cta_min;
+    int best = -1, best_cap = own_cap, best_jmin = own_jmin;
     float best_ms = 0.f;
-    for (int c : cand) {
+    for (int ci = 0; ci < (int)(sizeof(cand) / sizeof(cand[0])) * 4; ++ci) {
+      const int c = cand[ci / 4], ti = ci % 4;
+      const bool blocked = c == WBRZF_ENGINE_BLOCKED || c == WBRZF_ENGINE_BLOCKED_FMA;
+      if (!blocked && ti > 0) continue;
       if (!((engine_mask >> c) & 1u)) continue;
       if (wbrzf_set_engine(h, c) != WBRZF_OK) continue;
+      h->tile_cap = blocked ? tune[ti][0] : own_cap;
+      h->jacobi_cta_min = blocked ? tune[ti][1] : own_jmin;
       h->t = 0;
       wbrzf_status st = run_step(h, H0[i], W[i], group_mode(h, true), nullptr);
       if (st != WBRZF_OK) continue;
@@ -941,9 +978,13 @@ wbrzf_status wbrzf_group_autotune(wbrzf_group* g, const void* const* H0, const v
       if (st == WBRZF_OK && tmin >= 0.f && (best < 0 || tmin < best_ms)) {
         best = c;
         best_ms = tmin;
+        best_cap = h->tile_cap;
+        best_jmin = h->jacobi_cta_min;
       }
     }
     wbrzf_set_engine(h, best >= 0 ? best : own);
+    h->tile_cap = best >= 0 ? best_cap : own_cap;
+    h->jacobi_cta_min = best >= 0 ? best_jmin : own_jmin;
     if (best < 0) return WBRZF_ERR_UNSUPPORTED;
     g->engine[i] = best;
     h->t = 0;

@@ -138,6 +138,9 @@ def test_group_autotune_chooses_an_accepted_engine_and_keeps_parity():
     grp = binding.WBRZFGroup(members)
     Ws = [torch.empty(B, sc.N, sc.K, dtype=torch.complex64, device="cuda") for sc, B, _ in cls]
     chosen = grp.autotune([H[0] for H in Hs], [H[1] for H in Hs], Ws, reps=2)
+    for h, e in zip(members, chosen):           # the launch shape is one of the grid's
+        cap, jmin = h.blocked_tuning
+        assert cap in (32, 64) and jmin in (12, 65) if e.startswith("blocked") else True
     assert chosen[0] in ("tensor", "simt", "blocked", "blocked_fma")
     assert chosen[1] in ("tensor", "simt", "blocked", "blocked_fma")
     assert chosen[2] in ("blocked", "blocked_fma")                  # K = 80: blocked only
@@ -158,3 +161,43 @@ def test_group_autotune_chooses_an_accepted_engine_and_keeps_parity():
     grp.close()
     for h in members:
         h.close()
+
+
+def test_blocked_launch_shapes_keep_results():
+    """The batched GEMMs' tile cap changes no result (each output's k-sum keeps its order):
+    bitwise equal W and X with 64- and 32-wide tiles.  The one-warp and the CTA-wide
+    eigensolvers both meet the oracle at the complex64 tolerances."""
+    sc = channel.LeoScenario(n_x=16, n_y=8, K=96, disc_radius=100e3)
+    Hs = channel.trajectory(channel.draw_trajectories(sc, 3, seed=96), 5, dtype=torch.complex128)
+    rule = binding.RankRule(eta=0.9, k_init=2, p=8, r_max=32, reinverse_period=3, seed=2)
+    outs = {}
+    for cap, jmin in ((64, 12), (32, 12), (64, 65)):
+        h = binding.WBRZF(3, sc.N, sc.K, sc.alpha, sc.sigma2, p_t=sc.p_t, rule=rule,
+                          workspace_for="blocked")
+        h.set_engine("blocked")
+        h.set_blocked_tuning(cap, jmin)
+        assert h.blocked_tuning == (cap, jmin)
+        rec = []
+        for t in range(5):
+            H = Hs[t].to(device="cuda", dtype=torch.complex64)
+            W = h.full_inverse(H) if t == 0 else h.update(H)
+            rec.append((W.cpu().numpy(), h.state()[1].cpu().numpy(), h.step_info()))
+        outs[(cap, jmin)] = rec
+        h.close()
+    for t in range(5):
+        np.testing.assert_array_equal(outs[(64, 12)][t][0], outs[(32, 12)][t][0])
+        np.testing.assert_array_equal(outs[(64, 12)][t][1], outs[(32, 12)][t][1])
+    for key in ((64, 12), (64, 65)):
+        for b in range(3):
+            Hb = Hs[:, b].numpy().astype(np.complex64).astype(np.complex128)
+            ref = run_oracle(Hb, sc.alpha, sc.sigma2, sc.p_t, rule, instance=b)
+            for t in range(5):
+                W, X, info = outs[key][t]
+                assert relerr(X[b], ref[t].X) < 1e-4, (key, t, b)
+                assert relerr(W[b], ref[t].W) < tf32_w_tol(Hb[t], X[b], ref[t].W, sc.p_t)
+    with pytest.raises(binding.WbrzfError):
+        h = binding.WBRZF(1, sc.N, sc.K, sc.alpha, sc.sigma2, p_t=sc.p_t, rule=rule)
+        try:
+            h.set_blocked_tuning(48, 12)
+        finally:
+            h.close()
