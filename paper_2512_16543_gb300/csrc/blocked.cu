@@ -389,22 +389,41 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const Bufs<T> w, int d, i
   }
 }
 
-// Q <- Q R^{-1}, one thread per row of Q (K x dmax, columns >= d untouched: zero)
+// Q <- Q R^{-1}, one thread per row of Q (K x dmax, columns >= d untouched: zero), kFwdRows
+// rows per CTA.  R, 1 / R_cc and the CTA's rows of Q are staged in shared memory (layout of
+// fwdsubst_smem), so that the d (d - 1) / 2 dependent steps of a row wait on shared memory,
+// not on L2.
+constexpr int kFwdRows = 64;
+inline size_t fwdsubst_smem(int d, size_t cxb, size_t tb) {
+  return ((size_t)d * d + (size_t)kFwdRows * (d + 1)) * cxb + (size_t)d * tb;
+}
 template <class T>
-__global__ void fwdsubst_kernel(const StepArgs<T> a, const Bufs<T> w, int d) {
+__global__ void __launch_bounds__(kFwdRows) fwdsubst_kernel(const StepArgs<T> a,
+                                                            const Bufs<T> w, int d) {
+  extern __shared__ __align__(16) unsigned char sm[];
   const int b = blockIdx.y;
   if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.K) return;
-  const int dmax = w.dmax;
-  cx<T>* q = w.Q + (size_t)b * w.L.sOm + (size_t)i * dmax;
-  const cx<T>* R = w.Gy + (size_t)b * w.L.sGy;
-  const T* rv = w.rinv + (size_t)b * dmax;
-  for (int c = 0; c < d; ++c) {
-    cx<T> v = q[c];
-    for (int a2 = 0; a2 < c; ++a2) cfma(v, cscale(q[a2], T(-1)), R[a2 * dmax + c]);
-    q[c] = cscale(v, rv[c]);
+  const int dmax = w.dmax, tid = threadIdx.x, ld = d + 1;
+  const int i0 = blockIdx.x * kFwdRows, nrow = min(kFwdRows, a.K - i0);
+  cx<T>* const Rs = reinterpret_cast<cx<T>*>(sm);               // d x d
+  cx<T>* const Qs = Rs + (size_t)d * d;                          // kFwdRows x (d + 1)
+  T* const rvs = reinterpret_cast<T*>(Qs + (size_t)kFwdRows * ld);
+  cx<T>* const Qg = w.Q + (size_t)b * w.L.sOm + (size_t)i0 * dmax;
+  const cx<T>* const R = w.Gy + (size_t)b * w.L.sGy;
+  for (int e = tid; e < d * d; e += kFwdRows) Rs[e] = R[(e / d) * dmax + e % d];
+  for (int e = tid; e < d; e += kFwdRows) rvs[e] = w.rinv[(size_t)b * dmax + e];
+  for (int e = tid; e < nrow * d; e += kFwdRows) Qs[(e / d) * ld + e % d] = Qg[(e / d) * dmax + e % d];
+  __syncthreads();
+  if (tid < nrow) {
+    cx<T>* const q = Qs + (size_t)tid * ld;
+    for (int c = 0; c < d; ++c) {
+      cx<T> v = q[c];
+      for (int a2 = 0; a2 < c; ++a2) cfma(v, cscale(q[a2], T(-1)), Rs[a2 * d + c]);
+      q[c] = cscale(v, rvs[c]);
+    }
   }
+  __syncthreads();
+  for (int e = tid; e < nrow * d; e += kFwdRows) Qg[(e / d) * dmax + e % d] = Qs[(e / d) * ld + e % d];
 }
 
 // Cyclic Jacobi eigendecomposition of E (d x d Hermitian, ld dmax): eigenvalues to lam,
@@ -1638,6 +1657,9 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
     e = cudaFuncSetAttribute(cholesky_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(capinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fwdsubst_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fwdsubst_smem(dmax, sizeof(cx<T>), sizeof(T)));
   if (e == cudaSuccess && s64)
     e = cudaFuncSetAttribute(inverse64_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)inv64_smem(K));
@@ -1710,7 +1732,8 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
                          L.sGy, one, nullptr, zero, w.ctl, C_ACTIVE, 2));
           cholesky_kernel<T><<<B, 256, cs, q>>>(w, d, pass);
           WB_TRY(cudaGetLastError());
-          fwdsubst_kernel<T><<<dim3((K + 127) / 128, B), 128, 0, q>>>(a, w, d);
+          fwdsubst_kernel<T><<<dim3((K + kFwdRows - 1) / kFwdRows, B), kFwdRows,
+                               fwdsubst_smem(d, sizeof(cx<T>), sizeof(T)), q>>>(a, w, d);
           WB_TRY(cudaGetLastError());
         }
         WB_TRY(gemm<T>(q, B, dmax, K, K, w.Q, dmax, L.sOm, 1, w.D, K, L.sD, 0, w.Bm, K, L.sBm,
