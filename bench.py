@@ -391,7 +391,7 @@ def main_uneven(args):
             h.set_instance_ids([int(i) for i in c.index])
             hs.append(h)
         grp = binding.WBRZFGroup(hs)
-        engines = grp.autotune([H[0] for H in Hs], [H[1] for H in Hs], Ws, reps=2)
+        engines = grp.autotune([H[0] for H in Hs], [H[1] for H in Hs], Ws, reps=5)
         grp.set_graph(True)
         return grp, hs, engines
 

@@ -199,6 +199,15 @@ wbrzf_status wbrzf_get_steps(wbrzf* h, int* host_out, int count);
  */
 wbrzf_status wbrzf_sum_rate(wbrzf* h, float* sinr_out, float* sum_rate_out);
 
+/*
+ * The last call's per-instance sum-rate R_sum of eq. 15 (Section VI) as the kernels summed
+ * it, in FP64 (device double[batch]), on the stream: the per-user terms log2(1 + SINR_n) are
+ * computed in the handle's precision and added in FP64 (wbrzf_sum_rate and the step info
+ * carry the same sum rounded to FP32).  Instances that sat a masked step out keep their
+ * previous value.
+ */
+wbrzf_status wbrzf_sum_rate_f64(wbrzf* h, double* sum_rate_out);
+
 /* Copy the last call's per-instance outcome for instances [0, count) into host memory.
  * Synchronises the stream.  Returns WBRZF_ERR_NUMERICAL if any of them has status != 0. */
 wbrzf_status wbrzf_step_info_get(wbrzf* h, wbrzf_step_info* host_out, int count);

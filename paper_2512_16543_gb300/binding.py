@@ -101,6 +101,8 @@ def lib() -> ctypes.CDLL:
     L.wbrzf_set_precision_mode.argtypes = [vp, i32, i32]
     L.wbrzf_set_fp64_small_solves.restype = i32
     L.wbrzf_set_fp64_small_solves.argtypes = [vp, i32]
+    L.wbrzf_sum_rate_f64.restype = i32
+    L.wbrzf_sum_rate_f64.argtypes = [vp, vp]
     L.wbrzf_set_blocked_tuning.restype = i32
     L.wbrzf_set_blocked_tuning.argtypes = [vp, i32, i32]
     L.wbrzf_get_blocked_tuning.restype = i32
@@ -320,6 +322,12 @@ class WBRZF:
         rate = torch.empty(self.batch, dtype=torch.float32, device=self.device)
         _check(lib().wbrzf_sum_rate(self._h, _ptr(sinr), _ptr(rate)), "wbrzf_sum_rate")
         return sinr, rate
+
+    def sum_rate64(self) -> torch.Tensor:
+        """Per-instance R_sum summed in FP64: float64 tensor [batch] on the device."""
+        rate = torch.empty(self.batch, dtype=torch.float64, device=self.device)
+        _check(lib().wbrzf_sum_rate_f64(self._h, _ptr(rate)), "wbrzf_sum_rate_f64")
+        return rate
 
     def step_info(self, raise_on_numerical: bool = False) -> list[dict]:
         arr = (StepInfoC * self.batch)()

@@ -1510,13 +1510,14 @@ __global__ void __launch_bounds__(256) sinr_final_kernel(const StepArgs<T> a, co
   for (int n = tid; n < K; n += 256) part += rows[3 * n];
   const T wn2 = block_sum(part, red);
   const T s = sqrt(a.p_t / wn2);
-  T rate = 0;
+  double rate = 0;                             // R_sum's terms summed in FP64
   for (int n = tid; n < K; n += 256) {
     const T sn = (s * s * rows[3 * n + 2]) / (s * s * rows[3 * n + 1] + sigma2);
     a.sinr[(size_t)b * K + n] = (float)sn;
-    rate += log2(T(1) + sn);
+    rate += (double)log2(T(1) + sn);
   }
-  const T R = block_sum(rate, red);
+  __shared__ double red64[33];
+  const double R = block_sum(rate, red64);
   if (tid == 0) {
     const int* ctl = w.ctl + 8 * b;
     int status = ctl[C_STATUS];
@@ -1531,6 +1532,7 @@ __global__ void __launch_bounds__(256) sinr_final_kernel(const StepArgs<T> a, co
     inf.sum_rate = (float)R;
     inf.status = status;
     a.info[b] = inf;
+    if (a.rate64 != nullptr) a.rate64[b] = R;
     w.ws[b] = s;
     advance_step(a, b, step_index(a, b));   // the last kernel that reads t in this step
   }

@@ -123,6 +123,7 @@ wbrzf_status run_noalloc(int batch, int N, int K, const void* H, double alpha, d
   a.Xs = reinterpret_cast<cx<T>*>(base);   // neither pointer is dereferenced
   a.info = reinterpret_cast<wbrzf_step_info*>(base + sl.oInfo);
   a.sinr = reinterpret_cast<float*>(base + sl.oSinr);
+  a.rate64 = nullptr;
   a.alpha = d_alpha;
   a.sigma2 = d_sigma2;
   a.ids = d_ids;
@@ -137,6 +138,9 @@ wbrzf_status run_noalloc(int batch, int N, int K, const void* H, double alpha, d
   a.tc_products = 0;
   a.gemm_bf16 = 0;
   a.refine = 0;
+  a.small64 = 0;
+  a.tile_cap = 64;
+  a.jacobi_cta_min = 12;
   a.eta = 1.0;
   a.k_init = 1;
   a.p = 0;

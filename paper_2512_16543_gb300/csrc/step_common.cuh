@@ -29,6 +29,7 @@ struct StepArgs {
   cx<T>* Xs;               // [batch][K][K] resident inverse
   wbrzf_step_info* info;   // [batch]
   float* sinr;             // [batch][K]
+  double* rate64;          // [batch] R_sum summed in FP64 (NULL: not kept)
   const T* alpha;          // [batch]
   const T* sigma2;         // [batch]
   const uint32_t* ids;     // [batch] instance identity (Philox counter word 3 = 16 id + it)

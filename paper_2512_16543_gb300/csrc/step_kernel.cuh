@@ -1251,7 +1251,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
   const T s = sqrt(a.p_t / wn2);
   // SINR_n = s^2 |M_nn|^2 / (s^2 sum_{i != n} |M_ni|^2 + sigma^2): warp w takes rows
   // w, w + 8, ...; its lanes read a row's consecutive entries and sum them by shuffles
-  T rate = 0;
+  double rate = 0;                            // R_sum's terms summed in FP64
   {
     const int wp = tid >> 5, ln = tid & 31;
     for (int n = wp; n < K; n += kThreads / 32) {
@@ -1266,11 +1266,17 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       if (ln == 0) {
         const T sinr = (s * s * sig) / (s * s * intf + sigma2);
         a.sinr[(size_t)b * K + n] = (float)sinr;
-        rate += log2(T(1) + sinr);
+        rate += (double)log2(T(1) + sinr);
       }
     }
   }
-  const T R = block_sum(rate, red);
+  // only lane 0 of each warp holds a partial sum: one FP64 slot per warp, summed in a fixed
+  // order by every thread
+  __shared__ double red64[kThreads / 32];
+  if ((tid & 31) == 0) red64[tid >> 5] = rate;
+  __syncthreads();
+  double R = 0;
+  for (int q = 0; q < kThreads / 32; ++q) R += red64[q];
   if (!isfinite(s) || !isfinite(R)) status |= WBRZF_STATUS_NONFINITE;
   if (tid == 0) {
     wbrzf_step_info inf;
@@ -1283,6 +1289,7 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
     inf.sum_rate = (float)R;
     inf.status = status;
     a.info[b] = inf;
+    if (a.rate64 != nullptr) a.rate64[b] = R;
   }
 
   return s;

@@ -37,7 +37,7 @@ wbrzf_status cuda_fail(cudaError_t e) {
 }
 
 struct WsLayout {
-  size_t oG, oX, oInfo, oSinr, oAlpha, oSigma2, oIds, oTvec, bytes;
+  size_t oG, oX, oInfo, oSinr, oRate64, oAlpha, oSigma2, oIds, oTvec, bytes;
 };
 
 size_t cx_bytes(wbrzf_precision p) { return p == WBRZF_C128 ? 16 : 8; }
@@ -51,6 +51,7 @@ WsLayout ws_layout(int batch, int K, wbrzf_precision prec) {
   w.oX = o;      o = align_up(o + B * KK * cx_bytes(prec), 256);
   w.oInfo = o;   o = align_up(o + B * sizeof(wbrzf_step_info), 256);
   w.oSinr = o;   o = align_up(o + B * K * sizeof(float), 256);
+  w.oRate64 = o; o = align_up(o + B * sizeof(double), 256);
   w.oAlpha = o;  o = align_up(o + B * re_bytes(prec), 256);
   w.oSigma2 = o; o = align_up(o + B * re_bytes(prec), 256);
   w.oIds = o;    o = align_up(o + B * sizeof(uint32_t), 256);
@@ -206,6 +207,7 @@ StepArgs<T> make_args(const wbrzf* h, const void* H, void* W, int mode,
   a.Xs = reinterpret_cast<cx<T>*>(h->ws + h->wl.oX);
   a.info = reinterpret_cast<wbrzf_step_info*>(h->ws + h->wl.oInfo);
   a.sinr = reinterpret_cast<float*>(h->ws + h->wl.oSinr);
+  a.rate64 = reinterpret_cast<double*>(h->ws + h->wl.oRate64);
   a.alpha = reinterpret_cast<const T*>(h->ws + h->wl.oAlpha);
   a.sigma2 = reinterpret_cast<const T*>(h->ws + h->wl.oSigma2);
   a.ids = reinterpret_cast<const uint32_t*>(h->ws + h->wl.oIds);
@@ -568,6 +570,14 @@ wbrzf_status wbrzf_sum_rate(wbrzf* h, float* sinr_out, float* sum_rate_out) {
                           h->ws + h->wl.oInfo + offsetof(wbrzf_step_info, sum_rate),
                           sizeof(wbrzf_step_info), sizeof(float), h->batch,
                           cudaMemcpyDeviceToDevice, h->stream);
+  return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
+}
+
+wbrzf_status wbrzf_sum_rate_f64(wbrzf* h, double* sum_rate_out) {
+  if (!h || !sum_rate_out) return WBRZF_ERR_INVALID_ARG;
+  const cudaError_t e = cudaMemcpyAsync(sum_rate_out, h->ws + h->wl.oRate64,
+                                        (size_t)h->batch * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, h->stream);
   return e == cudaSuccess ? WBRZF_OK : cuda_fail(e);
 }
 

@@ -368,3 +368,33 @@ def test_full_size_batched_full_length_at_bench_eta():
         for t in range(T):
             assert relerr(Ws_s[t][j], ref[t].W) < 2e-3, (t, b)
             assert abs(rates_s[t][j] - ref[t].sum_rate) < 1e-3, (t, b)
+
+
+@pytest.mark.parametrize("prec,engine,tol", [("c128", "simt", 1e-9), ("c128", "blocked", 1e-9),
+                                             ("c64", "tensor", 1e-3), ("c64", "blocked", 1e-3)])
+def test_sum_rate_in_fp64(prec, engine, tol):
+    """The per-instance sum-rate summed in FP64 (wbrzf_sum_rate_f64): within the engine's
+    sum-rate tolerance of the oracle, equal to the FP32 report after rounding, and in complex128
+    beyond FP32's resolution of it (the FP32 copy is off by up to half an ulp, 2^-24 R)."""
+    sc = channel.LeoScenario(n_x=16, n_y=8, K=16, disc_radius=50e3)
+    Hs = _traj(sc, 3, 4, seed=64)
+    rule = binding.RankRule(eta=0.9, k_init=2, p=4, r_max=8, reinverse_period=3, seed=6)
+    dt = torch.complex64 if prec == "c64" else torch.complex128
+    h = binding.WBRZF(3, sc.N, sc.K, sc.alpha, sc.sigma2, p_t=sc.p_t, rule=rule,
+                      precision=prec, workspace_for="blocked")
+    h.set_engine(engine)
+    refs = [run_oracle(Hs[:, b].numpy().astype(np.complex64).astype(np.complex128)
+                       if prec == "c64" else Hs[:, b].numpy(), sc.alpha, sc.sigma2, sc.p_t,
+                       rule, instance=b) for b in range(3)]
+    for t in range(4):
+        H = Hs[t].to(device="cuda", dtype=dt).contiguous()
+        h.full_inverse(H) if t == 0 else h.update(H)
+        r64 = h.sum_rate64().cpu().numpy()
+        r32 = h.sum_rate()[1].cpu().numpy()
+        assert r64.dtype == np.float64
+        np.testing.assert_array_equal(r64.astype(np.float32), r32)
+        for b in range(3):
+            assert abs(r64[b] - refs[b][t].sum_rate) < tol, (t, b, r64[b], refs[b][t].sum_rate)
+            if prec == "c128":
+                assert abs(r64[b] - refs[b][t].sum_rate) < 2.0 ** -30 * refs[b][t].sum_rate
+    h.close()
