@@ -53,7 +53,8 @@ typedef enum {
   WBRZF_ERR_WORKSPACE = 3,       /* workspace smaller than wbrzf_workspace_bytes()           */
   WBRZF_ERR_NUMERICAL = 4,       /* an instance could not be inverted (see step info)        */
   WBRZF_ERR_CUDA = 5,            /* a CUDA runtime call failed (see wbrzf_last_cuda_error)   */
-  WBRZF_ERR_UNSUPPORTED = 6      /* shape or precision outside what the library supports     */
+  WBRZF_ERR_UNSUPPORTED = 6,     /* shape or precision outside what the library supports     */
+  WBRZF_ERR_TIMEOUT = 7          /* a bounded wait expired in some instance (see step info)  */
 } wbrzf_status;
 
 typedef enum {
@@ -209,7 +210,8 @@ wbrzf_status wbrzf_sum_rate(wbrzf* h, float* sinr_out, float* sum_rate_out);
 wbrzf_status wbrzf_sum_rate_f64(wbrzf* h, double* sum_rate_out);
 
 /* Copy the last call's per-instance outcome for instances [0, count) into host memory.
- * Synchronises the stream.  Returns WBRZF_ERR_NUMERICAL if any of them has status != 0. */
+ * Synchronises the stream.  Returns WBRZF_ERR_TIMEOUT if any of them has the
+ * WBRZF_STATUS_TIMEOUT bit, else WBRZF_ERR_NUMERICAL if any has status != 0. */
 wbrzf_status wbrzf_step_info_get(wbrzf* h, wbrzf_step_info* host_out, int count);
 
 /* Copy the resident state (device, batch contiguous K x K row-major, the handle's complex

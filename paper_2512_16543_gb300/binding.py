@@ -22,7 +22,7 @@ ENGINES = {"auto": 0, "simt": 1, "tensor": 2, "blocked": 3, "blocked_fma": 4}
 BRANCH_NAMES = {0: "keep", 1: "woodbury", 2: "init", 3: "periodic", 4: "rank", 5: "full",
                 6: "fallback"}
 STATUS = {0: "ok", 1: "invalid argument", 2: "not initialized", 3: "workspace too small",
-          4: "numerical", 5: "cuda error", 6: "unsupported"}
+          4: "numerical", 5: "cuda error", 6: "unsupported", 7: "timeout"}
 
 
 class WbrzfError(RuntimeError):
@@ -332,7 +332,7 @@ class WBRZF:
     def step_info(self, raise_on_numerical: bool = False) -> list[dict]:
         arr = (StepInfoC * self.batch)()
         code = lib().wbrzf_step_info_get(self._h, arr, self.batch)
-        if code not in (0, 4) or (code == 4 and raise_on_numerical):
+        if code not in (0, 4, 7) or (code in (4, 7) and raise_on_numerical):
             _check(code, "wbrzf_step_info_get")
         return [{f: getattr(x, f) for f, _ in StepInfoC._fields_} for x in arr]
 

@@ -1076,6 +1076,62 @@ __global__ void __launch_bounds__(256) capinv_kernel(const Bufs<T> w, int gmask)
   }
 }
 
+// Gauss-Jordan with partial pivoting on [C | Z] as gauss_jordan_warp (C n x n in columns
+// 0 .. n-1, Z in columns zc .. zc + nz - 1 of CZ, ld ldcz, shared memory; pivots at most
+// piv_tol, or not finite, mark the system singular), by all kThreads threads of the CTA:
+// warp 0 finds each column's pivot, the CTA swaps the two rows, then each thread eliminates
+// whole columns (column c itself is not written, so no barrier separates reading it from the
+// updates).  Three barriers per pivot.  Returns the singular flag, the same in every thread;
+// called by all threads.
+template <class T>
+__device__ bool gauss_jordan_cta(cx<T>* CZ, int ldcz, int n, int zc, int nz, T piv_tol) {
+  __shared__ int piv_s, sing_s;
+  const int tid = threadIdx.x, ncol = n + nz;
+  if (tid == 0) sing_s = 0;
+  __syncthreads();
+  for (int c = 0; c < n; ++c) {
+    if (tid < 32) {
+      T v = T(-1);
+      int pr = n;
+      for (int i = c + tid; i < n; i += 32) {
+        const T x = cabs2(CZ[i * ldcz + c]);
+        if (x > v) { v = x; pr = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int op = __shfl_xor_sync(0xffffffffu, pr, o);
+        if (ov > v || (ov == v && op < pr)) { v = ov; pr = op; }
+      }
+      if (tid == 0) {
+        if (!(sqrt(v) > piv_tol) || !isfinite(v)) sing_s = 1;
+        piv_s = pr >= n ? c : pr;               // no usable entry: keep the row (singular)
+      }
+    }
+    __syncthreads();
+    const int pr = piv_s;
+    if (pr != c) {
+      for (int j = c + tid; j < ncol; j += kThreads) {
+        const int col = j < n ? j : zc + (j - n);
+        const cx<T> t0 = CZ[c * ldcz + col];
+        CZ[c * ldcz + col] = CZ[pr * ldcz + col];
+        CZ[pr * ldcz + col] = t0;
+      }
+      __syncthreads();
+    }
+    const cx<T> ip = crecip(CZ[c * ldcz + c]);
+    for (int j = c + 1 + tid; j < ncol; j += kThreads) {
+      const int col = j < n ? j : zc + (j - n);
+      const cx<T> rcj = cmul(CZ[c * ldcz + col], ip);
+      for (int i = 0; i < n; ++i)
+        if (i != c) CZ[i * ldcz + col] = csub(CZ[i * ldcz + col], cmul(CZ[i * ldcz + c], rcj));
+      CZ[c * ldcz + col] = rcj;
+    }
+    __syncthreads();
+  }
+  return sing_s != 0;
+}
+
 // X <- X - T W for X (K x K, global memory), T (K x r, ld ldt) and W (r x K, ld ldw) in shared
 // memory: thread t updates column j = t mod K of X on rows g, g + G, ... (g = t / K,
 // G = kThreads / K), holding W's column j in registers (r <= NR).
@@ -1229,15 +1285,19 @@ __global__ void __launch_bounds__(256, 2) woodbury_fused_kernel(const StepArgs<T
     }
     __syncthreads();
   } else {
-  if (tid < 32) {
-    T cmax = 0;
-    for (int o = tid; o < r * r; o += 32) {
-      const int c = o / r, e = o - c * r;
-      cmax = fmax(cmax, sqrt(cabs2(CZ[c * ldz + e])));
+  {
+    __shared__ T tol_s;
+    if (tid < 32) {
+      T cmax = 0;
+      for (int o = tid; o < r * r; o += 32) {
+        const int c = o / r, e = o - c * r;
+        cmax = fmax(cmax, sqrt(cabs2(CZ[c * ldz + e])));
+      }
+      for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+      if (tid == 0) tol_s = cmax * ((sizeof(T) == 4) ? T(1e-6) : T(1e-14));
     }
-    for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-    const T tol = cmax * ((sizeof(T) == 4) ? T(1e-6) : T(1e-14));
-    const bool sg = gauss_jordan_warp<T>(CZ, ldz, r, RF, K, tol);
+    __syncthreads();
+    const bool sg = gauss_jordan_cta<T>(CZ, ldz, r, RF, K, tol_s);
     if (tid == 0) singular = sg ? 1 : 0;
   }
   __syncthreads();

@@ -589,9 +589,12 @@ wbrzf_status wbrzf_step_info_get(wbrzf* h, wbrzf_step_info* host_out, int count)
                                   h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e);
-  for (int b = 0; b < count; ++b)
-    if (host_out[b].status != WBRZF_STATUS_OK) return WBRZF_ERR_NUMERICAL;
-  return WBRZF_OK;
+  wbrzf_status st = WBRZF_OK;
+  for (int b = 0; b < count; ++b) {
+    if (host_out[b].status & WBRZF_STATUS_TIMEOUT) return WBRZF_ERR_TIMEOUT;
+    if (host_out[b].status != WBRZF_STATUS_OK) st = WBRZF_ERR_NUMERICAL;
+  }
+  return st;
 }
 
 wbrzf_status wbrzf_get_state(wbrzf* h, void* G_out, void* X_out) {
@@ -1040,6 +1043,7 @@ const char* wbrzf_status_string(wbrzf_status s) {
     case WBRZF_ERR_NUMERICAL: return "an instance could not be inverted";
     case WBRZF_ERR_CUDA: return "CUDA runtime error";
     case WBRZF_ERR_UNSUPPORTED: return "unsupported shape or precision";
+    case WBRZF_ERR_TIMEOUT: return "a bounded wait expired";
   }
   return "unknown status";
 }

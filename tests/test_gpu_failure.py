@@ -51,3 +51,32 @@ def test_bounded_wait_reports_timeout_and_the_context_stays_usable():
     assert all(i["status"] == 0 for i in h.step_info())
     assert bool(torch.isfinite(torch.view_as_real(W)).all())
     h.close()
+
+
+def test_step_info_reports_a_timed_out_instance_with_its_own_code():
+    """A TIMEOUT status bit in any instance's step info makes wbrzf_step_info_get return
+    WBRZF_ERR_TIMEOUT (7), ahead of WBRZF_ERR_NUMERICAL (4) for other non-zero statuses.  The
+    bit is planted on the host side of the contract: written into the step-info record of the
+    handle's workspace (the common layout: G, X, then the 32-byte records, each region
+    256-byte aligned; status at byte 28), not produced by a GPU wait."""
+    sc = channel.scenario_batched_256x32()
+    params = channel.draw_trajectories(sc, 3, seed=6)
+    h = binding.WBRZF(3, sc.N, sc.K, sc.alpha, sc.sigma2, p_t=sc.p_t)
+    h.full_inverse(channel.channel_at(params, 0, device="cuda", dtype=torch.complex64))
+    assert [i["status"] for i in h.step_info()] == [0, 0, 0]
+    kk = 3 * sc.K * sc.K * 8
+    al = lambda x: (x + 255) // 256 * 256
+    o_info = al(al(kk) + kk)
+    status = h.workspace[o_info:o_info + 3 * 32].view(3, 32)[:, 28:32]
+    status[1].copy_(torch.tensor([4, 0, 0, 0], dtype=torch.uint8))        # TIMEOUT
+    status[2].copy_(torch.tensor([1, 0, 0, 0], dtype=torch.uint8))        # NOT_PD
+    info = h.step_info()
+    assert [i["status"] for i in info] == [0, 4, 1]
+    with pytest.raises(binding.WbrzfError) as e:
+        h.step_info(raise_on_numerical=True)
+    assert e.value.code == 7
+    status[1].zero_()
+    with pytest.raises(binding.WbrzfError) as e:
+        h.step_info(raise_on_numerical=True)
+    assert e.value.code == 4
+    h.close()
