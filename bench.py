@@ -424,6 +424,7 @@ def main_uneven(args):
     full, fhs, fengines = make_group("full", 0.9)
     ms_full, _, rates_full = timed(full, fhs, collect=True)
     ftunings = [h.blocked_tuning for h in fhs]
+    fshortcuts = [h.energy_shortcut for h in fhs]
     full.close()
     for h in fhs:
         h.close()
@@ -448,6 +449,7 @@ def main_uneven(args):
         chosen = grid[-1]
     ms_wb, launches, engines, grp, hs = runs[chosen]
     tunings = [h.blocked_tuning for h in hs]          # launch shapes the autotuner kept
+    shortcuts = [h.energy_shortcut for h in hs]
 
     # ---- error against FP64: two sampled instances per class, the same steps run on the
     # library's complex128 path (FP64 FMA, parity-tested against the oracle to 1e-10)
@@ -483,7 +485,7 @@ def main_uneven(args):
 
     # ---- each class alone, both methods on their autotuned engines, steps replayed from a
     # CUDA graph (the blocked engine's optional blocks are IF nodes), L2 flushed between steps
-    def class_alone(ci, method, engine, eta, tuning):
+    def class_alone(ci, method, engine, eta, tuning, shortcut):
         c = pop[ci]
         h = binding.WBRZF(c.batch, c.scenario.N, c.scenario.K, c.alpha, c.sigma2,
                           p_t=c.scenario.p_t, rule=binding.RankRule(**uneven_rule_kw(
@@ -492,6 +494,7 @@ def main_uneven(args):
         h.set_instance_ids([int(i) for i in c.index])
         h.set_engine(engine)
         h.set_blocked_tuning(*tuning)
+        h.set_energy_shortcut(shortcut)
         h.set_graph(True)
         Hin, Wc = Hb[ci], Ws[ci]
         Hin.copy_(Hs[ci][0])
@@ -519,8 +522,8 @@ def main_uneven(args):
 
     per_class = []
     for ci, c in enumerate(pop):
-        t_wb, st = class_alone(ci, "wb", engines[ci], chosen, tunings[ci])
-        t_full, _ = class_alone(ci, "full", fengines[ci], 0.9, ftunings[ci])
+        t_wb, st = class_alone(ci, "wb", engines[ci], chosen, tunings[ci], shortcuts[ci])
+        t_full, _ = class_alone(ci, "full", fengines[ci], 0.9, ftunings[ci], fshortcuts[ci])
         per_class.append({"N": c.scenario.N, "K": c.scenario.K, "batch": c.batch,
                           "wb_engine": engines[ci], "full_engine": fengines[ci],
                           "wb_last_step": st,
@@ -616,9 +619,11 @@ def main_uneven(args):
                        "eta_grid_gaps_bits": gaps, "rate_gap_bound_bits": RATE_GAP_BOUND,
                        "classes": [{"N": c.scenario.N, "K": c.scenario.K, "batch": c.batch,
                                     "engine": e, "tile_cap": tu[0], "jacobi_cta_min": tu[1],
+                                    "energy_shortcut": sc,
                                     "full_engine": fe, "full_tile_cap": ftu[0]}
-                                   for c, e, tu, fe, ftu in zip(pop, engines, tunings,
-                                                                fengines, ftunings)],
+                                   for c, e, tu, sc, fe, ftu in zip(pop, engines, tunings,
+                                                                    shortcuts, fengines,
+                                                                    ftunings)],
                        "l2": "flushed (512 MB write) between timed snapshots",
                        "parallelism": f"instances sharded over {world} GPU(s)"},
             "p50_ms": float(np.percentile(ms_wb, 50)), "p99_ms": float(np.percentile(ms_wb, 99)),

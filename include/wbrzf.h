@@ -333,6 +333,19 @@ wbrzf_status wbrzf_set_fp64_small_solves(wbrzf* h, int enable);
  * Returns WBRZF_ERR_INVALID_ARG for other values.
  */
 wbrzf_status wbrzf_set_blocked_tuning(wbrzf* h, int tile_cap, int jacobi_cta_min);
+
+/*
+ * Tensor engine launch choice (not part of the paper's method): with enable != 0 the kernel
+ * takes Algorithm 1's energy test without the eigensolver -- on an iteration before the last,
+ * when ||B||_F^2 (the sum of all d values sigma_hat^2) is short of the target by more than
+ * 1e-4 of it, the iteration fails without the Jacobi rotations, as the full test would.  It
+ * saves the eigensolver where several iterations are common and costs a few percent where
+ * one decides (the kernel runs at its register cap), so it is off by default and
+ * wbrzf_group_autotune tries both.  The blocked and FMA engines always take the test.
+ * wbrzf_get_energy_shortcut returns the setting (-1 for a null handle).
+ */
+wbrzf_status wbrzf_set_energy_shortcut(wbrzf* h, int enable);
+int wbrzf_get_energy_shortcut(const wbrzf* h);
 wbrzf_status wbrzf_get_blocked_tuning(const wbrzf* h, int* tile_cap, int* jacobi_cta_min);
 
 /*
@@ -361,8 +374,9 @@ wbrzf_status wbrzf_set_graph(wbrzf* h, int enable);
  * wbrzf_group_autotune picks each member's engine by measurement: for every engine in
  * engine_mask (bit e = WBRZF_ENGINE_e) that the member accepts -- and for the blocked
  * engines every launch shape of the grid {tile cap 64, 32} x {CTA eigensolver from sketch
- * width 12, one-warp eigensolver} (wbrzf_set_blocked_tuning) -- a full inverse on H0[i] then
- * `reps` updates on H1[i] are run and the fastest update (CUDA events) wins; the member keeps
+ * width 12, one-warp eigensolver} (wbrzf_set_blocked_tuning), for the tensor engine the energy
+ * shortcut off and on (wbrzf_set_energy_shortcut) -- `reps` times a full inverse on H0[i]
+ * followed by an update on H1[i] are run and the fastest update (CUDA events) wins; the member keeps
  * the winning engine and launch shape (wbrzf_get_blocked_tuning reads the latter).  It
  * finishes with a full inverse on H0[i] with the choice (so the state is that of a fresh
  * full inverse), synchronises, and returns WBRZF_ERR_UNSUPPORTED if a member accepts none of

@@ -103,6 +103,10 @@ def lib() -> ctypes.CDLL:
     L.wbrzf_set_fp64_small_solves.argtypes = [vp, i32]
     L.wbrzf_sum_rate_f64.restype = i32
     L.wbrzf_sum_rate_f64.argtypes = [vp, vp]
+    L.wbrzf_set_energy_shortcut.restype = i32
+    L.wbrzf_set_energy_shortcut.argtypes = [vp, i32]
+    L.wbrzf_get_energy_shortcut.restype = i32
+    L.wbrzf_get_energy_shortcut.argtypes = [vp]
     L.wbrzf_set_blocked_tuning.restype = i32
     L.wbrzf_set_blocked_tuning.argtypes = [vp, i32, i32]
     L.wbrzf_get_blocked_tuning.restype = i32
@@ -275,6 +279,15 @@ class WBRZF:
         CTA-wide eigensolver."""
         _check(lib().wbrzf_set_blocked_tuning(self._h, int(tile_cap), int(jacobi_cta_min)),
                "wbrzf_set_blocked_tuning")
+
+    def set_energy_shortcut(self, enable: bool = True) -> None:
+        """Tensor engine: Algorithm 1's energy test without the eigensolver."""
+        _check(lib().wbrzf_set_energy_shortcut(self._h, int(enable)),
+               "wbrzf_set_energy_shortcut")
+
+    @property
+    def energy_shortcut(self) -> bool:
+        return lib().wbrzf_get_energy_shortcut(self._h) == 1
 
     @property
     def blocked_tuning(self) -> tuple[int, int]:

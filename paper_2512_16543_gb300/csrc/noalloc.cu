@@ -141,6 +141,7 @@ wbrzf_status run_noalloc(int batch, int N, int K, const void* H, double alpha, d
   a.small64 = 0;
   a.tile_cap = 64;
   a.jacobi_cta_min = 12;
+  a.energy_shortcut = 0;
   a.eta = 1.0;
   a.k_init = 1;
   a.p = 0;

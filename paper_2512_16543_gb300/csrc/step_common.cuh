@@ -59,6 +59,7 @@ struct StepArgs {
   // batched complex GEMMs (64 or 32), and the sketch width from which the fused kernel's
   // eigensolver runs on the whole CTA instead of one warp
   int tile_cap, jacobi_cta_min;
+  int energy_shortcut;     // tensor kernel: the energy test without the eigensolver
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

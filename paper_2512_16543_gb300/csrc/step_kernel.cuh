@@ -136,6 +136,17 @@ __device__ T block_sum(T v, T* red) {
   return out;
 }
 
+// Each warp's sum of |x_o|^2 over the entries o = tid, tid + kThreads, ... < n into red[warp]
+// (no barrier; kept out of line so that the register allocation of its callers -- the
+// tensor kernel runs at its 64-register cap -- is not disturbed).
+template <class T>
+__device__ __noinline__ void warp_sums_of_squares(const cx<T>* x, int n, T* red) {
+  T part = 0;
+  for (int o = threadIdx.x; o < n; o += kThreads) part += cabs2(x[o]);
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+}
+
 // ------------------------------------------------------------------ H chunk staging
 // Stage columns [n0, n0 + nc) of H (row-major K x N) transposed into buf[n][k] (row stride KP).
 template <class T>
@@ -860,8 +871,11 @@ __device__ void cholqr_pass_smem(cx<T>* Q, int ldq, int K, int d, cx<T>* Gy, int
 // step, the Woodbury update or direct inverse, the state write-back, the power scale and the
 // SINR / sum-rate.  Leaves X in w.X and returns the precoder scale s.
 // LARGEK: the instantiation for K > 32 (svd(B) by the two-sided Jacobi on E = B B^H); the
-// other one serves K <= 32 (one-sided Jacobi on B's rows).
-template <class T, bool LARGEK>
+// other one serves K <= 32 (one-sided Jacobi on B's rows).  SHORTCUT: the energy test without
+// the eigensolver on the iterations before the last (in the tensor kernel, which runs at its
+// register cap, the test's code costs a few percent where one iteration decides, so it is a
+// launch choice there).
+template <class T, bool LARGEK, bool SHORTCUT = true>
 __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
   // On entry for MODE_UPDATE, w.D holds G_{t-1} and w.X holds X_{t-1}: the kernels copy them
   // from the resident state with cp.async (prefetch_state) while the Gram matrix is formed.
@@ -973,7 +987,23 @@ __device__ T core_phases(const StepArgs<T>& a, const Work<T>& w, const int b) {
       }
       // 3d. projection B = Q^H dG  (d x K)
       mm<T, true, false, MM_SET>(d, K, K, Q, dmax, D, K, Bm, K);
+      // The d values sigma_hat^2 sum to ||B||_F^2 (rotations keep it): short of the energy
+      // target by more than the rotations' rounding, no r <= d meets eq. 14, and an iteration
+      // that is not the last fails here without the eigensolver.  Each thread adds |B_ij|^2
+      // over the entries mm gave it (its own writes: no barrier), warps into red[w] ahead of
+      // the barrier that ends the projection; red is next written behind later barriers.
+      const bool early = SHORTCUT && it + 1 < a.i_max;
+      if (early) warp_sums_of_squares<T>(Bm, d * K, red);
       __syncthreads();
+      if (early) {
+        T trB = 0;
+        for (int q = 0; q < kThreads / 32; ++q) trB += red[q];
+        if ((double)trB < a.eta * ldexp((double)dgs, -2 * dg_exp) * (1.0 - 1e-4)) {
+          iters = it + 1;
+          k0 *= 2;
+          continue;
+        }
+      }
       // 3e. svd(B).  Converged when no pair of rows of B has |b_p b_q^H|^2 above tol2
       // tr(B B^H)^2: FP32 1e-8 (each off-diagonal entry of E = B B^H then at most 1e-4 of its
       // trace, which leaves the eigenvalues -- the energy rule's input -- exact to second

@@ -6,14 +6,14 @@ namespace wbk {
 cudaError_t launch_step_tc(const StepArgs<float>& a, size_t smem, cudaStream_t s) {
   // Both attributes are per device: set them on every launch (cheap host calls), so that a
   // launch on another device than the last one gets them too.
-  cudaError_t e = cudaFuncSetAttribute(wbrzf_step_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const auto kern = a.energy_shortcut ? wbrzf_step_tc_kernel<true> : wbrzf_step_tc_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   // all of the SM's shared memory for shared-memory use, so four CTAs fit per SM
-  e = cudaFuncSetAttribute(wbrzf_step_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           100);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
-  wbrzf_step_tc_kernel<<<a.batch, kThreads, smem, s>>>(a);
+  kern<<<a.batch, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

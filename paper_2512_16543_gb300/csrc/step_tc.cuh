@@ -31,6 +31,7 @@
 namespace wbk {
 
 // ---------------------------------------------------------------- the kernel
+template <bool SHORTCUT>
 __global__ void __launch_bounds__(kThreads, 4) wbrzf_step_tc_kernel(const StepArgs<float> a) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw_u = smem_u32(smem_raw);
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 4) wbrzf_step_tc_kernel(const StepAr
   cp_async_wait<0>();
   __syncthreads();
   const Work<float> w = carve_work<float>(uni, K, a.dmax, a.rcap, G, X, Dm);
-  const float s = core_phases<float, false>(a, w, b);   // K <= 32
+  const float s = core_phases<float, false, SHORTCUT>(a, w, b);   // K <= 32
   __syncthreads();
 
   // ------------------------------------------------------------ 7. W = s H^H X on tensor cores

@@ -191,6 +191,7 @@ struct wbrzf {
   int small64;           // wbrzf_set_fp64_small_solves
   int tile_cap;          // wbrzf_set_blocked_tuning: largest batched-GEMM tile edge (64, 32)
   int jacobi_cta_min;    // wbrzf_set_blocked_tuning: first sketch width of the CTA eigensolver
+  int energy_shortcut;   // wbrzf_set_energy_shortcut (tensor engine)
   cudaStream_t cstream;  // blocked engine: records the bodies of CUDA-graph IF nodes while a
                          // step is captured (its own captures only; never runs work)
 };
@@ -238,6 +239,7 @@ StepArgs<T> make_args(const wbrzf* h, const void* H, void* W, int mode,
   a.small64 = h->small64;
   a.tile_cap = h->tile_cap;
   a.jacobi_cta_min = h->jacobi_cta_min;
+  a.energy_shortcut = h->energy_shortcut;
   return a;
 }
 
@@ -483,6 +485,7 @@ wbrzf_status wbrzf_create(int batch, int N, int K, const double* alpha, const do
   h->refine = 0;
   h->tile_cap = kDefaultTileCap;
   h->jacobi_cta_min = kDefaultJacobiCtaMin;
+  h->energy_shortcut = 0;
   h->cstream = nullptr;
   {
     const size_t tc = tc_smem_bytes(K, r.dmax, r.rcap);
@@ -761,6 +764,15 @@ wbrzf_status wbrzf_set_blocked_tuning(wbrzf* h, int tile_cap, int jacobi_cta_min
   return WBRZF_OK;
 }
 
+wbrzf_status wbrzf_set_energy_shortcut(wbrzf* h, int enable) {
+  if (!h) return WBRZF_ERR_INVALID_ARG;
+  h->energy_shortcut = enable ? 1 : 0;
+  invalidate_graph(h);
+  return WBRZF_OK;
+}
+
+int wbrzf_get_energy_shortcut(const wbrzf* h) { return h ? h->energy_shortcut : -1; }
+
 wbrzf_status wbrzf_get_blocked_tuning(const wbrzf* h, int* tile_cap, int* jacobi_cta_min) {
   if (!h || !tile_cap || !jacobi_cta_min) return WBRZF_ERR_INVALID_ARG;
   *tile_cap = h->tile_cap;
@@ -963,22 +975,30 @@ wbrzf_status wbrzf_group_autotune(wbrzf_group* g, const void* const* H0, const v
   for (size_t i = 0; i < g->m.size(); ++i) {
     wbrzf* h = g->m[i];
     const int own = h->engine, own_cap = h->tile_cap, own_jmin = h->jacobi_cta_min;
-    int best = -1, best_cap = own_cap, best_jmin = own_jmin;
+    const int own_sc = h->energy_shortcut;
+    int best = -1, best_cap = own_cap, best_jmin = own_jmin, best_sc = own_sc;
     float best_ms = 0.f;
     for (int ci = 0; ci < (int)(sizeof(cand) / sizeof(cand[0])) * 4; ++ci) {
       const int c = cand[ci / 4], ti = ci % 4;
       const bool blocked = c == WBRZF_ENGINE_BLOCKED || c == WBRZF_ENGINE_BLOCKED_FMA;
-      if (!blocked && ti > 0) continue;
+      const bool tensor = c == WBRZF_ENGINE_TENSOR;
+      if (!blocked && ti > (tensor ? 1 : 0)) continue;
       if (!((engine_mask >> c) & 1u)) continue;
       if (wbrzf_set_engine(h, c) != WBRZF_OK) continue;
       h->tile_cap = blocked ? tune[ti][0] : own_cap;
       h->jacobi_cta_min = blocked ? tune[ti][1] : own_jmin;
+      h->energy_shortcut = tensor ? ti : own_sc;
       h->t = 0;
       wbrzf_status st = run_step(h, H0[i], W[i], group_mode(h, true), nullptr);
       if (st != WBRZF_OK) continue;
       h->initialized = true;
       float tmin = -1.f;
       for (int r = 0; r < reps && st == WBRZF_OK; ++r) {
+        if (r > 0) {       // back to the state after H0, so that every rep is the H0 -> H1
+          h->t = 0;        // update (a second update on H1 would see dG = 0 and keep X)
+          st = run_step(h, H0[i], W[i], group_mode(h, true), nullptr);
+          if (st != WBRZF_OK) break;
+        }
         cudaEventRecord(g->t0, h->stream);
         st = run_step(h, H1[i], W[i], group_mode(h, false), nullptr);
         cudaEventRecord(g->t1, h->stream);
@@ -993,11 +1013,13 @@ wbrzf_status wbrzf_group_autotune(wbrzf_group* g, const void* const* H0, const v
         best_ms = tmin;
         best_cap = h->tile_cap;
         best_jmin = h->jacobi_cta_min;
+        best_sc = h->energy_shortcut;
       }
     }
     wbrzf_set_engine(h, best >= 0 ? best : own);
     h->tile_cap = best >= 0 ? best_cap : own_cap;
     h->jacobi_cta_min = best >= 0 ? best_jmin : own_jmin;
+    h->energy_shortcut = best >= 0 ? best_sc : own_sc;
     if (best < 0) return WBRZF_ERR_UNSUPPORTED;
     g->engine[i] = best;
     h->t = 0;

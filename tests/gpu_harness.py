@@ -25,7 +25,7 @@ def oracle_rule(rule: binding.RankRule) -> om.RankRule:
 
 def run_gpu(Hs: torch.Tensor, alpha, sigma2, p_t, rule: binding.RankRule, *, precision="c64",
             method="wb", ids=None, trace=False, keep_state=True, device="cuda", engine="auto",
-            fp64_small=False):
+            fp64_small=False, energy_shortcut=False):
     """Hs: [T, B, K, N] complex tensor (any device).  Returns a list of per-step dicts.
     fp64_small: the blocked engine's FP64 small-solve mode."""
     T, B, K, N = Hs.shape
@@ -37,6 +37,8 @@ def run_gpu(Hs: torch.Tensor, alpha, sigma2, p_t, rule: binding.RankRule, *, pre
         h.set_engine(engine)
     if fp64_small:
         h.set_fp64_small_solves(True)
+    if energy_shortcut:
+        h.set_energy_shortcut(True)
     if ids is not None:
         h.set_instance_ids(ids)
     if trace:

@@ -398,3 +398,20 @@ def test_sum_rate_in_fp64(prec, engine, tol):
             if prec == "c128":
                 assert abs(r64[b] - refs[b][t].sum_rate) < 2.0 ** -30 * refs[b][t].sum_rate
     h.close()
+
+
+@pytest.mark.parametrize("engine,shortcut", [("tensor", False), ("tensor", True),
+                                             ("simt", True)])
+def test_energy_shortcut_keeps_parity(engine, shortcut):
+    """A wide disc and eta = 0.9 at K = 32 make Algorithm 1 iterate (d = 10 .. 24): with the
+    energy test taken without the eigensolver (tensor kernel's launch choice; always in the
+    FMA kernel) or with the full test, the branches, ranks and results meet the oracle."""
+    sc = channel.LeoScenario(n_x=16, n_y=16, K=32, disc_radius=200e3)
+    Hs = _traj(sc, 3, 5, seed=320)
+    rule = binding.RankRule(eta=0.9, k_init=2, p=8, r_max=32, reinverse_period=0, seed=7)
+    gpu, meta = run_gpu(Hs, sc.alpha, sc.sigma2, sc.p_t, rule, precision="c64", engine=engine,
+                        energy_shortcut=shortcut)
+    assert meta["engine"] == engine
+    assert _check(gpu, Hs, sc, rule, "c64", engine=engine) <= 2
+    assert max(g["info"][b]["iters"] for g in gpu[1:] for b in range(3)) >= 3
+    assert any(g["info"][b]["branch"] == 1 for g in gpu[1:] for b in range(3))
