@@ -34,15 +34,17 @@ constexpr int kDirectMask = (1 << WBRZF_BRANCH_INIT) | (1 << WBRZF_BRANCH_PERIOD
 
 constexpr int kPending = 15;   // branch code while the low-rank step has not decided
 constexpr int kInactive = 14;  // branch code of an instance that sits this step out
-constexpr int kWoodburyWide = 13;    // rank above the fused Woodbury kernel's cap
+// a Woodbury step whose rank exceeds the fused kernel's cap: the batched products take it
+// (reported as Woodbury)
+constexpr int kWoodburyWide = 13;
 // Stream accumulators per thread (dr_product / ad_product) of the fused Woodbury step and of the
 // fused Algorithm 1 kernel; each bounds the columns a stream covers to MAXA kThreads / K.
 constexpr int kWoodburyMaxA = 12;
 constexpr int kWoodburyFusedTop = 24;      // largest rank of the fused Woodbury kernel (FP32)
 // Sketch widths up to this take the register CholQR in the fused kernel as well
 constexpr int kCqRegsWide = 16;
-template <class T> constexpr int fused_max_a() { return sizeof(T) == 4 ? 12 : 6; }  // Woodbury step whose rank exceeds the fused kernel's cap:
-                                   // the batched products take it (reported as Woodbury)
+// Stream accumulators per thread of the fused Algorithm 1 kernel's sketch and projection
+template <class T> constexpr int fused_max_a() { return sizeof(T) == 4 ? 12 : 6; }
 constexpr int kLiveMask = ~(1 << kInactive);
 
 template <class T>
@@ -752,9 +754,11 @@ __device__ void jacobi_eig_cta(cx<T>* E, cx<T>* U, int ld, int d, T tol2, int ma
 // Fused Algorithm 1 iterations (K <= 128, the leading nf iterations, whose sketch widths fit
 // the shared-memory layout of width df): one CTA of kThreads threads per instance runs them
 // with the one-CTA engines' device code -- Omega from the same Philox counters, Y = 2^-e dG
-// Omega and B = Q^H 2^-e dG with dG streamed from global memory in 16-wide chunks, CholQR2,
-// the one-sided Jacobi on B's rows (B <- U^H B; U accumulated) and the energy rule -- in
-// place of a dozen batched launches per iteration.  It leaves what the per-step kernels leave
+// Omega and B = Q^H 2^-e dG with dG streamed from global memory in 8-wide chunks, CholQR2,
+// the energy test without the eigensolver when ||B||_F^2 falls short, else the eigensolver
+// (one-sided Jacobi on B's rows for K <= 32; E = B B^H by one warp, or by the CTA from sketch
+// width jacobi_cta_min, for K > 32) and the energy rule -- in place of a dozen batched
+// launches per iteration.  It leaves what the per-step kernels leave
 // for the Woodbury stage: the control words, perm, lam, the trace, the unrotated B, and for a
 // Woodbury instance Q and U_r.  An instance still short of its target after the nf
 // iterations stays active and continues on the per-step kernels.
