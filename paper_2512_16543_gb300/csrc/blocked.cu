@@ -195,6 +195,125 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) cgemm_kernel(const GemmAr
   }
 }
 
+// cgemm_kernel with the reduction over k split among kSplitK groups of (BM / 4) (BN / 4)
+// threads in one CTA: for products with few output tiles and a long reduction (the d x d
+// Gram and E = B B^H of one large array's Algorithm 1, its sketch and projection), where the
+// plain kernel would run a handful of CTAs through a chain of k-chunks.  Group g takes the
+// 16-deep k-chunks c with c mod kSplitK = g in ascending order; the groups' partial tiles are
+// then added in the order 0, 1, 2, 3 through shared memory.  The order of every output's sum
+// depends only on k, so the tile shape still changes no result.  Dynamic shared memory:
+// cgemm_split_smem.
+constexpr int kSplitK = 4;
+constexpr int kSplitKMaxTiles = 4;     // at most this many output tiles (at 64 x 64) per instance
+constexpr int kSplitKMinK = 256;       // and a reduction at least this long
+template <class T>
+constexpr size_t cgemm_split_smem(int BM, int BN) {
+  return (size_t)kSplitK * 16 * (BM + 1 + BN + 1) * sizeof(cx<T>);
+}
+template <class T, int BM, int BN>
+__global__ void __launch_bounds__((BM / 4) * (BN / 4) * kSplitK)
+cgemm_split_kernel(const GemmArgs<T> g) {
+  constexpr int NT = (BM / 4) * (BN / 4), TX = BN / 4;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int b = blockIdx.z;
+  if (!gate_ok(g.ctl, b, g.gidx, g.gmask)) return;
+  const int grp = threadIdx.x / NT, tid = threadIdx.x - grp * NT;
+  cx<T>* const As = reinterpret_cast<cx<T>*>(smraw) + (size_t)grp * 16 * (BM + 1 + BN + 1);
+  cx<T>* const Bs = As + 16 * (BM + 1);
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int ty = tid / TX, tx = tid % TX;
+  const cx<T>* A = g.A + (size_t)b * g.sA;
+  const cx<T>* B = g.B + (size_t)b * g.sB;
+  int mlive = g.m_live, nlive = g.n_live, klive = g.k_live;
+  if (g.lm >= 0) mlive = min(mlive, g.ctl[8 * b + g.lm]);
+  if (g.ln >= 0) nlive = min(nlive, g.ctl[8 * b + g.ln]);
+  if (g.lk >= 0) klive = min(klive, g.ctl[8 * b + g.lk]);
+  const int kend = (m0 >= mlive || n0 >= nlive) ? 0 : min(g.k, klive);
+  cx<T> acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = cmk<T>(0, 0);
+  // every group runs the same number of rounds (barriers are CTA-wide); a group whose chunk
+  // lies beyond kend loads zeros
+  const int nchunk = (kend + 15) / 16, rounds = (nchunk + kSplitK - 1) / kSplitK;
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int k0 = (rd * kSplitK + grp) * 16;
+    for (int e = tid; e < 16 * BM; e += NT) {
+      int r, kk;
+      if (g.opA == 0) { r = e >> 4; kk = e & 15; } else { kk = e / BM; r = e % BM; }
+      const int gi = m0 + r, gk = k0 + kk;
+      cx<T> v = cmk<T>(0, 0);
+      if (gi < g.m && gk < kend) {
+        v = (g.opA == 0) ? A[(size_t)gi * g.lda + gk] : cconj(A[(size_t)gk * g.lda + gi]);
+        if (g.dshift != nullptr && gi == gk) v.re -= g.dshift[b];
+      }
+      As[kk * (BM + 1) + r] = v;
+    }
+    for (int e = tid; e < 16 * BN; e += NT) {
+      int c, kk;
+      if (g.opB == 0) { kk = e / BN; c = e % BN; } else { c = e >> 4; kk = e & 15; }
+      const int gj = n0 + c, gk = k0 + kk;
+      cx<T> v = cmk<T>(0, 0);
+      if (gj < g.n && gk < kend)
+        v = (g.opB == 0) ? B[(size_t)gk * g.ldb + gj] : cconj(B[(size_t)gj * g.ldb + gk]);
+      Bs[kk * (BN + 1) + c] = v;
+    }
+    __syncthreads();
+    if (k0 < kend) {
+#pragma unroll 4
+      for (int kk = 0; kk < 16; ++kk) {
+        cx<T> av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk * (BM + 1) + ty + (BM / 4) * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk * (BN + 1) + tx + (BN / 4) * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cfma(acc[i][j], av[i], bv[j]);
+      }
+    }
+    __syncthreads();
+  }
+  // groups 1, 2, 3 hand their partial tiles to group 0 in turn (BM x BN buffer over the
+  // operand tiles, which are dead now)
+  cx<T>* const P = reinterpret_cast<cx<T>*>(smraw);
+  for (int q = 1; q < kSplitK; ++q) {
+    if (grp == q) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) P[(ty + (BM / 4) * i) * BN + tx + (BN / 4) * j] = acc[i][j];
+    }
+    __syncthreads();
+    if (grp == 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          acc[i][j] = cadd(acc[i][j], P[(ty + (BM / 4) * i) * BN + tx + (BN / 4) * j]);
+    }
+    __syncthreads();
+  }
+  if (grp != 0) return;
+  const T al = g.scale ? g.alpha * g.scale[b] : g.alpha;
+  cx<T>* C = g.C + (size_t)b * g.sC;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = m0 + ty + (BM / 4) * i;
+    if (gi >= g.m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = n0 + tx + (BN / 4) * j;
+      if (gj >= g.n) continue;
+      cx<T> v = cscale(acc[i][j], al);
+      if (g.beta != T(0)) v = cadd(v, cscale(C[(size_t)gi * g.ldc + gj], g.beta));
+      C[(size_t)gi * g.ldc + gj] = v;
+    }
+  }
+}
+
 // The tile cap of the step being enqueued on this host thread (set by run_blocked from the
 // handle's tuning; the tile shape changes no result: each output's k-sum keeps its order).
 thread_local int t_tile_cap = 64;
@@ -202,6 +321,19 @@ thread_local int t_tile_cap = 64;
 template <class T, int BM, int BN>
 cudaError_t launch_cgemm(const GemmArgs<T>& g, int batch, cudaStream_t s) {
   dim3 grid((g.n + BN - 1) / BN, (g.m + BM - 1) / BM, batch);
+  // few output tiles per instance and a long reduction: split k inside the CTA.  The choice
+  // depends on the product's shape only (tiles counted at 64 x 64), not on the tile shape or
+  // the batch, so an instance's bits do not depend on either.
+  // (complex64 only: the complex128 64 x 64 variant, 1024 threads at 64 registers, spills)
+  const int tiles64 = ((g.m + 63) / 64) * ((g.n + 63) / 64);
+  if (sizeof(T) == 4 && tiles64 <= kSplitKMaxTiles && g.k >= kSplitKMinK) {
+    const size_t smem = cgemm_split_smem<T>(BM, BN);
+    cudaError_t e = cudaFuncSetAttribute(cgemm_split_kernel<T, BM, BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cgemm_split_kernel<T, BM, BN><<<grid, (BM / 4) * (BN / 4) * kSplitK, smem, s>>>(g);
+    return cudaGetLastError();
+  }
   cgemm_kernel<T, BM, BN><<<grid, (BM / 4) * (BN / 4), 0, s>>>(g);
   return cudaGetLastError();
 }
