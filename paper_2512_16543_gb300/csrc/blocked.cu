@@ -204,7 +204,7 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) cgemm_kernel(const GemmAr
 // depends only on k, so the tile shape still changes no result.  Dynamic shared memory:
 // cgemm_split_smem.
 constexpr int kSplitK = 4;
-constexpr int kSplitKMaxTiles = 4;     // at most this many output tiles (at 64 x 64) per instance
+constexpr int kSplitKMaxTiles = 64;    // at most this many output tiles (at 64 x 64) per instance
 constexpr int kSplitKMinK = 256;       // and a reduction at least this long
 template <class T>
 constexpr size_t cgemm_split_smem(int BM, int BN) {
