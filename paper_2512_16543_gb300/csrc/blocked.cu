@@ -1597,35 +1597,42 @@ __global__ void panel_kernel(const StepArgs<T> a, const Bufs<T> w, int p, int bs
   }
 }
 
-// Pb <- Pb^{-1} (bs x bs Hermitian positive definite) by Gauss-Jordan exchange steps
+// Pb <- Pb^{-1} (bs x bs Hermitian positive definite) by Gauss-Jordan exchange steps on four
+// warps: lane j takes column j and warp w rows 8w..8w+7. Each exchange step reads one copy of
+// the block in shared memory and writes the other, so a step costs one barrier; every thread
+// forms the pivot's reciprocal itself. Each entry takes the same operations in the same order
+// at every block size; only entries inside the bs x bs block are written back.
+constexpr int kBlockInvThreads = 128;
 template <class T>
-__global__ void __launch_bounds__(256) blockinv_kernel(const Bufs<T> w, int bs) {
-  __shared__ cx<T> A[32][33];
-  __shared__ cx<T> colp[32], rowp[32];
-  const int b = blockIdx.x, tid = threadIdx.x;
+__global__ void __launch_bounds__(kBlockInvThreads) blockinv_kernel(const Bufs<T> w, int bs) {
+  __shared__ cx<T> A[2][32][33];
+  const int b = blockIdx.x, tid = threadIdx.x, j = tid & 31, i0 = (tid >> 5) * 8;
   if (!gate_ok(w.ctl, b, C_BRANCH, kDirectMask)) return;
   cx<T>* P = w.Pb + (size_t)b * w.L.sPb;
-  for (int e = tid; e < 32 * 32; e += 256) A[e >> 5][e & 31] = P[e];
+  for (int e = tid; e < 32 * 32; e += kBlockInvThreads) A[0][e >> 5][e & 31] = P[e];
   __syncthreads();
   bool bad = false;
   for (int p = 0; p < bs; ++p) {
-    if (tid < bs) { colp[tid] = A[tid][p]; rowp[tid] = A[p][tid]; }
-    __syncthreads();
-    const cx<T> ap = colp[p];
+    const int c = p & 1;
+    const cx<T> ap = A[c][p][p];
     if (!(ap.re > T(0)) || !cfinite(ap)) bad = true;
     const cx<T> ia = crecip(ap);
-    for (int e = tid; e < bs * bs; e += 256) {
-      const int i = e / bs, j = e - i * bs;
+    const cx<T> t = cmul(A[c][p][j], ia);                  // A[p][j] / A[p][p]
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = i0 + k;
+      const cx<T> ci = A[c][i][p];
       cx<T> v;
-      if (i == p && j == p) v = ia;
-      else if (i == p) v = cscale(cmul(rowp[j], ia), T(-1));
-      else if (j == p) v = cmul(colp[i], ia);
-      else v = csub(A[i][j], cmul(colp[i], cmul(rowp[j], ia)));
-      A[i][j] = v;
+      if (i == p) v = (j == p) ? ia : cscale(t, T(-1));
+      else if (j == p) v = cmul(ci, ia);
+      else v = csub(A[c][i][j], cmul(ci, t));
+      A[c ^ 1][i][j] = v;
     }
     __syncthreads();
   }
-  for (int e = tid; e < 32 * 32; e += 256) P[e] = A[e >> 5][e & 31];
+  const int c = bs & 1;
+  for (int e = tid; e < 32 * 32; e += kBlockInvThreads)
+    if ((e >> 5) < bs && (e & 31) < bs) P[e] = A[c][e >> 5][e & 31];
   if (bad && tid == 0) atomicOr(&w.ctl[8 * b + C_STATUS], WBRZF_STATUS_NOT_PD);
 }
 
@@ -2008,7 +2015,7 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
       const int bs = (K - 32 * p) < 32 ? (K - 32 * p) : 32;
       panel_kernel<T><<<dim3((K * 32 + 255) / 256, B), 256, 0, q>>>(a, w, p, bs);
       WB_TRY(cudaGetLastError());
-      blockinv_kernel<T><<<B, 256, 0, q>>>(w, bs);
+      blockinv_kernel<T><<<B, kBlockInvThreads, 0, q>>>(w, bs);
       WB_TRY(cudaGetLastError());
       WB_TRY(gemm<T>(q, B, K, bs, bs, w.PC, 32, L.sPC, 0, w.Pb, 32, L.sPb, 0, w.PU, 32, L.sPC,
                      one, nullptr, zero, w.ctl, C_BRANCH, kDirectMask));
