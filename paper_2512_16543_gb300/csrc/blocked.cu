@@ -471,10 +471,14 @@ __global__ void omega_kernel(const StepArgs<T> a, const Bufs<T> w, int it, int d
 }
 
 // Cholesky Gy = R^H R (d x d, ld dmax) with column drop; R and 1/R_cc (0 for dropped) out.
+// Column j: every thread forms the pivot's 1 / R_jj itself, row j of R goes straight to Gy
+// (the trailing update reads row j unscaled and scales each entry as it uses it), and warp w
+// updates rows j+1+w, j+9+w, ... of the trailing upper triangle, lane l its columns l, l+32,
+// ...; so a column costs one barrier.
 template <class T>
 __global__ void __launch_bounds__(256) cholesky_kernel(const Bufs<T> w, int d, int pass) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int b = blockIdx.x, tid = threadIdx.x, dmax = w.dmax;
+  const int b = blockIdx.x, tid = threadIdx.x, dmax = w.dmax, lane = tid & 31, wp = tid >> 5;
   if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
   cx<T>* A = reinterpret_cast<cx<T>*>(sm);
   T* cn = reinterpret_cast<T*>(A + (size_t)dmax * dmax);
@@ -482,6 +486,7 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const Bufs<T> w, int d, i
   int* drop = reinterpret_cast<int*>(rv + dmax);
   cx<T>* Gy = w.Gy + (size_t)b * w.L.sGy;
   int* gdrop = w.drop + (size_t)b * dmax;
+  T* grinv = w.rinv + (size_t)b * dmax;
   const T tol_rel = (sizeof(T) == 4) ? T(1e-4) : T(1e-12);
   for (int e = tid; e < d * d; e += 256) {
     const int i = e / d, j = e - i * d;
@@ -492,22 +497,16 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const Bufs<T> w, int d, i
   for (int c = tid; c < d; c += 256) cn[c] = A[c * dmax + c].re;
   __syncthreads();
   for (int j = 0; j < d; ++j) {
-    if (tid == 0) {
-      const T piv = A[j * dmax + j].re;
-      const bool dj = drop[j] || !(cn[j] > T(0)) || !(piv > tol_rel * cn[j]) || !isfinite(piv);
-      drop[j] = dj ? 1 : 0;
-      rv[j] = dj ? T(0) : T(1) / sqrt(piv);
-    }
-    __syncthreads();
-    const T rinv = rv[j];
-    for (int c = j + tid; c < d; c += 256) A[j * dmax + c] = cscale(A[j * dmax + c], rinv);
-    __syncthreads();
-    const int m = d - j - 1;
-    for (int e = tid; e < m * m; e += 256) {
-      const int ai = j + 1 + e / m, ci = j + 1 + e % m;
-      if (ai <= ci) {
+    const T piv = A[j * dmax + j].re;
+    const bool dj = drop[j] || !(cn[j] > T(0)) || !(piv > tol_rel * cn[j]) || !isfinite(piv);
+    const T rinv = dj ? T(0) : T(1) / sqrt(piv);
+    if (tid == 0) { gdrop[j] = dj ? 1 : 0; grinv[j] = rinv; }
+    for (int c = j + tid; c < d; c += 256) Gy[j * dmax + c] = cscale(A[j * dmax + c], rinv);
+    for (int ai = j + 1 + wp; ai < d; ai += 8) {
+      const cx<T> naj = cscale(cscale(A[j * dmax + ai], rinv), T(-1));
+      for (int ci = ai + lane; ci < d; ci += 32) {
         cx<T> v = A[ai * dmax + ci];
-        cfma_jc(v, cscale(A[j * dmax + ai], T(-1)), A[j * dmax + ci]);
+        cfma_jc(v, naj, cscale(A[j * dmax + ci], rinv));
         A[ai * dmax + ci] = v;
       }
     }
@@ -515,49 +514,51 @@ __global__ void __launch_bounds__(256) cholesky_kernel(const Bufs<T> w, int d, i
   }
   for (int e = tid; e < d * d; e += 256) {
     const int i = e / d, j = e - i * d;
-    Gy[i * dmax + j] = (j >= i) ? A[i * dmax + j] : cmk<T>(0, 0);
-  }
-  for (int c = tid; c < d; c += 256) {
-    w.rinv[(size_t)b * dmax + c] = rv[c];
-    gdrop[c] = drop[c];
+    if (j < i) Gy[i * dmax + j] = cmk<T>(0, 0);
   }
 }
 
-// Q <- Q R^{-1}, one thread per row of Q (K x dmax, columns >= d untouched: zero), kFwdRows
+// Q <- Q R^{-1}, two threads per row of Q (K x dmax, columns >= d untouched: zero), kFwdRows
 // rows per CTA.  R, 1 / R_cc and the CTA's rows of Q are staged in shared memory (layout of
-// fwdsubst_smem), so that the d (d - 1) / 2 dependent steps of a row wait on shared memory,
-// not on L2.
+// fwdsubst_smem), so that the dependent steps of a row wait on shared memory, not on L2.
+// Entry c of a row is (Q_c - sum_{a<c} X_a R_ac) / R_cc: the thread of parity 0 sums Q_c and
+// the even a, the other the odd a, each in order; one shuffle joins the two sums (even + odd,
+// the same in both threads), and X_c stays with the thread of parity c mod 2, the one that
+// reads it later.  Every thread runs every step (rows past the last one compute on staging
+// space that is not written back), so the shuffles see the whole warp.
 constexpr int kFwdRows = 64;
 inline size_t fwdsubst_smem(int d, size_t cxb, size_t tb) {
   return ((size_t)d * d + (size_t)kFwdRows * (d + 1)) * cxb + (size_t)d * tb;
 }
 template <class T>
-__global__ void __launch_bounds__(kFwdRows) fwdsubst_kernel(const StepArgs<T> a,
-                                                            const Bufs<T> w, int d) {
+__global__ void __launch_bounds__(2 * kFwdRows) fwdsubst_kernel(const StepArgs<T> a,
+                                                                const Bufs<T> w, int d) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int b = blockIdx.y;
   if (!gate_ok(w.ctl, b, C_ACTIVE, 2)) return;
-  const int dmax = w.dmax, tid = threadIdx.x, ld = d + 1;
+  constexpr int NT = 2 * kFwdRows;
+  const int dmax = w.dmax, tid = threadIdx.x, ld = d + 1, par = tid & 1;
   const int i0 = blockIdx.x * kFwdRows, nrow = min(kFwdRows, a.K - i0);
   cx<T>* const Rs = reinterpret_cast<cx<T>*>(sm);               // d x d
   cx<T>* const Qs = Rs + (size_t)d * d;                          // kFwdRows x (d + 1)
   T* const rvs = reinterpret_cast<T*>(Qs + (size_t)kFwdRows * ld);
   cx<T>* const Qg = w.Q + (size_t)b * w.L.sOm + (size_t)i0 * dmax;
   const cx<T>* const R = w.Gy + (size_t)b * w.L.sGy;
-  for (int e = tid; e < d * d; e += kFwdRows) Rs[e] = R[(e / d) * dmax + e % d];
-  for (int e = tid; e < d; e += kFwdRows) rvs[e] = w.rinv[(size_t)b * dmax + e];
-  for (int e = tid; e < nrow * d; e += kFwdRows) Qs[(e / d) * ld + e % d] = Qg[(e / d) * dmax + e % d];
+  for (int e = tid; e < d * d; e += NT) Rs[e] = R[(e / d) * dmax + e % d];
+  for (int e = tid; e < d; e += NT) rvs[e] = w.rinv[(size_t)b * dmax + e];
+  for (int e = tid; e < nrow * d; e += NT) Qs[(e / d) * ld + e % d] = Qg[(e / d) * dmax + e % d];
   __syncthreads();
-  if (tid < nrow) {
-    cx<T>* const q = Qs + (size_t)tid * ld;
-    for (int c = 0; c < d; ++c) {
-      cx<T> v = q[c];
-      for (int a2 = 0; a2 < c; ++a2) cfma(v, cscale(q[a2], T(-1)), Rs[a2 * d + c]);
-      q[c] = cscale(v, rvs[c]);
-    }
+  cx<T>* const q = Qs + (size_t)(tid >> 1) * ld;
+  for (int c = 0; c < d; ++c) {
+    cx<T> v = par == 0 ? q[c] : cmk<T>(0, 0);
+    for (int a2 = par; a2 < c; a2 += 2) cfma(v, cscale(q[a2], T(-1)), Rs[a2 * d + c]);
+    const cx<T> o = cmk<T>(__shfl_xor_sync(0xffffffffu, v.re, 1),
+                           __shfl_xor_sync(0xffffffffu, v.im, 1));
+    const cx<T> x = cscale(par == 0 ? cadd(v, o) : cadd(o, v), rvs[c]);
+    if (par == (c & 1)) q[c] = x;
   }
   __syncthreads();
-  for (int e = tid; e < nrow * d; e += kFwdRows) Qg[(e / d) * dmax + e % d] = Qs[(e / d) * ld + e % d];
+  for (int e = tid; e < nrow * d; e += NT) Qg[(e / d) * dmax + e % d] = Qs[(e / d) * ld + e % d];
 }
 
 // Cyclic Jacobi eigendecomposition of E (d x d Hermitian, ld dmax): eigenvalues to lam,
@@ -1937,7 +1938,7 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
                          L.sGy, one, nullptr, zero, w.ctl, C_ACTIVE, 2));
           cholesky_kernel<T><<<B, 256, cs, q>>>(w, d, pass);
           WB_TRY(cudaGetLastError());
-          fwdsubst_kernel<T><<<dim3((K + kFwdRows - 1) / kFwdRows, B), kFwdRows,
+          fwdsubst_kernel<T><<<dim3((K + kFwdRows - 1) / kFwdRows, B), 2 * kFwdRows,
                                fwdsubst_smem(d, sizeof(cx<T>), sizeof(T)), q>>>(a, w, d);
           WB_TRY(cudaGetLastError());
         }
