@@ -326,8 +326,9 @@ wbrzf_status wbrzf_set_fp64_small_solves(wbrzf* h, int enable);
 /*
  * Launch shapes of the blocked engine (not part of the paper's method; no result depends on
  * the tile cap, the eigensolver threshold changes results only within the eigensolver's
- * tolerance).  tile_cap: the largest tile edge of the batched complex GEMMs, 64 (default) or
- * 32 (more, smaller CTAs).  jacobi_cta_min (>= 2): the first sketch width at which the fused
+ * tolerance).  tile_cap: the largest tile edge of the batched complex GEMMs: 64, 32 (more,
+ * smaller CTAs), or 0 (default, auto: 32 for a product whose 64 x 64 tiles over the whole
+ * batch number fewer than the GPU's SMs, else 64).  jacobi_cta_min (>= 2): the first sketch width at which the fused
  * Algorithm 1 kernel's eigensolver of E = B B^H runs on the whole CTA instead of one warp
  * (default 12; 65 or more keeps one warp).  wbrzf_group_autotune searches both.
  * Returns WBRZF_ERR_INVALID_ARG for other values.

@@ -274,9 +274,9 @@ class WBRZF:
         _check(lib().wbrzf_set_fp64_small_solves(self._h, int(enable)),
                "wbrzf_set_fp64_small_solves")
 
-    def set_blocked_tuning(self, tile_cap: int = 64, jacobi_cta_min: int = 12) -> None:
-        """Blocked engine launch shapes: GEMM tile cap (64 or 32), first sketch width of the
-        CTA-wide eigensolver."""
+    def set_blocked_tuning(self, tile_cap: int = 0, jacobi_cta_min: int = 12) -> None:
+        """Blocked engine launch shapes: GEMM tile cap (64, 32, or 0 = auto by grid size),
+        first sketch width of the CTA-wide eigensolver."""
         _check(lib().wbrzf_set_blocked_tuning(self._h, int(tile_cap), int(jacobi_cta_min)),
                "wbrzf_set_blocked_tuning")
 

@@ -316,7 +316,11 @@ cgemm_split_kernel(const GemmArgs<T> g) {
 
 // The tile cap of the step being enqueued on this host thread (set by run_blocked from the
 // handle's tuning; the tile shape changes no result: each output's k-sum keeps its order).
+// 0 (auto): 32-wide tiles for a product whose 64 x 64 tiles over the whole batch number fewer
+// than the SMs (one large array's products would otherwise leave most SMs idle while each
+// CTA runs its tile's whole reduction), else 64-wide.
 thread_local int t_tile_cap = 64;
+thread_local int t_sm_count = 0;
 
 template <class T, int BM, int BN>
 cudaError_t launch_cgemm(const GemmArgs<T>& g, int batch, cudaStream_t s) {
@@ -349,8 +353,11 @@ cudaError_t gemm(cudaStream_t s, int batch, int m, int n, int k, const cx<T>* A,
                 ctl, gidx, gmask, dshift, live.m, live.n, live.k, lm, ln, lk};
   // tile widths from the extents known on the host (the control-word limits can only shrink
   // them further), at most the step's tile cap (t_tile_cap)
-  const bool nm = (m < live.m ? m : live.m) <= 32 || t_tile_cap <= 32;
-  const bool nn = (n < live.n ? n : live.n) <= 32 || t_tile_cap <= 32;
+  int cap = t_tile_cap;
+  if (cap == 0)
+    cap = (long long)batch * (((m + 63) / 64) * ((n + 63) / 64)) < t_sm_count ? 32 : 64;
+  const bool nm = (m < live.m ? m : live.m) <= 32 || cap <= 32;
+  const bool nn = (n < live.n ? n : live.n) <= 32 || cap <= 32;
   if (nm && nn) return launch_cgemm<T, 32, 32>(g, batch, s);
   if (nm) return launch_cgemm<T, 32, 64>(g, batch, s);
   if (nn) return launch_cgemm<T, 64, 32>(g, batch, s);
@@ -1839,6 +1846,13 @@ cudaError_t run_blocked(const StepArgs<T>& a, unsigned char* base, cudaStream_t 
   const Bufs<T> w = make_bufs<T>(base, B, N, K, dmax, rcap);
   const BlockedLayout& L = w.L;
   t_tile_cap = a.tile_cap;
+  if (a.tile_cap == 0) {
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 == cudaSuccess)
+      e0 = cudaDeviceGetAttribute(&t_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e0 != cudaSuccess) return e0;
+  }
   const size_t KK = (size_t)K * K;
   cudaError_t e;
   int nl = 0;

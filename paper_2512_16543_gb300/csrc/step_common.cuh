@@ -56,8 +56,8 @@ struct StepArgs {
   int small64;             // blocked engine, complex64: the eigensolver of B B^H, the
                            // capacitance inverse and every direct inverse of G in FP64
   // blocked engine launch shapes (wbrzf_set_blocked_tuning): the largest tile edge of the
-  // batched complex GEMMs (64 or 32), and the sketch width from which the fused kernel's
-  // eigensolver runs on the whole CTA instead of one warp
+  // batched complex GEMMs (64, 32, or 0: chosen per product by grid size), and the sketch
+  // width from which the fused kernel's eigensolver runs on the whole CTA instead of one warp
   int tile_cap, jacobi_cta_min;
   int energy_shortcut;     // tensor kernel: the energy test without the eigensolver
 };

@@ -26,7 +26,7 @@ namespace {
 // where the output is wider than 32, and the CTA-wide eigensolver from sketch width 12 (a
 // phase-clock probe of the fused kernel at K = 64 and 128 measured 12 and 16 equal and 24 and
 // the one-warp solver slower)
-constexpr int kDefaultTileCap = 64;
+constexpr int kDefaultTileCap = 0;     // auto: 32-wide tiles for products too small to fill the SMs
 constexpr int kDefaultJacobiCtaMin = 12;
 
 thread_local char g_cuda_err[256] = "";
@@ -189,7 +189,7 @@ struct wbrzf {
   int gemm_bf16;         // wbrzf_set_precision_mode: BF16 precoder product
   int refine;            // wbrzf_set_precision_mode: Newton refinement steps (0 or 1)
   int small64;           // wbrzf_set_fp64_small_solves
-  int tile_cap;          // wbrzf_set_blocked_tuning: largest batched-GEMM tile edge (64, 32)
+  int tile_cap;          // wbrzf_set_blocked_tuning: largest batched-GEMM tile edge (64, 32; 0 auto)
   int jacobi_cta_min;    // wbrzf_set_blocked_tuning: first sketch width of the CTA eigensolver
   int energy_shortcut;   // wbrzf_set_energy_shortcut (tensor engine)
   cudaStream_t cstream;  // blocked engine: records the bodies of CUDA-graph IF nodes while a
@@ -757,7 +757,8 @@ wbrzf_status wbrzf_set_precision_mode(wbrzf* h, int bf16_products, int refine_st
 }
 
 wbrzf_status wbrzf_set_blocked_tuning(wbrzf* h, int tile_cap, int jacobi_cta_min) {
-  if (!h || (tile_cap != 32 && tile_cap != 64) || jacobi_cta_min < 2) return WBRZF_ERR_INVALID_ARG;
+  if (!h || (tile_cap != 0 && tile_cap != 32 && tile_cap != 64) || jacobi_cta_min < 2)
+    return WBRZF_ERR_INVALID_ARG;
   h->tile_cap = tile_cap;
   h->jacobi_cta_min = jacobi_cta_min;
   invalidate_graph(h);

@@ -165,13 +165,13 @@ def test_group_autotune_chooses_an_accepted_engine_and_keeps_parity():
 
 def test_blocked_launch_shapes_keep_results():
     """The batched GEMMs' tile cap changes no result (each output's k-sum keeps its order):
-    bitwise equal W and X with 64- and 32-wide tiles.  The one-warp and the CTA-wide
+    bitwise equal W and X with 64- and 32-wide tiles and the automatic choice.  The one-warp and the CTA-wide
     eigensolvers both meet the oracle at the complex64 tolerances."""
     sc = channel.LeoScenario(n_x=16, n_y=8, K=96, disc_radius=100e3)
     Hs = channel.trajectory(channel.draw_trajectories(sc, 3, seed=96), 5, dtype=torch.complex128)
     rule = binding.RankRule(eta=0.9, k_init=2, p=8, r_max=32, reinverse_period=3, seed=2)
     outs = {}
-    for cap, jmin in ((64, 12), (32, 12), (64, 65)):
+    for cap, jmin in ((64, 12), (32, 12), (0, 12), (64, 65)):
         h = binding.WBRZF(3, sc.N, sc.K, sc.alpha, sc.sigma2, p_t=sc.p_t, rule=rule,
                           workspace_for="blocked")
         h.set_engine("blocked")
@@ -187,6 +187,8 @@ def test_blocked_launch_shapes_keep_results():
     for t in range(5):
         np.testing.assert_array_equal(outs[(64, 12)][t][0], outs[(32, 12)][t][0])
         np.testing.assert_array_equal(outs[(64, 12)][t][1], outs[(32, 12)][t][1])
+        np.testing.assert_array_equal(outs[(64, 12)][t][0], outs[(0, 12)][t][0])
+        np.testing.assert_array_equal(outs[(64, 12)][t][1], outs[(0, 12)][t][1])
     for key in ((64, 12), (64, 65)):
         for b in range(3):
             Hb = Hs[:, b].numpy().astype(np.complex64).astype(np.complex128)
