@@ -70,7 +70,7 @@ RATE_GAP_BOUND = 0.05        # bit/s/Hz, mean |R_WB - R_full|
 # tensor-core step kernel on this workload, from the ncu capture summarised in
 # profiles/step_tc_kernel_batched_256x32.md; reported only while the kernel source is the one
 # the counters were taken on (sha256 of its four source files, first 16 hex digits).
-NCU_TRAFFIC = {"source_sha": "4b637dd3c7cb3064", "bytes_per_launch": 121144320}
+NCU_TRAFFIC = {"source_sha": "6050579374bc332b", "bytes_per_launch": 121394688}
 KERNEL_SOURCES = ("step_common.cuh", "step_kernel.cuh", "step_tc.cuh", "tc_ptx.cuh")
 
 
